@@ -1,0 +1,265 @@
+"""Conjugate gradient solvers for the oracle (TEST INFRASTRUCTURE ONLY).
+
+  hscg      Algorithm 1 (Hestenes-Stiefel CG, Section 1)
+  sstep_cg  Algorithm 5 (improved adaptive s-step CG, Section 4), with the
+            Algorithm 2 / fixed-s comparators of Section 5 as options
+
+Readings of the paper used here (the CUDA path takes the same ones):
+  C9   Y is stored interleaved, so Y_l is the leading 2l+1 columns.
+  C10  conditions (condy) and (newcondy) use relative residuals ||r||/||b||, phi/||b||.
+  C11  c starts at eps^{-1/2} and is the latest value thereafter.
+  C12  if no l satisfies (condy), s~ = 1.
+  C14  kappa_l = +inf when lambda_min(G_l) <= 2^-44 lambda_max(G_l): below that
+       level the smallest eigenvalue is rounding noise of the N-term inner
+       products in G (this also covers lambda_min <= 0).
+  C15  besides the outer test, sqrt(r'^T G r')/||b|| <= tol is tested after
+       every inner step (``inner_conv_check``), ending the block.
+  C16  convergence is declared on the updated residual, then confirmed with the
+       true residual b - A x; if that is above tol, r := b - A x, p := r,
+       psi := 1 and the iteration continues (a "replacement").
+  C17  alpha invalid (p'^T G B p' <= 0 or not finite) at inner step j > 0 ends
+       the block with s_k = j; at j = 0 the solve stops with BREAKDOWN.
+       r'^T G r' <= 0 after a step reads as "residual estimate zero": the step is
+       kept and the convergence test fires.
+  C21  the order inside the inner step is as printed in Alg. 5.
+  C22  the Meurant-Tichy state is fed every alpha; the estimates are used from
+       global iteration 2 on (m + j + 1 > 1).
+  C23  gamma_l := kappa(Y_{l+1}) for l = 1..s~-1; the break test at step j uses gamma_{j+1}.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import basis as bs
+from .ritz import RitzTracker
+
+EPS64 = 2.0 ** -53
+KAPPA_CUT = 2.0 ** -44
+
+OK, NOT_CONVERGED, BREAKDOWN = 0, 3, 2
+
+
+def _norm(v) -> float:
+    return float(np.sqrt(v @ v))
+
+
+def hscg(A, b, x0, tol: float, max_iters: int = 100000):
+    """Algorithm 1 (HSCG).  Stops when ||r_i||/||b|| <= tol on the updated
+    residual, then confirms with the true residual (readings C16, C20).
+
+    Returns (x, info) with info = {iters, alphas, betas, replacements, status,
+    relres_true}.
+    """
+    x = np.array(x0, dtype=np.float64, copy=True)
+    r = b - A @ x
+    p = r.copy()
+    rr = float(r @ r)
+    normb = _norm(b)
+    alphas, betas = [], []
+    it = 0
+    replacements = 0
+    status = NOT_CONVERGED
+    while it < max_iters:
+        if math.sqrt(rr) / normb <= tol:
+            rt = b - A @ x
+            if _norm(rt) / normb <= tol:
+                status = OK
+                break
+            r, p = rt, rt.copy()
+            rr = float(r @ r)
+            replacements += 1
+        q = A @ p
+        alpha = rr / float(p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = float(r @ r)
+        beta = rr_new / rr
+        p = r + beta * p
+        rr = rr_new
+        alphas.append(alpha)
+        betas.append(beta)
+        it += 1
+    relres = _norm(b - A @ x) / normb
+    return x, dict(iters=it, alphas=alphas, betas=betas, replacements=replacements,
+                   status=status, relres_true=relres)
+
+
+@dataclasses.dataclass
+class Options:
+    """Parameters of Algorithm 5 (sigma = smax, s̄_0 = s0, f) and the readings' switches."""
+    smax: int = 8
+    basis: str = "chebyshev"          # monomial | newton | chebyshev
+    s0: int | None = None              # reading C13: s̄_0 = sigma
+    f: int | None = None               # reading C13: f = sigma
+    max_outer: int = 100000
+    c_mode: str = "xi"                 # xi | xi_scaled | one | kappa_ratio | const
+    c_const: float = 1.0
+    newton_scale: str = "capacity"     # capacity | paper_unit   (reading C6)
+    cheb_params: str = "standard"      # standard | paper_printed (reading C5)
+    inner_conv_check: bool = True      # reading C15
+    eps: float = EPS64
+    kappa_cut: float = KAPPA_CUT       # reading C14
+    y_fp32: bool = False               # store the basis rounded to FP32
+    variant: str = "improved"          # improved (Alg. 5) | fixed (s_k = sigma)
+
+
+def kappa_estimates(G: np.ndarray, sbar: int, kappa_cut: float = KAPPA_CUT):
+    """kappa_l ~ kappa(Y_l) = sqrt(kappa(G_l)), l = 1..sbar (Section 3).
+
+    G_l is the leading (2l+1) x (2l+1) block of G; its extreme eigenvalues come
+    from a dense symmetric eigensolve.  Entry 0 is unused.
+    """
+    kap = np.full(sbar + 1, np.nan)
+    lmins = np.full(sbar + 1, np.nan)
+    lmaxs = np.full(sbar + 1, np.nan)
+    for l in range(1, sbar + 1):
+        n = 2 * l + 1
+        w = np.linalg.eigvalsh(G[:n, :n])
+        lmins[l], lmaxs[l] = w[0], w[-1]
+        if not (w[-1] > 0.0) or w[0] <= kappa_cut * w[-1]:
+            kap[l] = math.inf
+        else:
+            kap[l] = math.sqrt(w[-1] / w[0])
+    return kap, lmins, lmaxs
+
+
+def c_value(mode: str, lmin: float, lmax: float, psi: float, c_const: float = 1.0) -> float:
+    """c_{m+j+1} of Alg. 5 (eq. xiupd) and the alternatives of Section 5.1."""
+    if mode == "xi":
+        return max(1.0, lmax * math.sqrt(psi / lmin))
+    if mode == "xi_scaled":
+        return max(1.0, lmax * math.sqrt(psi) / lmin)
+    if mode == "one":
+        return 1.0
+    if mode == "kappa_ratio":
+        return lmax / lmin
+    if mode == "const":
+        return c_const
+    raise ValueError(mode)
+
+
+def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: bool = False):
+    """Algorithm 5 (improved adaptive s-step CG), step by step.
+
+    A is anything with ``A @ v`` (a scipy sparse matrix).  Returns (x, info);
+    info holds the status, counts, the alpha/beta sequence, the final Ritz
+    estimates and a per-outer-loop decision log ``hist`` (list of dicts).
+    """
+    o = opts or Options()
+    kind = bs.BASIS_NAMES[o.basis]
+    sigma = o.smax
+    s0 = o.s0 if o.s0 is not None else sigma
+    f = o.f if o.f is not None else sigma
+    eps = o.eps
+
+    x = np.array(x0, dtype=np.float64, copy=True)
+    r = b - A @ x
+    p = r.copy()
+    normb = _norm(b)
+    psi = 1.0
+    c = eps ** -0.5
+    m = 0
+    theta, gamma, mu = bs.basis_params(bs.MONOMIAL, sigma, None, None)
+    ritz = RitzTracker()
+    alphas, betas = [], []
+    hist = []
+    replacements = 0
+    status = NOT_CONVERGED
+    s_prev = None
+    done = False
+    for k in range(o.max_outer):
+        sbar = s0 if k == 0 else min(s_prev + f, sigma)
+        Y = bs.krylov_basis(A, p, r, sbar, theta, gamma, mu)
+        if o.y_fp32:
+            Y = Y.astype(np.float32).astype(np.float64)
+        G = Y.T @ Y
+        kap, _, _ = kappa_estimates(G, sbar, o.kappa_cut)
+        normr = math.sqrt(G[1, 1])
+        if o.variant == "fixed":
+            stilde = sbar
+        else:
+            thr = tol / (c * eps * normr / normb)
+            cands = [l for l in range(1, sbar + 1) if kap[l] <= thr]
+            stilde = max(cands) if cands else 1
+        n = 2 * stilde + 1
+        Gs = G[:n, :n]
+        Bs = bs.b_matrix(stilde, theta, gamma, mu)
+        gam = {l: kap[l + 1] for l in range(1, stilde)}
+        pc = np.zeros(n); pc[bs.p_index(0)] = 1.0
+        rc = np.zeros(n); rc[bs.r_index(0)] = 1.0
+        xc = np.zeros(n)
+        rr = float(rc @ Gs @ rc)
+        phi = math.sqrt(max(rr, 0.0))
+        c_start = c
+        sk = 0
+        converged_est = False
+        breakdown = False
+        for j in range(stilde):
+            Bp = Bs @ pc
+            den = float(pc @ (Gs @ Bp))
+            alpha = rr / den if den > 0.0 else math.nan
+            if not math.isfinite(alpha) or alpha <= 0.0:
+                if j == 0:
+                    breakdown = True
+                break
+            sk = j + 1
+            xc = xc + alpha * pc
+            rc = rc - alpha * Bp
+            rr_new = float(rc @ Gs @ rc)
+            if not (rr_new > 0.0) or not math.isfinite(rr_new):
+                converged_est = True
+                break
+            alphas.append(alpha)
+            beta = rr_new / rr
+            pc = rc + beta * pc
+            phi = max(phi, math.sqrt(rr_new))
+            psi = psi / (psi + beta)
+            ritz.push(alpha, betas[-1] if betas else None)
+            betas.append(beta)
+            if m + j + 1 > 1:
+                c = c_value(o.c_mode, ritz.lmin, ritz.lmax, psi, o.c_const)
+            rr = rr_new
+            if o.inner_conv_check and math.sqrt(rr_new) / normb <= tol:
+                converged_est = True
+                break
+            if o.variant != "fixed" and j < stilde - 1 and \
+                    gam[j + 1] >= tol / (c * eps * phi / normb):
+                break
+        if breakdown:
+            status = BREAKDOWN
+            hist.append(dict(sbar=sbar, stilde=stilde, sk=0, kappa=kap.tolist(), c=c_start))
+            break
+        Yn = Y[:, :n]
+        x = x + Yn @ xc
+        r = Yn @ rc
+        p = Yn @ pc
+        m += sk
+        s_prev = sk
+        hist.append(dict(sbar=sbar, stilde=stilde, sk=sk, kappa=kap.tolist(), c_start=c_start,
+                         c=c, phi=phi, lmin=ritz.lmin, lmax=ritz.lmax,
+                         relres_est=math.sqrt(max(rr, 0.0)) / normb, m=m))
+        if m > 1 and kind != bs.MONOMIAL:
+            theta, gamma, mu = bs.basis_params(kind, sigma, ritz.lmin, ritz.lmax,
+                                               o.newton_scale, o.cheb_params)
+        if not converged_est and not o.inner_conv_check:
+            converged_est = _norm(r) / normb <= tol
+        if converged_est:
+            rt = b - A @ x
+            if _norm(rt) / normb <= tol:
+                status = OK
+                done = True
+            else:
+                r, p = rt, rt.copy()
+                psi = 1.0
+                replacements += 1
+                hist[-1]["replaced"] = True
+        if done:
+            break
+    relres = _norm(b - A @ x) / normb
+    info = dict(status=status, outer=len(hist), inner=m, alphas=alphas, betas=betas,
+                hist=hist, replacements=replacements, relres_true=relres,
+                lmin=ritz.lmin, lmax=ritz.lmax, c=c, psi=psi)
+    return x, info
