@@ -1,0 +1,322 @@
+"""Benchmark: converged adaptive s-step CG solves/s on one GB300 (and HSCG beside it).
+
+Workload (default): FP64 3D 7-point variable-coefficient diffusion on a 160^3
+grid (N = 4,096,000), per-face conductivities exp(g) with g ~ N(0, 1) i.i.d.,
+b ~ N(0, 1), x0 = 0, sigma = 16, Newton basis with Leja-ordered shifts from the
+running Ritz estimates, tol = 1e-10 (relative true residual).  One step = one
+complete solve through the C ABI (every kernel of the method), inputs resident
+in HBM.  Plain Hestenes-Stiefel CG (Algorithm 1) on the same GPU is timed
+beside it.  Synthetic, seeded data.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 (torchrun), every rank solves its own copy (replicas: the method has
+no data-parallel exchange on one system), value = total solves / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s & HBM GB/s at rel. residual 1e-10: s-step CG vs plain HSCG, one GB300"
+WORKLOADS = {
+    "varcoef3d_160": dict(desc="FP64 3D 7-pt var-coef diffusion 160^3 (N=4,096,000), k=exp(N(0,1)) per face, "
+                               "b~N(0,1), x0=0", smax=16, basis="newton", tol=1e-10),
+    "poisson2d_64": dict(desc="FP64 2D 5-pt Poisson 64x64 CSR (N=4096), b=A x*, x*~U(-1,1), x0=0",
+                         smax=8, basis="chebyshev", tol=1e-10),
+}
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="varcoef3d_160", choices=sorted(WORKLOADS))
+    ap.add_argument("--hscg-steps", type=int, default=3)
+    ap.add_argument("--cpu-outer", type=int, default=3, help="outer loops in the oracle sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def load_inputs(name):
+    from sscg_inputs import generators as gen
+    return gen.config_problem(name)
+
+
+def oracle_counts(name):
+    path = os.path.join(ROOT, "tests", "golden", "oracle_counts.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        if name in d:
+            return d[name]
+    return None
+
+
+def time_oracle_sample(op, b, x0, cfg, n_outer):
+    """Time the CPU oracle (as it stands) for n_outer outer loops of the workload."""
+    from oracle import cg
+    from oracle.operators import as_matrix
+    A = as_matrix(op)
+    opts = cg.Options(smax=cfg["smax"], basis=cfg["basis"], max_outer=n_outer)
+    t = time.perf_counter()
+    _, info = cg.sstep_cg(A, b, x0, cfg["tol"], opts)
+    el = time.perf_counter() - t
+    return el, info["outer"], info["inner"]
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={SMI_FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def algorithmic_bytes_per_outer(n, s, bytes_a):
+    """Bytes the method must move per outer loop (A once, 2s-1 new basis columns
+    written once, 2s+1 columns read once by the recombination, x/r/p)."""
+    return bytes_a + 8.0 * n * (4 * s + 6)
+
+
+def run_reference(args, cfg):
+    """The oracle as it stands, on the host cores: a bounded sample per step."""
+    op, b, x0, _ = load_inputs(args.workload)
+    counts = oracle_counts(args.workload)
+    n_outer = args.cpu_outer
+    times = []
+    for i in range(args.warmup + args.steps):
+        el, outer, inner = time_oracle_sample(op, b, x0, cfg, n_outer)
+        if i >= args.warmup:
+            times.append(el / max(outer, 1))
+    per_outer = statistics.median(times)
+    full_outer = counts["sstep_outer"] if counts else None
+    value = 1.0 / (per_outer * full_outer) if full_outer else None
+    sample = (f"{n_outer} outer loops of the full-size solve per step, scaled by the oracle's own full-solve "
+              f"outer-loop count ({full_outer}, tests/golden/oracle_counts.json)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_outer * (full_outer or 0) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["desc"], "s_max": cfg["smax"], "basis": cfg["basis"], "tol": cfg["tol"]},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    cfg = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, cfg)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1908_04081_gb300 as pkg
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+
+    op, b_np, x0_np, _ = load_inputs(args.workload)
+    n = b_np.size
+    if hasattr(op, "kx"):
+        solver = pkg.Solver.stencil(op.kx, op.ky, op.kz)
+        bytes_a = 8.0 * (op.kx.size + op.ky.size + (op.kz.size if op.kz is not None else 0) + n)
+    else:
+        solver = pkg.Solver.csr(op.rowptr, op.col, op.val)
+        bytes_a = 12.0 * op.val.size + 8.0 * (n + 1)
+    b = torch.tensor(b_np, dtype=torch.float64, device=dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def solve(profile=1):
+        x.zero_()
+        return solver.solve(b, x, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], hist_cap=20000,
+                            profile=profile)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K complete solves, per-phase CUDA events inside each
+    stats = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(solve())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed = float(t.item())
+    clocks = clk.summary()
+    ok = all(s.status == 0 and s.true_relres <= cfg["tol"] for s in stats)
+    value = world * args.steps / elapsed
+    ms_per_step = elapsed / args.steps * 1e3
+
+    # roofline of the dominant kernel (the Gram contraction: FP64 ALU bound)
+    t_gram = sum(s.t_gram_ms for s in stats) / 1e3
+    f_gram = sum(s.gram_flops for s in stats)
+    n_gram = sum(s.n_gram_launches for s in stats)
+    t_mpk = sum(s.t_mpk_ms for s in stats) / 1e3
+    phase_ms = {k: sum(getattr(s, "t_" + k + "_ms") for s in stats) / args.steps
+                for k in ("mpk", "gram", "kappa", "control", "recombine", "other")}
+    gram_tflops = f_gram / t_gram / 1e12 if t_gram > 0 else None
+    st0 = stats[-1]
+    hist = pkg.sscg.history(st0)
+    alg_bytes = sum(algorithmic_bytes_per_outer(n, h["sbar"], bytes_a) for h in hist)
+    hbm_gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
+    launches = sum(s.kernel_launches for s in stats)
+
+    # ---- HSCG on the same GPU
+    hs = []
+    if args.hscg_steps > 0:
+        solver.hscg(b, x.zero_(), tol=cfg["tol"])
+        torch.cuda.synchronize()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(args.hscg_steps):
+            x.zero_()
+            hs.append(solver.hscg(b, x, tol=cfg["tol"]))
+        h1.record(stream)
+        torch.cuda.synchronize()
+        hscg_el = h0.elapsed_time(h1) / 1e3
+        hscg = {"value": args.hscg_steps / hscg_el, "unit": "solves/s", "ms_per_step": hscg_el / args.hscg_steps * 1e3,
+                "iters": hs[-1].inner_iters, "true_relres": hs[-1].true_relres,
+                "hbm_gbs_alg": (hs[-1].inner_iters * (bytes_a + 8.0 * n * 9)) / (hscg_el / args.hscg_steps) / 1e9}
+    else:
+        hscg = None
+
+    # ---- end to end through the C ABI with host buffers (copies inside)
+    pin_b = torch.tensor(b_np, dtype=torch.float64).pin_memory()
+    pin_x = torch.zeros(n, dtype=torch.float64).pin_memory()
+    bn, xn = pin_b.numpy(), pin_x.numpy()
+    e2e_steps = max(0, min(args.steps, args.e2e_steps))
+    e2e = None
+    if e2e_steps > 0:
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        for _ in range(e2e_steps):
+            xn[:] = 0.0
+            solver.solve_host(bn, xn, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"])
+        te = time.perf_counter() - te
+        e2e = {"value": world * e2e_steps / te, "unit": "solves/s", "h2d_bytes_per_step": 16 * n,
+               "d2h_bytes_per_step": 8 * n, "steps": e2e_steps}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        el, outer, _ = time_oracle_sample(op, b_np, x0_np, cfg, args.cpu_outer)
+        per_outer = el / max(outer, 1)
+        cpu = {"value": 1.0 / (per_outer * st0.outer_iters), "unit": "solves/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"first {outer} outer loops of the full-size oracle solve ({el:.1f} s), scaled by the "
+                         f"GPU solve's {st0.outer_iters} outer loops; numpy/OpenBLAS Gram on all cores, "
+                         f"scipy SpMV single-threaded"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["desc"], "s_max": cfg["smax"], "basis": cfg["basis"], "tol": cfg["tol"],
+                       "parallelism": "replicas" if world > 1 else "single-gpu",
+                       "l2": "inputs larger than L2 (basis Y 1.08 GB, coefficients 99 MB)",
+                       "timing": "CUDA events around K solves; per-phase CUDA events inside each solve"},
+            "converged": ok, "true_relres": max(s.true_relres for s in stats),
+            "outer_loops": st0.outer_iters, "inner_iters": st0.inner_iters, "host_syncs": st0.host_syncs,
+            "ms_per_outer_loop": ms_per_step / st0.outer_iters,
+            "hbm_gbs_alg": hbm_gbs, "phase_ms_per_solve": phase_ms,
+            "hscg": hscg,
+            "roofline": {"bound": "alu", "kernel": "gram_partial+gram_reduce (G = Y^T Y, FP64)",
+                         "achieved": gram_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": (gram_tflops / FP64_PEAK_TFLOPS) if gram_tflops else None,
+                         "traffic": None, "launches": n_gram,
+                         "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 is not in "
+                                      "MEASURED_PEAKS.json)"},
+            "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

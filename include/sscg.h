@@ -1,0 +1,239 @@
+/*
+ * sscg.h - C ABI of libsscg: adaptive s-step conjugate gradient on one GB300.
+ *
+ * The method is the improved adaptive s-step CG of E. C. Carson, "An Adaptive
+ * s-step Conjugate Gradient Algorithm with Dynamic Basis Updating" (2019),
+ * Algorithm 5, for sparse symmetric positive definite A.  Every step of a solve
+ * runs in this library's CUDA kernels; the host only enqueues work and polls a
+ * device-side "done" flag.
+ *
+ * Conventions for every entry point
+ *  - Return value: 0 (SSCG_OK) or a negative SSCG_ERR_* code; solver outcomes
+ *    (SSCG_NOT_CONVERGED, SSCG_BREAKDOWN) are positive.  No C++ exception
+ *    crosses this boundary.  sscg_strerror() names every code.
+ *  - Floating point is IEEE binary64 throughout unless stated.
+ *  - "device pointer" means memory of the current CUDA device (cudaMalloc or a
+ *    torch CUDA tensor's data_ptr()); "host pointer" means ordinary host memory.
+ *  - A handle owns a CUDA stream given at creation (NULL = the legacy default
+ *    stream); all of its work is ordered on that stream.  Calls on one handle
+ *    must not overlap from several host threads.
+ *  - Vectors are dense, contiguous, length n, with the row numbering of A.
+ */
+#ifndef SSCG_H
+#define SSCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SSCG_MAX_S 16 /* largest sigma (maximum s_k) the kernels support */
+
+typedef struct sscg_ctx* sscg_t;
+
+/* Polynomial basis of the s-step Krylov basis, Section 2 eqs. (rho),
+ * (newtbasis), (chebbasis).  Until two iterations have run, Algorithm 5 uses
+ * the monomial basis whatever is chosen here. */
+typedef enum { SSCG_MONOMIAL = 0, SSCG_NEWTON = 1, SSCG_CHEBYSHEV = 2 } sscg_basis;
+
+/* c in conditions (condy)/(newcondy): Alg. 5 sets c = max{1, lmax sqrt(psi/lmin)}
+ * (eq. xiupd, SSCG_C_XI).  The other modes are the alternatives of Section 5.1:
+ * the scale-consistent form max{1, lmax sqrt(psi)/lmin}, c = 1, c = lmax/lmin,
+ * and a user constant. */
+typedef enum { SSCG_C_XI = 0, SSCG_C_XI_SCALED = 1, SSCG_C_ONE = 2, SSCG_C_KAPPA_RATIO = 3,
+               SSCG_C_CONST = 4 } sscg_c_mode;
+
+/* Status codes. */
+enum {
+  SSCG_OK = 0,
+  SSCG_BREAKDOWN = 2,        /* p'^T G B p' <= 0 at the first step of a block: A not SPD (numerically) */
+  SSCG_NOT_CONVERGED = 3,    /* max_outer (or max_iters) reached */
+  SSCG_ERR_INVALID_ARG = -1,
+  SSCG_ERR_CUDA = -2,        /* a CUDA runtime call failed; sscg_last_cuda_error() has the text */
+  SSCG_ERR_NO_MEMORY = -3,
+  SSCG_ERR_UNSUPPORTED = -4
+};
+
+/* Options of Algorithm 5 and of the readings the library takes where the paper
+ * leaves a choice.  sscg_opts_default() fills the defaults given per field. */
+typedef struct {
+  int s0;                /* initial s (s-bar_0, Alg. 5 input); default 0 = sigma */
+  int f;                 /* maximum basis growth per outer loop (Alg. 5 input); default 0 = sigma */
+  int max_outer;         /* outer-loop cap; default 100000 */
+  int c_mode;            /* sscg_c_mode; default SSCG_C_XI */
+  int newton_scale;      /* 0: gamma_l = (lmax - lmin)/4 (interval capacity); 1: gamma_l = 1 as printed; default 0 */
+  int cheb_params;       /* 0: rho_l(z) = T_l((z-c)/h); 1: eq. (chebbasis) as printed; default 0 */
+  int inner_conv_check;  /* 1: test sqrt(r'^T G r')/||b|| <= tol after every inner step; default 1 */
+  int y_fp32;            /* 1: store the basis Y in binary32 (arithmetic stays binary64); default 0 */
+  int variant;           /* 0: Algorithm 5; 1: fixed s-step CG (s_k = sigma, no break test); default 0 */
+  int check_every;       /* outer loops enqueued between two polls of the done flag; default 4 */
+  int use_graph;         /* 1: replay one outer loop as a CUDA graph; default 1 */
+  int profile;           /* 1: time each kernel phase with CUDA events (direct launches); default 0 */
+  double c_const;        /* c for SSCG_C_CONST; default 1 */
+  double eps;            /* unit roundoff in (condy)/(newcondy); default 2^-53 */
+  double kappa_cut;      /* kappa_l = inf when lambda_min(G_l) <= kappa_cut * lambda_max(G_l); default 2^-44 */
+} sscg_opts;
+
+/* Per-outer-loop decision record (Alg. 5): s-bar_k, s-tilde_k, s_k, c at the
+ * start and end of the block, phi, the Ritz estimates after the block, the
+ * coordinate residual estimate, and kappa_l ~ kappa(Y_l) for l = 1..s-bar_k
+ * (kappa[0] unused; +inf when numerically singular). */
+typedef struct {
+  int sbar, stilde, sk, replaced;
+  double c_start, c_end, phi, lmin, lmax, relres_est;
+  double kappa[SSCG_MAX_S + 1];
+} sscg_outer_record;
+
+/* Statistics of the last solve.  `hist` is caller-owned and optional: when
+ * non-NULL, up to hist_cap records are written, one per outer loop. */
+typedef struct {
+  int status;            /* SSCG_OK / SSCG_NOT_CONVERGED / SSCG_BREAKDOWN */
+  int outer_iters;       /* outer loops = global synchronisations of the method */
+  int inner_iters;       /* total CG iterations m */
+  int host_syncs;        /* times the host waited on the device during the solve */
+  int replacements;      /* residual replacements after a failed true-residual check */
+  int kernel_launches;   /* kernels of this library launched by the solve (graph nodes counted) */
+  double lambda_min, lambda_max; /* final Ritz estimates (Algs. 3-4) */
+  double c_last;         /* final c */
+  double true_relres;    /* ||b - A x|| / ||b|| at exit, computed on the device */
+  double upd_relres;     /* coordinate estimate of the updated residual at exit */
+  /* profile == 1 only: summed kernel time per phase (ms) and launch counts */
+  double t_mpk_ms, t_gram_ms, t_kappa_ms, t_control_ms, t_recombine_ms, t_other_ms;
+  int n_gram_launches;
+  double gram_flops;     /* algorithmic flops of all Gram launches: sum of 2 * n * (2s+1)(2s+2)/2 */
+  double mpk_spmvs;      /* shifted SpMVs of all matrix-powers levels: sum over loops of 2 s-bar_k - 1 */
+  sscg_outer_record* hist;
+  int hist_cap;
+  int hist_len;
+} sscg_stats;
+
+/* ---------------------------------------------------------------- handles */
+
+/* Create a handle for a CSR matrix (Section 1: sparse SPD A).
+ * rowptr: n+1 int64 offsets; col: nnz int32 column indices (sorted or not);
+ * val: nnz binary64 values.  A must be symmetric positive definite; this is not
+ * checked (a non-SPD A ends a solve with SSCG_BREAKDOWN or no convergence).
+ * on_device: 1 if the three arrays are device pointers, 0 if host pointers.
+ * The handle copies A into its own device memory; the caller keeps ownership of
+ * its arrays.  cuda_stream: a cudaStream_t or NULL.
+ * Errors: INVALID_ARG (n <= 0, nnz < 0, NULL pointers), NO_MEMORY, CUDA. */
+int sscg_create_csr(sscg_t* out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                    const double* val, int on_device, void* cuda_stream);
+
+/* Create a handle for a 2D 5-point or 3D 7-point variable-coefficient stencil
+ * with homogeneous Dirichlet boundary: (A u)_i = sum over the faces f of cell i
+ * of k_f (u_i - u_nb(f)), u_nb = 0 outside the grid.  Cells are numbered x
+ * fastest, then y, then z.  shape = {nx, ny, nz} (nz = 1 for dim = 2).
+ * Face arrays, C order (slowest first):
+ *   kx: [nz][ny][nx+1]  (west face of cell x is kx[..][..][x], east is x+1)
+ *   ky: [nz][ny+1][nx]
+ *   kz: [nz+1][ny][nx]  (dim = 3 only; NULL for dim = 2)
+ * All k_f must be > 0.  on_device/cuda_stream as for sscg_create_csr; the
+ * handle copies the coefficients.  Errors: INVALID_ARG, NO_MEMORY, CUDA. */
+int sscg_create_stencil(sscg_t* out, int dim, const int64_t shape[3], const double* kx,
+                        const double* ky, const double* kz, int on_device, void* cuda_stream);
+
+/* Release the handle and all device memory it owns (safe on NULL). */
+void sscg_destroy(sscg_t h);
+
+/* Problem size n of the handle, or a negative error code. */
+int64_t sscg_size(sscg_t h);
+
+/* ---------------------------------------------------------------- solves */
+
+/* Fill opts with the defaults documented in sscg_opts. */
+void sscg_opts_default(sscg_opts* opts);
+
+/* Solve A x = b by Algorithm 5 (improved adaptive s-step CG, Section 4).
+ * b: device pointer, length n (read only).  x: device pointer, length n; on
+ * entry the initial guess x0, on exit the solution.  tol = eps* (relative
+ * residual ||b - A x||/||b||), s_max = sigma in [1, SSCG_MAX_S].
+ * opts may be NULL (defaults); stats may be NULL.
+ * Convergence is declared on the coordinate residual estimate and confirmed by
+ * a true residual computed on the device; if that check fails, r := b - A x,
+ * p := r and the iteration continues (counted in stats->replacements).
+ * Returns SSCG_OK, SSCG_NOT_CONVERGED, SSCG_BREAKDOWN or a negative error.
+ * The call returns after the solve has finished on the device. */
+int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg_basis basis,
+               const sscg_opts* opts, sscg_stats* stats);
+
+/* As sscg_solve with b and x in HOST memory: copies b and x0 to the device,
+ * solves, copies x back (all on the handle's stream). */
+int sscg_solve_host(sscg_t h, const double* b_host, double* x_host, double tol, int s_max,
+                    sscg_basis basis, const sscg_opts* opts, sscg_stats* stats);
+
+/* Hestenes-Stiefel CG (Algorithm 1, Section 1), the comparator.  Same b, x,
+ * tol conventions and true-residual confirmation as sscg_solve.  max_iters
+ * caps the iterations (<= 0: 100000).  stats->inner_iters is the iteration
+ * count; outer_iters = inner_iters. */
+int sscg_solve_hscg(sscg_t h, const double* b, double* x, double tol, int max_iters,
+                    sscg_stats* stats);
+
+/* Ritz estimates (Algs. 3-4, eq. lest) of the handle's last s-step solve. */
+int sscg_ritz(sscg_t h, double* lmin, double* lmax);
+
+/* ----------------------------------------------------- single steps (tests) */
+
+/* y = A v (device pointers, length n). */
+int sscg_spmv(sscg_t h, const double* v, double* y);
+
+/* The s-step basis of eq. (cg-krylovbasis) by the recurrence eq. (rho):
+ * Y = [P_0, R_0, P_1, R_1, ..., P_{s-1}, R_{s-1}, P_s] (interleaved column
+ * order: the basis Y_l of the first l inner steps is the leading 2l+1 columns),
+ * P_0 = p, R_0 = r, P_{l+1} = ((A - theta_l) P_l - mu_{l-1} P_{l-1}) / gamma_l.
+ * p, r: device, length n.  theta, gamma, mu: HOST arrays of length s (mu[l]
+ * multiplies rho_l in the recurrence for rho_{l+2}).  Y: device, column major,
+ * leading dimension ldy >= n, 2s+1 columns, written.  1 <= s <= SSCG_MAX_S. */
+int sscg_build_basis(sscg_t h, const double* p, const double* r, int s, const double* theta,
+               const double* gamma, const double* mu, double* Y, int64_t ldy);
+
+/* G = Y^T Y (Section 2, the block inner product of Alg. 5), Y device column
+ * major n x ncols with leading dimension ldy, G device ncols x ncols row major
+ * (symmetric, both triangles written).  1 <= ncols <= 2*SSCG_MAX_S+1.
+ * Deterministic: a fixed blocking and reduction order independent of timing.
+ * cuda_stream: cudaStream_t or NULL.  Scratch for the block partial sums is
+ * allocated and freed inside the call. */
+int sscg_gram(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, void* cuda_stream);
+
+/* kappa_l ~ sqrt(kappa(G_l)) for the leading (2l+1) blocks of G, l = 1..sbar
+ * (Section 3), from the extreme eigenvalues of each block.  G: device,
+ * ldg x ldg row major, ldg >= 2*sbar+1.  kappa, lmin, lmax: device arrays of
+ * length sbar+1 (entry 0 unused).  kappa_l = +inf when lmin <= kappa_cut * lmax. */
+int sscg_kappa(const double* G, int ldg, int sbar, double kappa_cut, double* kappa, double* lmin,
+               double* lmax, void* cuda_stream);
+
+/* The first s Leja points of [-1, 1] starting 1, -1 (eq. newtbasis on the
+ * reference interval), computed on the device.  t: HOST array of length s. */
+int sscg_leja(int s, double* t);
+
+/* --------------------------------------------------- differentiable solve */
+
+/* Gradient of a loss L(x) with respect to the face conductivities of a stencil
+ * handle, for x = A^{-1} b: with the adjoint state lam = A^{-1} dL/dx (A is
+ * symmetric, so the adjoint solve is another sscg_solve), dA/dk_f is
+ * (e_i - e_j)(e_i - e_j)^T for the interior face between cells i and j and
+ * e_i e_i^T for a boundary face of cell i, so
+ *   dL/dk_f = -(lam_i - lam_j)(x_i - x_j)   (lam = x = 0 outside the grid).
+ * dL/db = lam needs no call.  lam, x: device, length n.  gkx, gky, gkz:
+ * device arrays with the shapes of kx, ky, kz (gkz NULL for dim = 2),
+ * overwritten.  Errors: INVALID_ARG (NULL pointers, not a stencil handle). */
+int sscg_stencil_face_grad(sscg_t h, const double* lam, const double* x, double* gkx, double* gky,
+                           double* gkz);
+
+/* dL/dA_ij = -lam_i x_j for every stored entry of a CSR handle (each stored
+ * value treated as an independent parameter).  gval: device, length nnz,
+ * overwritten.  Errors: INVALID_ARG (NULL pointers, not a CSR handle). */
+int sscg_csr_value_grad(sscg_t h, const double* lam, const double* x, double* gval);
+
+/* ------------------------------------------------------------------ misc */
+
+const char* sscg_strerror(int code);
+const char* sscg_last_cuda_error(void);
+/* Library version string. */
+const char* sscg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSCG_H */

@@ -39,12 +39,22 @@ def r_index(l: int) -> int:
 # ----------------------------------------------------------------------------
 
 def _leja_dlog(t: float, pts) -> float:
-    """d/dt of sum_m log|t - t_m|: strictly decreasing between two neighbours."""
-    return sum(1.0 / (t - tm) for tm in pts)
+    """d/dt of sum_m log|t - t_m|: strictly decreasing between two neighbours.
+
+    Summed left to right in plain binary64 (Python's built-in sum() of floats
+    is compensated since 3.12; plain order keeps the bisection's decisions a
+    function of the IEEE operations alone)."""
+    acc = 0.0
+    for tm in pts:
+        acc = acc + 1.0 / (t - tm)
+    return acc
 
 
 def _leja_logprod(t: float, pts) -> float:
-    return sum(math.log(abs(t - tm)) for tm in pts)
+    acc = 0.0
+    for tm in pts:
+        acc = acc + math.log(abs(t - tm))
+    return acc
 
 
 def leja_points(s: int) -> np.ndarray:

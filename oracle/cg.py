@@ -53,11 +53,14 @@ def hscg(A, b, x0, tol: float, max_iters: int = 100000):
     Returns (x, info) with info = {iters, alphas, betas, replacements, status,
     relres_true}.
     """
+    normb = _norm(b)
+    if normb == 0.0:  # b = 0: the solution is x = 0
+        return np.zeros_like(np.asarray(x0, dtype=np.float64)), dict(
+            iters=0, alphas=[], betas=[], replacements=0, status=OK, relres_true=0.0)
     x = np.array(x0, dtype=np.float64, copy=True)
     r = b - A @ x
     p = r.copy()
     rr = float(r @ r)
-    normb = _norm(b)
     alphas, betas = [], []
     it = 0
     replacements = 0
@@ -104,6 +107,12 @@ class Options:
     kappa_cut: float = KAPPA_CUT       # reading C14
     y_fp32: bool = False               # store the basis rounded to FP32
     variant: str = "improved"          # improved (Alg. 5) | fixed (s_k = sigma)
+    # replay: a decision log [{"stilde", "sk", "replaced"}, ...] from another
+    # implementation.  The oracle then takes those decisions instead of its own,
+    # evaluates its own ones beside them and records, for each decision, the
+    # log-distance of the deciding quantity to its threshold ("margins"); the
+    # solve ends after the last record.
+    replay: list | None = None
 
 
 def kappa_estimates(G: np.ndarray, sbar: int, kappa_cut: float = KAPPA_CUT):
@@ -155,12 +164,16 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
     f = o.f if o.f is not None else sigma
     eps = o.eps
 
+    normb = _norm(b)
+    if normb == 0.0:  # b = 0: the solution is x = 0
+        return np.zeros_like(np.asarray(x0, dtype=np.float64)), dict(
+            status=OK, outer=0, inner=0, alphas=[], betas=[], hist=[], replacements=0,
+            relres_true=0.0, lmin=None, lmax=None, c=None, psi=1.0)
     x = np.array(x0, dtype=np.float64, copy=True)
     r = b - A @ x
     p = r.copy()
-    normb = _norm(b)
     psi = 1.0
-    c = eps ** -0.5
+    c = 1.0 / math.sqrt(eps)  # c_1 = eps^{-1/2}
     m = 0
     theta, gamma, mu = bs.basis_params(bs.MONOMIAL, sigma, None, None)
     ritz = RitzTracker()
@@ -178,12 +191,22 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
         G = Y.T @ Y
         kap, _, _ = kappa_estimates(G, sbar, o.kappa_cut)
         normr = math.sqrt(G[1, 1])
+        margins = {}
         if o.variant == "fixed":
             stilde = sbar
         else:
             thr = tol / (c * eps * normr / normb)
             cands = [l for l in range(1, sbar + 1) if kap[l] <= thr]
             stilde = max(cands) if cands else 1
+            if o.replay is not None:
+                own = stilde
+                stilde = o.replay[k]["stilde"]
+                if own != stilde:
+                    lo, hi = min(own, stilde), max(own, stilde)
+                    margins["stilde"] = min(abs(math.log(kap[l] / thr)) for l in range(lo, hi + 1)
+                                            if 1 <= l <= sbar and math.isfinite(kap[l]) and kap[l] > 0) \
+                        if any(math.isfinite(kap[l]) for l in range(lo, hi + 1) if 1 <= l <= sbar) else math.inf
+        forced_sk = o.replay[k]["sk"] if o.replay is not None else None
         n = 2 * stilde + 1
         Gs = G[:n, :n]
         Bs = bs.b_matrix(stilde, theta, gamma, mu)
@@ -222,12 +245,25 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
             if m + j + 1 > 1:
                 c = c_value(o.c_mode, ritz.lmin, ritz.lmax, psi, o.c_const)
             rr = rr_new
-            if o.inner_conv_check and math.sqrt(rr_new) / normb <= tol:
-                converged_est = True
-                break
-            if o.variant != "fixed" and j < stilde - 1 and \
-                    gam[j + 1] >= tol / (c * eps * phi / normb):
-                break
+            own_conv = o.inner_conv_check and math.sqrt(rr_new) / normb <= tol
+            own_brk = (not own_conv) and o.variant != "fixed" and j < stilde - 1 and \
+                gam[j + 1] >= tol / (c * eps * phi / normb)
+            if forced_sk is None:
+                if own_conv:
+                    converged_est = True
+                    break
+                if own_brk:
+                    break
+            else:
+                stop = j + 1 >= forced_sk
+                if stop != (own_conv or own_brk or j == stilde - 1):
+                    qc = abs(math.log(math.sqrt(rr_new) / (normb * tol))) if o.inner_conv_check else math.inf
+                    qb = abs(math.log(gam[j + 1] * c * eps * phi / (normb * tol))) \
+                        if (j < stilde - 1 and math.isfinite(gam[j + 1])) else math.inf
+                    margins[f"stop_j{j}"] = min(qc, qb)
+                if stop:
+                    converged_est = own_conv
+                    break
         if breakdown:
             status = BREAKDOWN
             hist.append(dict(sbar=sbar, stilde=stilde, sk=0, kappa=kap.tolist(), c=c_start))
@@ -240,12 +276,25 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
         s_prev = sk
         hist.append(dict(sbar=sbar, stilde=stilde, sk=sk, kappa=kap.tolist(), c_start=c_start,
                          c=c, phi=phi, lmin=ritz.lmin, lmax=ritz.lmax,
-                         relres_est=math.sqrt(max(rr, 0.0)) / normb, m=m))
+                         relres_est=math.sqrt(max(rr, 0.0)) / normb, m=m, margins=margins))
         if m > 1 and kind != bs.MONOMIAL:
             theta, gamma, mu = bs.basis_params(kind, sigma, ritz.lmin, ritz.lmax,
                                                o.newton_scale, o.cheb_params)
         if not converged_est and not o.inner_conv_check:
-            converged_est = _norm(r) / normb <= tol
+            # outer-level test only (reading C15 off): the coordinate estimate
+            # of the updated residual at the end of the block
+            converged_est = math.sqrt(max(rr, 0.0)) / normb <= tol
+        if o.replay is not None:
+            if k + 1 >= len(o.replay):
+                status = OK if _norm(b - A @ x) / normb <= tol else NOT_CONVERGED
+                break
+            if o.replay[k].get("replaced"):
+                rt = b - A @ x
+                r, p = rt, rt.copy()
+                psi = 1.0
+                replacements += 1
+                hist[-1]["replaced"] = True
+            continue
         if converged_est:
             rt = b - A @ x
             if _norm(rt) / normb <= tol:

@@ -1,0 +1,52 @@
+"""Differentiable solve: x = A(k)^{-1} b for a face-conductivity stencil.
+
+``stencil_solve(kx, ky, kz, b)`` is a ``torch.autograd.Function``.  The
+forward pass is the adaptive s-step solve (Algorithm 5); the backward pass is
+the adjoint s-step solve A lam = dL/dx (A is symmetric) followed by the
+library's gradient-gather kernel, dL/dk_f = -(lam_i - lam_j)(x_i - x_j), and
+dL/db = lam.  Both solves and the gather run in libsscg.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import sscg
+
+
+class StencilSolve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, kx, ky, kz, b, tol=1e-10, s_max=16, basis="newton"):
+        solver = sscg.Solver.stencil(kx.detach().contiguous(), ky.detach().contiguous(),
+                                     kz.detach().contiguous() if kz is not None else None)
+        x = torch.zeros_like(b)
+        st = solver.solve(b.detach().contiguous(), x, tol=tol, s_max=s_max, basis=basis)
+        if st.status != sscg.OK:
+            raise sscg.SscgError(f"forward solve status {st.status}")
+        ctx.solver = solver
+        ctx.cfg = (tol, s_max, basis)
+        ctx.has_kz = kz is not None
+        ctx.save_for_backward(x)
+        ctx.shapes = (kx.shape, ky.shape, kz.shape if kz is not None else None)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        tol, s_max, basis = ctx.cfg
+        solver = ctx.solver
+        lam = torch.zeros_like(x)
+        st = solver.solve(gx.contiguous(), lam, tol=tol, s_max=s_max, basis=basis)
+        if st.status != sscg.OK:
+            raise sscg.SscgError(f"adjoint solve status {st.status}")
+        sx, sy, sz = ctx.shapes
+        gkx = torch.empty(sx, dtype=x.dtype, device=x.device)
+        gky = torch.empty(sy, dtype=x.dtype, device=x.device)
+        gkz = torch.empty(sz, dtype=x.dtype, device=x.device) if ctx.has_kz else None
+        sscg.sscg_stencil_face_grad(solver.h, lam, x, gkx, gky, gkz)
+        solver.close()
+        return gkx, gky, gkz, lam, None, None, None
+
+
+def stencil_solve(kx, ky, kz, b, tol=1e-10, s_max=16, basis="newton"):
+    """x = A(k)^{-1} b, differentiable in kx, ky, kz and b."""
+    return StencilSolve.apply(kx, ky, kz, b, tol, s_max, basis)

@@ -1,0 +1,704 @@
+// Host side of libsscg: handles, the outer-loop driver of Algorithm 5 (Carson
+// 2019, Section 4), the HSCG comparator (Algorithm 1) and the step-level entry
+// points.  The host only enqueues kernels: every decision of a solve is taken
+// by device code, and the host polls a device "done" flag once every
+// `check_every` outer loops (bodies after convergence exit immediately).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sscg_internal.cuh"
+
+using namespace sscg;
+
+namespace {
+
+thread_local std::string g_last_cuda_error;
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_cuda_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? SSCG_ERR_NO_MEMORY : SSCG_ERR_CUDA;
+}
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+  } while (0)
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t count) {
+    if (count <= n) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e == cudaSuccess) n = count;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct sscg_ctx {
+  Operator op{};
+  int64_t n = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;  // private stream (stream capture needs a non-legacy stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // operator storage
+  DevBuf<int64_t> rowptr;
+  DevBuf<int32_t> col;
+  DevBuf<double> val, kx, ky, kz, diag;
+  // solve storage
+  int64_t ld = 0;
+  DevBuf<double> Y, G, partials, rt, b, x, r, p, q, leja;
+  DevBuf<SolveState> state;
+  DevBuf<sscg_outer_record> hist;
+  SolveState* host_state = nullptr;  // pinned mirror
+  // cached graph of one outer loop
+  cudaGraphExec_t graph = nullptr;
+  int graph_sigma = -1;
+  int graph_launches = 0;
+  double last_lmin = 0.0, last_lmax = 0.0;
+};
+
+namespace {
+
+int init_common(sscg_ctx* h, void* cuda_stream) {
+  h->user_stream = (cudaStream_t)cuda_stream;
+  CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+  CK(cudaMallocHost(&h->host_state, sizeof(SolveState)));
+  CK(h->leja.ensure(kMaxS));
+  CK(launch_leja(h->leja.p, kMaxS, h->stream));
+  CK(h->state.ensure(1));
+  CK(h->G.ensure(kMaxCols * kMaxCols));
+  return SSCG_OK;
+}
+
+// order the private stream after the caller's stream (start) and the caller's
+// stream after the private one (end)
+int join_in(sscg_ctx* h) {
+  CK(cudaEventRecord(h->ev_in, h->user_stream));
+  CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+  return SSCG_OK;
+}
+int join_out(sscg_ctx* h) {
+  CK(cudaEventRecord(h->ev_out, h->stream));
+  CK(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0));
+  return SSCG_OK;
+}
+
+template <typename T>
+cudaMemcpyKind kind_of(int on_device) {
+  return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+
+int ensure_solve_buffers(sscg_ctx* h, int sigma, int hist_cap) {
+  const int64_t n = h->n;
+  h->ld = round_up(n, 32);
+  const size_t ycount = (size_t)h->ld * (2 * sigma + 1);
+  if (ycount > h->Y.n) {
+    if (h->graph) {
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+      h->graph_sigma = -1;
+    }
+  }
+  CK(h->Y.ensure(ycount));
+  const int gb = gram_blocks(n);
+  const int rb = reduce_blocks(n);
+  CK(h->partials.ensure(std::max((size_t)gb * kMaxPairs, (size_t)4 * rb)));
+  CK(h->rt.ensure(n));
+  CK(h->b.ensure(n));
+  CK(h->x.ensure(n));
+  if (hist_cap > 0 && (size_t)hist_cap > h->hist.n) {
+    if (h->graph) {
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+      h->graph_sigma = -1;
+    }
+    CK(h->hist.ensure(hist_cap));
+  }
+  return SSCG_OK;
+}
+
+// Enqueue one outer loop of Algorithm 5.  Returns the number of kernels.
+int enqueue_body(sscg_ctx* h, int sigma, cudaStream_t st, std::vector<cudaEvent_t>* evs, int* nlaunch) {
+  SolveState* ds = h->state.p;
+  LevelCoef coef{ds->theta, ds->inv_gamma, ds->mu};
+  int count = 0;
+  auto mark = [&](int i) -> int {
+    if (evs) CK(cudaEventRecord((*evs)[i], st));
+    return SSCG_OK;
+  };
+  int rc;
+  if ((rc = mark(0))) return rc;
+  for (int l = 0; l < sigma; ++l) {
+    CK(launch_mpk_level(h->op, h->Y.p, h->ld, l, ds, 0, coef, false, st));
+    ++count;
+  }
+  if ((rc = mark(1))) return rc;
+  CK(launch_gram(h->Y.p, h->n, h->ld, nullptr, 0, ds, h->partials.p, gram_blocks(h->n), h->G.p, kMaxCols, false,
+                 st));
+  count += 2;
+  if ((rc = mark(2))) return rc;
+  CK(launch_kappa(h->G.p, kMaxCols, ds, 0, 0.0 /* taken from the state */, ds->kappa, ds->glmin,
+                  ds->glmax, sigma, st));
+  ++count;
+  if ((rc = mark(3))) return rc;
+  CK(launch_control(ds, h->G.p, kMaxCols, h->leja.p, h->hist.n ? h->hist.p : nullptr, st));
+  ++count;
+  if ((rc = mark(4))) return rc;
+  CK(launch_recombine(ds, h->Y.p, h->ld, h->x.p, h->n, false, st));
+  ++count;
+  if ((rc = mark(5))) return rc;
+  CK(launch_true_residual(ds, h->op, h->b.p, h->x.p, h->rt.p, h->partials.p, reduce_blocks(h->n), st));
+  CK(launch_apply_replacement(ds, h->rt.p, h->Y.p, h->ld, h->n, false, h->hist.n ? h->hist.p : nullptr, st));
+  count += 4;
+  if ((rc = mark(6))) return rc;
+  *nlaunch = count;
+  return SSCG_OK;
+}
+
+int build_graph(sscg_ctx* h, int sigma) {
+  if (h->graph && h->graph_sigma == sigma) return SSCG_OK;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int nl = 0;
+  int rc = enqueue_body(h, sigma, h->stream, nullptr, &nl);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  h->graph_sigma = sigma;
+  h->graph_launches = nl;
+  return SSCG_OK;
+}
+
+void fill_state_config(SolveState& s, int sigma, double tol, int basis, const sscg_opts& o, int hist_cap) {
+  std::memset(&s, 0, sizeof(s));
+  s.sigma = sigma;
+  s.s0 = o.s0 > 0 ? std::min(o.s0, sigma) : sigma;
+  s.f = o.f > 0 ? o.f : sigma;
+  s.basis = basis;
+  s.c_mode = o.c_mode;
+  s.newton_scale = o.newton_scale;
+  s.cheb_params = o.cheb_params;
+  s.inner_conv_check = o.inner_conv_check;
+  s.variant = o.variant;
+  s.max_outer = o.max_outer > 0 ? o.max_outer : 100000;
+  s.y_fp32 = o.y_fp32;
+  s.hist_cap = hist_cap;
+  s.tol = tol;
+  s.eps = o.eps;
+  s.kappa_cut = o.kappa_cut;
+  s.c_const = o.c_const;
+  s.sbar = s.s0;
+  s.status = SSCG_NOT_CONVERGED;
+  s.c = 1.0 / std::sqrt(o.eps);  // c_1 = eps^{-1/2} (Alg. 5)
+  s.psi = 1.0;
+  for (int l = 0; l < kMaxS; ++l) {
+    s.theta[l] = 0.0;  // monomial basis until Ritz values exist
+    s.gamma[l] = 1.0;
+    s.inv_gamma[l] = 1.0;
+    s.mu[l] = 0.0;
+  }
+}
+
+int validate_opts(const sscg_opts& o) {
+  if (o.c_mode < 0 || o.c_mode > SSCG_C_CONST) return SSCG_ERR_INVALID_ARG;
+  if (!(o.eps > 0.0) || !(o.kappa_cut >= 0.0)) return SSCG_ERR_INVALID_ARG;
+  if (o.y_fp32) return SSCG_ERR_UNSUPPORTED;
+  return SSCG_OK;
+}
+
+}  // namespace
+
+// ===================================================================== API
+extern "C" {
+
+const char* sscg_version(void) { return "sscg 0.1 (sm_103a)"; }
+
+const char* sscg_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+const char* sscg_strerror(int code) {
+  switch (code) {
+    case SSCG_OK: return "ok";
+    case SSCG_BREAKDOWN: return "breakdown: p'^T G B p' <= 0 at the first step of a block (A not SPD?)";
+    case SSCG_NOT_CONVERGED: return "not converged within the iteration cap";
+    case SSCG_ERR_INVALID_ARG: return "invalid argument";
+    case SSCG_ERR_CUDA: return "CUDA runtime error (see sscg_last_cuda_error)";
+    case SSCG_ERR_NO_MEMORY: return "out of device memory";
+    case SSCG_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+void sscg_opts_default(sscg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->s0 = 0;
+  o->f = 0;
+  o->max_outer = 100000;
+  o->c_mode = SSCG_C_XI;
+  o->newton_scale = 0;
+  o->cheb_params = 0;
+  o->inner_conv_check = 1;
+  o->y_fp32 = 0;
+  o->variant = 0;
+  o->check_every = 4;
+  o->use_graph = 1;
+  o->profile = 0;
+  o->c_const = 1.0;
+  o->eps = std::ldexp(1.0, -53);
+  o->kappa_cut = std::ldexp(1.0, -44);
+}
+
+int sscg_create_csr(sscg_t* out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                    const double* val, int on_device, void* cuda_stream) {
+  if (!out || n <= 0 || nnz < 0 || !rowptr || (nnz > 0 && (!col || !val))) return SSCG_ERR_INVALID_ARG;
+  if (n > (int64_t)INT32_MAX) return SSCG_ERR_INVALID_ARG;  // int32 column indices
+  *out = nullptr;
+  sscg_ctx* h = new (std::nothrow) sscg_ctx();
+  if (!h) return SSCG_ERR_NO_MEMORY;
+  int rc = init_common(h, cuda_stream);
+  if (rc) {
+    sscg_destroy(h);
+    return rc;
+  }
+  h->n = n;
+  auto fail = [&](cudaError_t e, const char* w) {
+    int r = cuda_fail(e, w);
+    sscg_destroy(h);
+    return r;
+  };
+  cudaError_t e;
+  if ((e = h->rowptr.ensure(n + 1)) != cudaSuccess) return fail(e, "alloc rowptr");
+  if ((e = h->col.ensure(std::max<int64_t>(nnz, 1))) != cudaSuccess) return fail(e, "alloc col");
+  if ((e = h->val.ensure(std::max<int64_t>(nnz, 1))) != cudaSuccess) return fail(e, "alloc val");
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if ((e = cudaMemcpyAsync(h->rowptr.p, rowptr, (n + 1) * sizeof(int64_t), k, h->stream)) != cudaSuccess)
+    return fail(e, "copy rowptr");
+  if (nnz > 0) {
+    if ((e = cudaMemcpyAsync(h->col.p, col, nnz * sizeof(int32_t), k, h->stream)) != cudaSuccess)
+      return fail(e, "copy col");
+    if ((e = cudaMemcpyAsync(h->val.p, val, nnz * sizeof(double), k, h->stream)) != cudaSuccess)
+      return fail(e, "copy val");
+  }
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return fail(e, "create_csr sync");
+  h->op.kind = 0;
+  h->op.n = n;
+  h->op.rowptr = h->rowptr.p;
+  h->op.col = h->col.p;
+  h->op.val = h->val.p;
+  *out = h;
+  return SSCG_OK;
+}
+
+int sscg_create_stencil(sscg_t* out, int dim, const int64_t shape[3], const double* kx, const double* ky,
+                        const double* kz, int on_device, void* cuda_stream) {
+  if (!out || !shape || (dim != 2 && dim != 3) || !kx || !ky || (dim == 3 && !kz)) return SSCG_ERR_INVALID_ARG;
+  const int64_t nx = shape[0], ny = shape[1], nz = dim == 3 ? shape[2] : 1;
+  if (nx <= 0 || ny <= 0 || nz <= 0 || nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30))
+    return SSCG_ERR_INVALID_ARG;
+  *out = nullptr;
+  sscg_ctx* h = new (std::nothrow) sscg_ctx();
+  if (!h) return SSCG_ERR_NO_MEMORY;
+  int rc = init_common(h, cuda_stream);
+  if (rc) {
+    sscg_destroy(h);
+    return rc;
+  }
+  const int64_t n = nx * ny * nz;
+  h->n = n;
+  auto fail = [&](cudaError_t e, const char* w) {
+    int r = cuda_fail(e, w);
+    sscg_destroy(h);
+    return r;
+  };
+  const size_t cx = (size_t)nz * ny * (nx + 1), cy = (size_t)nz * (ny + 1) * nx, cz = (size_t)(nz + 1) * ny * nx;
+  cudaError_t e;
+  if ((e = h->kx.ensure(cx)) != cudaSuccess) return fail(e, "alloc kx");
+  if ((e = h->ky.ensure(cy)) != cudaSuccess) return fail(e, "alloc ky");
+  if (dim == 3 && (e = h->kz.ensure(cz)) != cudaSuccess) return fail(e, "alloc kz");
+  if ((e = h->diag.ensure(n)) != cudaSuccess) return fail(e, "alloc diag");
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if ((e = cudaMemcpyAsync(h->kx.p, kx, cx * sizeof(double), k, h->stream)) != cudaSuccess) return fail(e, "copy kx");
+  if ((e = cudaMemcpyAsync(h->ky.p, ky, cy * sizeof(double), k, h->stream)) != cudaSuccess) return fail(e, "copy ky");
+  if (dim == 3 && (e = cudaMemcpyAsync(h->kz.p, kz, cz * sizeof(double), k, h->stream)) != cudaSuccess)
+    return fail(e, "copy kz");
+  h->op.kind = 1;
+  h->op.n = n;
+  h->op.dim = dim;
+  h->op.nx = (int)nx;
+  h->op.ny = (int)ny;
+  h->op.nz = (int)nz;
+  h->op.kx = h->kx.p;
+  h->op.ky = h->ky.p;
+  h->op.kz = dim == 3 ? h->kz.p : nullptr;
+  h->op.diag = h->diag.p;
+  if ((e = launch_stencil_diag(h->op, h->diag.p, h->stream)) != cudaSuccess) return fail(e, "stencil diag");
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return fail(e, "create_stencil sync");
+  *out = h;
+  return SSCG_OK;
+}
+
+void sscg_destroy(sscg_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->rowptr.release();
+  h->col.release();
+  h->val.release();
+  h->kx.release();
+  h->ky.release();
+  h->kz.release();
+  h->diag.release();
+  h->Y.release();
+  h->G.release();
+  h->partials.release();
+  h->rt.release();
+  h->b.release();
+  h->x.release();
+  h->r.release();
+  h->p.release();
+  h->q.release();
+  h->leja.release();
+  h->state.release();
+  h->hist.release();
+  if (h->host_state) cudaFreeHost(h->host_state);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int64_t sscg_size(sscg_t h) { return h ? h->n : SSCG_ERR_INVALID_ARG; }
+
+int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg_basis basis, const sscg_opts* opts,
+               sscg_stats* stats) {
+  if (!h || !b || !x || !(tol > 0.0) || s_max < 1 || s_max > kMaxS) return SSCG_ERR_INVALID_ARG;
+  if (basis < SSCG_MONOMIAL || basis > SSCG_CHEBYSHEV) return SSCG_ERR_INVALID_ARG;
+  sscg_opts o;
+  sscg_opts_default(&o);
+  if (opts) o = *opts;
+  int rc = validate_opts(o);
+  if (rc) return rc;
+  const int sigma = s_max;
+  int hist_cap = 0;
+  if (stats && stats->hist && stats->hist_cap > 0) hist_cap = stats->hist_cap;
+  if (o.profile && hist_cap == 0) hist_cap = std::min(o.max_outer > 0 ? o.max_outer : 100000, 100000);
+  hist_cap = std::min(hist_cap, o.max_outer > 0 ? o.max_outer : 100000);
+  if ((rc = ensure_solve_buffers(h, sigma, hist_cap))) return rc;
+  if ((rc = join_in(h))) return rc;
+  cudaStream_t st = h->stream;
+  const int64_t n = h->n;
+  CK(cudaMemcpyAsync(h->b.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->x.p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // configuration -> device state (through the pinned mirror; the copy is
+  // complete before the mirror is touched again, see the syncs below)
+  CK(cudaStreamSynchronize(st));
+  fill_state_config(*h->host_state, sigma, tol, (int)basis, o, hist_cap);
+  CK(cudaMemcpyAsync(h->state.p, h->host_state, sizeof(SolveState), cudaMemcpyHostToDevice, st));
+  CK(launch_init_state(h->state.p, h->op, h->b.p, h->x.p, h->Y.p, h->ld, h->partials.p, reduce_blocks(n), false, st));
+  int launches = 2;
+  int host_syncs = 1;
+
+  const bool prof = o.profile != 0;
+  const bool graph = o.use_graph && !prof;
+  if (graph && (rc = build_graph(h, sigma))) return rc;
+  const int every = std::max(1, o.check_every);
+  double tph[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<cudaEvent_t> evs;
+  if (prof) {
+    evs.resize(7 * every);
+    for (auto& e : evs) CK(cudaEventCreate(&e));
+  }
+  int bodies = 0;
+  while (true) {
+    for (int b2 = 0; b2 < every; ++b2) {
+      if (graph) {
+        CK(cudaGraphLaunch(h->graph, st));
+        launches += h->graph_launches;
+      } else {
+        std::vector<cudaEvent_t> sub;
+        if (prof) sub.assign(evs.begin() + 7 * b2, evs.begin() + 7 * b2 + 7);
+        int nl = 0;
+        if ((rc = enqueue_body(h, sigma, st, prof ? &sub : nullptr, &nl))) return rc;
+        launches += nl;
+      }
+      ++bodies;
+    }
+    CK(cudaMemcpyAsync(h->host_state, h->state.p, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ++host_syncs;
+    if (prof) {
+      for (int b2 = 0; b2 < every; ++b2)
+        for (int ph = 0; ph < 6; ++ph) {
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, evs[7 * b2 + ph], evs[7 * b2 + ph + 1]));
+          tph[ph] += ms;
+        }
+    }
+    if (h->host_state->done) break;
+  }
+  for (auto& e : evs) cudaEventDestroy(e);
+  // final true residual for the statistics
+  CK(launch_final_norm(h->state.p, h->op, h->b.p, h->x.p, h->rt.p, h->partials.p, reduce_blocks(n), st));
+  launches += 2;
+  CK(cudaMemcpyAsync(x, h->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->host_state, h->state.p, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+  std::vector<sscg_outer_record> hh;
+  const SolveState& s0 = *h->host_state;
+  CK(cudaStreamSynchronize(st));
+  ++host_syncs;
+  const SolveState s = s0;
+  const int outer = s.k;
+  const int nh = std::min(outer, hist_cap);
+  if (nh > 0) {
+    hh.resize(nh);
+    CK(cudaMemcpy(hh.data(), h->hist.p, nh * sizeof(sscg_outer_record), cudaMemcpyDeviceToHost));
+  }
+  h->last_lmin = s.lmin;
+  h->last_lmax = s.lmax;
+  if ((rc = join_out(h))) return rc;
+  if (stats) {
+    stats->status = s.status;
+    stats->outer_iters = outer;
+    stats->inner_iters = s.m;
+    stats->host_syncs = host_syncs;
+    stats->replacements = s.replacements;
+    stats->kernel_launches = launches;
+    stats->lambda_min = s.lmin;
+    stats->lambda_max = s.lmax;
+    stats->c_last = s.c;
+    stats->true_relres = s.normb > 0.0 ? std::sqrt(s.rt2) / s.normb : 0.0;
+    stats->upd_relres = s.upd_relres;
+    stats->t_mpk_ms = tph[0];
+    stats->t_gram_ms = tph[1];
+    stats->t_kappa_ms = tph[2];
+    stats->t_control_ms = tph[3];
+    stats->t_recombine_ms = tph[4];
+    stats->t_other_ms = tph[5];
+    stats->n_gram_launches = prof ? outer : 0;
+    double gf = 0.0, mf = 0.0;
+    for (int k = 0; k < nh; ++k) {
+      const int nc = 2 * hh[k].sbar + 1;
+      gf += 2.0 * (double)n * (nc * (nc + 1) / 2);
+      mf += (double)(2 * hh[k].sbar - 1);
+    }
+    stats->gram_flops = gf;
+    stats->mpk_spmvs = mf;
+    if (stats->hist && stats->hist_cap > 0) {
+      const int cp = std::min(nh, stats->hist_cap);
+      std::memcpy(stats->hist, hh.data(), cp * sizeof(sscg_outer_record));
+      stats->hist_len = cp;
+    } else {
+      stats->hist_len = 0;
+    }
+  }
+  (void)bodies;
+  return s.status;
+}
+
+int sscg_solve_host(sscg_t h, const double* b_host, double* x_host, double tol, int s_max, sscg_basis basis,
+                    const sscg_opts* opts, sscg_stats* stats) {
+  if (!h || !b_host || !x_host) return SSCG_ERR_INVALID_ARG;
+  const int64_t n = h->n;
+  DevBuf<double> db, dx;
+  CK(db.ensure(n));
+  CK(dx.ensure(n));
+  CK(cudaMemcpyAsync(db.p, b_host, n * sizeof(double), cudaMemcpyHostToDevice, h->user_stream));
+  CK(cudaMemcpyAsync(dx.p, x_host, n * sizeof(double), cudaMemcpyHostToDevice, h->user_stream));
+  int rc = sscg_solve(h, db.p, dx.p, tol, s_max, basis, opts, stats);
+  if (rc < 0) {
+    db.release();
+    dx.release();
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(x_host, dx.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->user_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->user_stream);
+  db.release();
+  dx.release();
+  if (e != cudaSuccess) return cuda_fail(e, "solve_host copy back");
+  return rc;
+}
+
+int sscg_solve_hscg(sscg_t h, const double* b, double* x, double tol, int max_iters, sscg_stats* stats) {
+  if (!h || !b || !x || !(tol > 0.0)) return SSCG_ERR_INVALID_ARG;
+  const int64_t n = h->n;
+  cudaStream_t st = h->stream;
+  int rc;
+  if ((rc = ensure_solve_buffers(h, 1, 0))) return rc;
+  CK(h->r.ensure(n));
+  CK(h->p.ensure(n));
+  CK(h->q.ensure(n));
+  if ((rc = join_in(h))) return rc;
+  CK(cudaMemcpyAsync(h->b.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->x.p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  SolveState& hs = *h->host_state;
+  std::memset(&hs, 0, sizeof(hs));
+  hs.tol = tol;
+  hs.status = SSCG_NOT_CONVERGED;
+  hs.h_max_iters = max_iters > 0 ? max_iters : 100000;
+  hs.max_outer = hs.h_max_iters;
+  CK(cudaMemcpyAsync(h->state.p, h->host_state, sizeof(SolveState), cudaMemcpyHostToDevice, st));
+  const int nb = reduce_blocks(n);
+  CK(launch_hscg_init(h->state.p, h->op, h->b.p, h->x.p, h->r.p, h->p.p, h->partials.p, nb, st));
+  int launches = 2, host_syncs = 1;
+  const int per_check = 8, checks_per_poll = 4;
+  while (true) {
+    for (int c = 0; c < checks_per_poll; ++c) {
+      CK(launch_hscg_check(h->state.p, h->op, h->b.p, h->x.p, h->r.p, h->p.p, h->rt.p, h->partials.p, nb, st));
+      for (int it = 0; it < per_check; ++it)
+        CK(launch_hscg_iteration(h->state.p, h->op, h->x.p, h->r.p, h->p.p, h->q.p, h->partials.p, nb, st));
+      launches += 4 + 4 * per_check;
+    }
+    CK(launch_hscg_check(h->state.p, h->op, h->b.p, h->x.p, h->r.p, h->p.p, h->rt.p, h->partials.p, nb, st));
+    launches += 4;
+    CK(cudaMemcpyAsync(h->host_state, h->state.p, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ++host_syncs;
+    if (h->host_state->done) break;
+  }
+  CK(launch_final_norm(h->state.p, h->op, h->b.p, h->x.p, h->rt.p, h->partials.p, nb, st));
+  CK(cudaMemcpyAsync(x, h->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->host_state, h->state.p, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ++host_syncs;
+  const SolveState s = *h->host_state;
+  if ((rc = join_out(h))) return rc;
+  if (stats) {
+    stats->status = s.status;
+    stats->outer_iters = s.h_iters;
+    stats->inner_iters = s.h_iters;
+    stats->host_syncs = host_syncs;
+    stats->replacements = s.replacements;
+    stats->kernel_launches = launches + 2;
+    stats->true_relres = s.normb > 0.0 ? std::sqrt(s.rt2) / s.normb : 0.0;
+    stats->upd_relres = s.normb > 0.0 ? std::sqrt(s.h_rr) / s.normb : 0.0;
+    stats->hist_len = 0;
+  }
+  return s.status;
+}
+
+int sscg_ritz(sscg_t h, double* lmin, double* lmax) {
+  if (!h || !lmin || !lmax) return SSCG_ERR_INVALID_ARG;
+  *lmin = h->last_lmin;
+  *lmax = h->last_lmax;
+  return SSCG_OK;
+}
+
+int sscg_spmv(sscg_t h, const double* v, double* y) {
+  if (!h || !v || !y) return SSCG_ERR_INVALID_ARG;
+  int rc;
+  if ((rc = join_in(h))) return rc;
+  CK(launch_spmv(h->op, v, y, h->stream));
+  if ((rc = join_out(h))) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  return SSCG_OK;
+}
+
+int sscg_build_basis(sscg_t h, const double* p, const double* r, int s, const double* theta, const double* gamma,
+               const double* mu, double* Y, int64_t ldy) {
+  if (!h || !p || !r || !theta || !gamma || !mu || !Y || s < 1 || s > kMaxS || ldy < h->n)
+    return SSCG_ERR_INVALID_ARG;
+  double coef[3 * kMaxS];
+  for (int l = 0; l < s; ++l) {
+    if (!(gamma[l] != 0.0)) return SSCG_ERR_INVALID_ARG;
+    coef[l] = theta[l];
+    coef[kMaxS + l] = 1.0 / gamma[l];
+    coef[2 * kMaxS + l] = mu[l];
+  }
+  DevBuf<double> dc;
+  CK(dc.ensure(3 * kMaxS));
+  int rc;
+  if ((rc = join_in(h))) return rc;
+  cudaStream_t st = h->stream;
+  CK(cudaMemcpyAsync(dc.p, coef, sizeof(coef), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(Y, p, h->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(Y + ldy, r, h->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  LevelCoef lc{dc.p, dc.p + kMaxS, dc.p + 2 * kMaxS};
+  for (int l = 0; l < s; ++l) CK(launch_mpk_level(h->op, Y, ldy, l, nullptr, s, lc, false, st));
+  CK(cudaStreamSynchronize(st));
+  if ((rc = join_out(h))) return rc;
+  dc.release();
+  return SSCG_OK;
+}
+
+int sscg_gram(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, void* cuda_stream) {
+  if (!Y || !G || n <= 0 || ldy < n || ncols < 1 || ncols > kMaxCols) return SSCG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int nb = gram_blocks(n);
+  DevBuf<double> part;
+  CK(part.ensure((size_t)nb * kMaxPairs));
+  CK(launch_gram(Y, n, ldy, nullptr, ncols, nullptr, part.p, nb, G, ncols, false, st));
+  CK(cudaStreamSynchronize(st));
+  part.release();
+  return SSCG_OK;
+}
+
+int sscg_kappa(const double* G, int ldg, int sbar, double kappa_cut, double* kappa, double* lmin, double* lmax,
+               void* cuda_stream) {
+  if (!G || !kappa || !lmin || !lmax || sbar < 1 || sbar > kMaxS || ldg < 2 * sbar + 1) return SSCG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(launch_kappa(G, ldg, nullptr, sbar, kappa_cut, kappa, lmin, lmax, sbar, st));
+  CK(cudaStreamSynchronize(st));
+  return SSCG_OK;
+}
+
+int sscg_stencil_face_grad(sscg_t h, const double* lam, const double* x, double* gkx, double* gky, double* gkz) {
+  if (!h || !lam || !x || !gkx || !gky || h->op.kind != 1 || (h->op.dim == 3 && !gkz)) return SSCG_ERR_INVALID_ARG;
+  int rc;
+  if ((rc = join_in(h))) return rc;
+  CK(launch_face_grad(h->op, lam, x, gkx, gky, gkz, h->stream));
+  if ((rc = join_out(h))) return rc;
+  return SSCG_OK;
+}
+
+int sscg_csr_value_grad(sscg_t h, const double* lam, const double* x, double* gval) {
+  if (!h || !lam || !x || !gval || h->op.kind != 0) return SSCG_ERR_INVALID_ARG;
+  int rc;
+  if ((rc = join_in(h))) return rc;
+  CK(launch_csr_grad(h->op, lam, x, gval, h->stream));
+  if ((rc = join_out(h))) return rc;
+  return SSCG_OK;
+}
+
+int sscg_leja(int s, double* t) {
+  if (!t || s < 1 || s > kMaxS) return SSCG_ERR_INVALID_ARG;
+  DevBuf<double> d;
+  CK(d.ensure(kMaxS));
+  CK(launch_leja(d.p, s, nullptr));
+  CK(cudaMemcpy(t, d.p, s * sizeof(double), cudaMemcpyDeviceToHost));
+  d.release();
+  return SSCG_OK;
+}
+
+}  // extern "C"

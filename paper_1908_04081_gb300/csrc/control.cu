@@ -1,0 +1,593 @@
+// Device-side control of Algorithm 5 (Carson 2019, Sections 3-4): the basis
+// condition estimates, the choice of s-tilde, the coordinate-space CG steps,
+// the Meurant-Tichy Ritz estimates (Algorithms 3-4), the error/residual ratio
+// c (eq. xiupd), the break test (eq. newcondy) and the next basis parameters
+// (eqs. newtbasis, chebbasis).  Everything is O(s^3) scalar work on tiny
+// matrices, done by single blocks so the host never waits inside a solve.
+//
+// This file is compiled with FMA contraction disabled: its scalar formulas are
+// evaluated operation by operation in the order they are written, so equal
+// inputs give equal decisions on any IEEE binary64 implementation.
+#include <math.h>
+
+#include "sscg_internal.cuh"
+
+namespace sscg {
+
+namespace {
+
+constexpr int kKappaThreads = 128;
+constexpr int kControlThreads = 128;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ kappa
+// Number of eigenvalues of the symmetric tridiagonal (d, e2 = squared
+// off-diagonals) that are smaller than x: sign changes of the Sturm sequence
+// p_0 = 1, p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2}.  Division free; an
+// exact zero p_i is replaced by a tiny value of the opposite sign of p_{i-1}.
+__device__ int sturm_count(const double* d, const double* e2, int n, double x) {
+  double pm = 1.0;
+  double p = d[0] - x;
+  if (p == 0.0) p = -1e-300;
+  int cnt = p < 0.0 ? 1 : 0;
+  for (int i = 1; i < n; ++i) {
+    double q = (d[i] - x) * p - e2[i - 1] * pm;
+    if (q == 0.0) q = p < 0.0 ? 1e-300 : -1e-300;
+    cnt += ((q < 0.0) != (p < 0.0)) ? 1 : 0;
+    // keep the sequence in range (both terms by the same power of two)
+    const int ex = (int)((__double_as_longlong(q) >> 52) & 0x7ff);
+    if (ex > 1023 + 600 || ex < 1023 - 600) {
+      const double sc = ex > 1023 ? 0x1p-600 : 0x1p600;
+      q *= sc;
+      p *= sc;
+    }
+    pm = p;
+    p = q;
+  }
+  return cnt;
+}
+
+// Multisection by one warp: 32 points per round in (lo, hi).  `target` is the
+// count threshold: the result is the point where count(x) first reaches it.
+__device__ double warp_multisection(const double* d, const double* e2, int n, double lo, double hi, int target) {
+  const int lane = threadIdx.x & 31;
+  for (int round = 0; round < 16; ++round) {
+    const double step = (hi - lo) * (1.0 / 33.0);
+    const double x = lo + step * (double)(lane + 1);
+    const int c = sturm_count(d, e2, n, x);
+    const unsigned ball = __ballot_sync(0xffffffffu, c >= target);
+    const int f = ball ? __ffs(ball) - 1 : 32;
+    const double xf = __shfl_sync(0xffffffffu, x, f & 31);
+    const double xfm = __shfl_sync(0xffffffffu, x, (f - 1) & 31);
+    const double nlo = f == 0 ? lo : xfm;
+    const double nhi = f == 32 ? hi : xf;
+    lo = nlo;
+    hi = nhi;
+    if (hi - lo <= 0x1p-56) break;  // absolute, on the normalised matrix
+  }
+  return 0.5 * (lo + hi);
+}
+
+// One block per l = 1..sbar: Householder tridiagonalisation of the leading
+// (2l+1) block of G, then its extreme eigenvalues by multisection;
+// kappa_l = sqrt(lmax/lmin) (Section 3: kappa(Y_l) ~ sqrt(kappa(G_l))).
+__global__ void __launch_bounds__(kKappaThreads) kappa_kernel(const double* __restrict__ G, int ldg,
+                                                              const SolveState* __restrict__ st, int sbar_fixed,
+                                                              double kappa_cut, double* __restrict__ kap,
+                                                              double* __restrict__ lmin_out,
+                                                              double* __restrict__ lmax_out) {
+  int sbar = sbar_fixed;
+  if (sbar <= 0) {
+    if (st->done) return;
+    sbar = st->sbar;
+    kappa_cut = st->kappa_cut;
+  }
+  const int l = blockIdx.x + 1;
+  if (l > sbar) return;
+  const int n = 2 * l + 1;
+  const int t = threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+
+  __shared__ double A[kMaxCols][kMaxCols + 1];
+  __shared__ double v[kMaxCols], p[kMaxCols], w[kMaxCols];
+  __shared__ double dd[kMaxCols], ee[kMaxCols], e2[kMaxCols];
+  __shared__ double sh[4];
+
+  for (int e = t; e < n * n; e += kKappaThreads) {
+    const int i = e / n, j = e - (e / n) * n;
+    A[i][j] = G[i * ldg + j];
+  }
+  __syncthreads();
+
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;  // trailing block rows k+1..n-1
+    if (warp == 0) {
+      const double xi = lane < m ? A[k + 1 + lane][k] : 0.0;
+      const double all = warp_sum(xi * xi);
+      const double rest = warp_sum(lane >= 1 && lane < m ? xi * xi : 0.0);
+      if (lane == 0) {
+        sh[0] = all;
+        sh[1] = rest;
+      }
+    }
+    __syncthreads();
+    const double sig2 = sh[0], rest = sh[1];
+    const double x0 = A[k + 1][k];
+    if (rest == 0.0) {  // already tridiagonal in this column
+      if (t == 0) {
+        dd[k] = A[k][k];
+        ee[k] = x0;
+      }
+      __syncthreads();
+      continue;
+    }
+    const double alpha = x0 >= 0.0 ? -sqrt(sig2) : sqrt(sig2);
+    const double v0 = x0 - alpha;
+    const double tau = 2.0 / (rest + v0 * v0);
+    if (t < m) v[t] = t == 0 ? v0 : A[k + 1 + t][k];
+    __syncthreads();
+    // p = tau * A_sub v, four threads per row (m <= 32: one pass, all lanes shuffle)
+    {
+      const int i = t >> 2;
+      double s = 0.0;
+      if (i < m)
+        for (int j = t & 3; j < m; j += 4) s += A[k + 1 + i][k + 1 + j] * v[j];
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      if (i < m && (t & 3) == 0) p[i] = tau * s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const double pv = warp_sum(lane < m ? p[lane] * v[lane] : 0.0);
+      if (lane == 0) sh[2] = 0.5 * tau * pv;
+    }
+    __syncthreads();
+    const double K = sh[2];
+    if (t < m) w[t] = p[t] - K * v[t];
+    __syncthreads();
+    // A_sub -= v w^T + w v^T on the lower triangle, mirrored to the upper one
+    for (int e = t; e < m * (m + 1) / 2; e += kKappaThreads) {
+      int i = 0, rem = e;
+      while (rem > i) {
+        rem -= i + 1;
+        ++i;
+      }
+      const int j = rem;
+      const double val = A[k + 1 + i][k + 1 + j] - (v[i] * w[j] + w[i] * v[j]);
+      A[k + 1 + i][k + 1 + j] = val;
+      A[k + 1 + j][k + 1 + i] = val;
+    }
+    if (t == 0) {
+      dd[k] = A[k][k];
+      ee[k] = alpha;
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    dd[n - 2] = A[n - 2][n - 2];
+    dd[n - 1] = A[n - 1][n - 1];
+    ee[n - 2] = A[n - 1][n - 2];
+  }
+  __syncthreads();
+
+  // normalise by a power of two near the Gershgorin bound (exact scaling)
+  __shared__ double glo, ghi;
+  __shared__ int sc_exp;
+  if (t == 0) {
+    double lo = 1e308, hi = -1e308;
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i < n - 1 ? fabs(ee[i]) : 0.0);
+      lo = fmin(lo, dd[i] - r);
+      hi = fmax(hi, dd[i] + r);
+    }
+    const double mag = fmax(fabs(lo), fabs(hi));
+    int ex = mag > 0.0 ? (int)((__double_as_longlong(mag) >> 52) & 0x7ff) - 1023 : 0;
+    sc_exp = ex;
+    const double sc = ldexp(1.0, -ex);
+    glo = lo * sc;
+    ghi = hi * sc;
+  }
+  __syncthreads();
+  const double sc = ldexp(1.0, -sc_exp);
+  if (t < n) {
+    dd[t] = dd[t] * sc;
+    if (t < n - 1) {
+      const double es = ee[t] * sc;
+      e2[t] = es * es;
+    }
+  }
+  __syncthreads();
+  const double lo0 = glo - 0x1p-50, hi0 = ghi + 0x1p-50;
+  __shared__ double ev[2];
+  if (warp == 0) {
+    const double r = warp_multisection(dd, e2, n, lo0, hi0, 1);
+    if (lane == 0) ev[0] = r;
+  } else if (warp == 1) {
+    const double r = warp_multisection(dd, e2, n, lo0, hi0, n);
+    if (lane == 0) ev[1] = r;
+  }
+  __syncthreads();
+  if (t == 0) {
+    const double lmn = ldexp(ev[0], sc_exp), lmx = ldexp(ev[1], sc_exp);
+    lmin_out[l] = lmn;
+    lmax_out[l] = lmx;
+    kap[l] = (!(lmx > 0.0) || lmn <= kappa_cut * lmx) ? INFINITY : sqrt(lmx / lmn);
+  }
+}
+
+// --------------------------------------------------------------- control
+// (B p)_i for the interleaved B of eq. (B): A P_l = gamma_l P_{l+1} + theta_l P_l
+// + mu_{l-1} P_{l-1} for l < s (P chain) and l < s-1 (R chain); the last P and
+// the last R column of B are zero.
+__device__ __forceinline__ double b_times(const double* pc, int i, int s, const double* th, const double* ga,
+                                          const double* mu) {
+  const int chain = i & 1;           // 0: P, 1: R
+  const int l = i >> 1;              // index within the chain
+  const int len = chain ? s : s + 1; // number of columns of the chain
+  double acc = 0.0;
+  if (l >= 1) acc += ga[l - 1] * pc[i - 2];                       // gamma_{l-1} from column l-1
+  if (l < len - 1) acc += th[l] * pc[i];                          // diagonal theta_l
+  if (l + 1 < len - 1) acc += mu[l] * pc[i + 2];                  // mu_l from column l+1
+  return acc;
+}
+
+// y = G x over the leading n x n block (G in shared memory, 4 threads per row,
+// row passes uniform across the block so every lane joins the shuffles);
+// returns w^T y to thread 0 (other threads get 0).
+__device__ double gmv_dot(const double (*Gs)[kMaxCols + 1], const double* x, const double* w, double* y, int n,
+                          double* red) {
+  const int t = threadIdx.x;
+  double part = 0.0;
+  for (int base = 0; base < n; base += kControlThreads / 4) {
+    const int i = base + (t >> 2);
+    double s = 0.0;
+    if (i < n)
+      for (int j = t & 3; j < n; j += 4) s += Gs[i][j] * x[j];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (i < n && (t & 3) == 0) {
+      y[i] = s;
+      part += w[i] * s;
+    }
+  }
+  part = warp_sum(part);
+  if ((t & 31) == 0) red[t >> 5] = part;
+  __syncthreads();
+  double q = 0.0;
+  if (t == 0) q = ((red[0] + red[1]) + red[2]) + red[3];
+  __syncthreads();
+  return q;
+}
+
+__device__ __forceinline__ double clamp01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
+
+// Algorithms 3-4 fed with alpha_i and beta_{i-1} (thread 0 only).
+__device__ void ritz_push(SolveState* st, double alpha, double beta_prev) {
+  const double zeta = 1.0 / sqrt(alpha);
+  if (st->mt_n == 0) {
+    st->up_omega = zeta * zeta;
+    st->up_h = 1.0;
+    st->lo_omega = 1.0 / (zeta * zeta);
+    st->lo_a = st->lo_omega;
+    st->lo_d = 0.0;
+    st->lo_g = 0.0;
+    st->lo_h = 1.0;
+    st->lmax = st->up_omega;
+    st->lmin = 1.0 / st->lo_omega;
+  } else {
+    const double zl = st->zeta_prev, zl1 = zeta;
+    const double eta = sqrt(beta_prev / st->alpha_prev);
+    // Algorithm 3 (xi read as zeta)
+    {
+      const double d = zl * zl * eta * eta * st->up_h;
+      const double a = eta * eta + zl1 * zl1;
+      const double dm = st->up_omega - a;
+      const double chi = sqrt(dm * dm + 4.0 * d);
+      if (chi == 0.0) {
+        st->up_h = 1.0;
+      } else {
+        st->up_h = clamp01(0.5 * (1.0 - (st->up_omega - a) / chi));
+        st->up_omega = st->up_omega + chi * st->up_h;
+      }
+    }
+    // Algorithm 4
+    {
+      const double d1 = -(eta / zl1) * (st->lo_g * st->lo_d + st->lo_h * st->lo_a);
+      const double a1 = (eta * eta * st->lo_a + 1.0) / (zl1 * zl1);
+      const double dm = st->lo_omega - a1;
+      const double chi = sqrt(dm * dm + 4.0 * d1 * d1);
+      double h, g;
+      if (chi == 0.0) {
+        h = 1.0;
+        g = 0.0;
+      } else {
+        const double h2 = clamp01(0.5 * (1.0 - (st->lo_omega - a1) / chi));
+        st->lo_omega = st->lo_omega + chi * h2;
+        h = sqrt(h2);
+        g = sqrt(clamp01(1.0 - h2));
+      }
+      st->lo_h = fabs(h) * (d1 < 0.0 ? -1.0 : 1.0);
+      st->lo_g = g;
+      st->lo_d = d1;
+      st->lo_a = a1;
+    }
+    st->lmax = st->up_omega;
+    st->lmin = 1.0 / st->lo_omega;
+  }
+  st->zeta_prev = zeta;
+  st->alpha_prev = alpha;
+  st->mt_n += 1;
+}
+
+__device__ double c_value(int mode, double lmin, double lmax, double psi, double c_const) {
+  switch (mode) {
+    case SSCG_C_XI: return fmax(1.0, lmax * sqrt(psi / lmin));
+    case SSCG_C_XI_SCALED: return fmax(1.0, lmax * sqrt(psi) / lmin);
+    case SSCG_C_ONE: return 1.0;
+    case SSCG_C_KAPPA_RATIO: return lmax / lmin;
+    default: return c_const;
+  }
+}
+
+// Recurrence coefficients for the next outer loops from the Ritz estimates.
+__device__ void basis_update(SolveState* st, const double* leja) {
+  const double lmin = st->lmin, lmax = st->lmax;
+  const double c = 0.5 * (lmax + lmin);
+  const double h = 0.5 * (lmax - lmin);
+  for (int l = 0; l < st->sigma; ++l) {
+    double th = 0.0, ga = 1.0, mu = 0.0;
+    if (st->basis == SSCG_NEWTON) {
+      th = c + h * leja[l];
+      ga = st->newton_scale == 0 ? (lmax - lmin) / 4.0 : 1.0;
+    } else if (st->basis == SSCG_CHEBYSHEV) {
+      th = c;
+      if (st->cheb_params == 0) {
+        ga = l == 0 ? h : 0.5 * h;
+        mu = 0.5 * h;
+      } else {
+        ga = l == 0 ? lmax - lmin : 0.5 * (lmax - lmin);
+        mu = 2.0 * (lmax - lmin);
+      }
+    }
+    st->theta[l] = th;
+    st->gamma[l] = ga;
+    st->inv_gamma[l] = 1.0 / ga;
+    st->mu[l] = mu;
+  }
+}
+
+__global__ void __launch_bounds__(kControlThreads) control_kernel(SolveState* __restrict__ st,
+                                                                  const double* __restrict__ G, int ldg,
+                                                                  const double* __restrict__ leja,
+                                                                  sscg_outer_record* __restrict__ hist) {
+  if (st->done) return;
+  const int t = threadIdx.x;
+  __shared__ double Gs[kMaxCols][kMaxCols + 1];
+  __shared__ double xc[kMaxCols], rc[kMaxCols], pc[kMaxCols], bp[kMaxCols], u[kMaxCols];
+  __shared__ double th[kMaxS], ga[kMaxS], mu[kMaxS];
+  __shared__ double red[4];
+  __shared__ int s_stilde, s_flag;
+  __shared__ double s_alpha, s_beta;
+
+  const int sbar = st->sbar;
+  if (t == 0) {
+    int stl = 1;
+    if (st->variant == 1) {
+      stl = sbar;
+    } else {
+      const double normr = sqrt(G[1 * ldg + 1]);
+      const double thr = st->tol / (st->c * st->eps * normr / st->normb);
+      for (int l = 1; l <= sbar; ++l)
+        if (st->kappa[l] <= thr) stl = l;
+    }
+    s_stilde = stl;
+  }
+  if (t < kMaxS) {
+    th[t] = st->theta[t];
+    ga[t] = st->gamma[t];
+    mu[t] = st->mu[t];
+  }
+  __syncthreads();
+  const int stl = s_stilde;
+  const int n = 2 * stl + 1;
+  for (int e = t; e < n * n; e += kControlThreads) {
+    const int i = e / n, j = e - (e / n) * n;
+    Gs[i][j] = G[i * ldg + j];
+  }
+  if (t < kMaxCols) {
+    xc[t] = 0.0;
+    rc[t] = t == 1 ? 1.0 : 0.0;
+    pc[t] = t == 0 ? 1.0 : 0.0;
+  }
+  __syncthreads();
+
+  // thread-0 scalars of the inner loop
+  double rr = Gs[1][1];
+  double phi = sqrt(rr > 0.0 ? rr : 0.0);
+  const double c_start = st->c;
+  int sk = 0;
+  int conv = 0, breakdown = 0;
+  const int m0 = st->m;
+
+  for (int j = 0; j < stl; ++j) {
+    if (t < n) bp[t] = b_times(pc, t, stl, th, ga, mu);
+    __syncthreads();
+    const double pGBp = gmv_dot(Gs, bp, pc, u, n, red);  // p'^T G (B p')
+    if (t == 0) {
+      const double alpha = pGBp > 0.0 ? rr / pGBp : NAN;
+      s_flag = 0;
+      if (!(alpha > 0.0) || !isfinite(alpha)) {
+        s_flag = 1;
+        if (j == 0) breakdown = 1;
+      }
+      s_alpha = alpha;
+    }
+    __syncthreads();
+    if (s_flag) break;
+    const double alpha = s_alpha;
+    if (t < n) {
+      xc[t] = xc[t] + alpha * pc[t];
+      rc[t] = rc[t] - alpha * bp[t];
+    }
+    __syncthreads();
+    const double rr_new = gmv_dot(Gs, rc, rc, u, n, red);
+    if (t == 0) {
+      sk = j + 1;
+      s_flag = 0;
+      if (!(rr_new > 0.0) || !isfinite(rr_new)) {
+        conv = 1;
+        s_flag = 1;
+      } else {
+        const double beta = rr_new / rr;
+        s_beta = beta;
+        phi = fmax(phi, sqrt(rr_new));
+        st->psi = st->psi / (st->psi + beta);
+        ritz_push(st, alpha, st->beta_prev);
+        st->beta_prev = beta;
+        if (m0 + j + 1 > 1) st->c = c_value(st->c_mode, st->lmin, st->lmax, st->psi, st->c_const);
+        rr = rr_new;
+        if (st->inner_conv_check && sqrt(rr_new) / st->normb <= st->tol) {
+          conv = 1;
+          s_flag = 2;
+        } else if (st->variant != 1 && j < stl - 1 &&
+                   st->kappa[j + 2] >= st->tol / (st->c * st->eps * phi / st->normb)) {
+          s_flag = 2;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_flag == 1) break;
+    const double beta = s_beta;
+    if (t < n) pc[t] = rc[t] + beta * pc[t];
+    __syncthreads();
+    if (s_flag == 2) break;
+  }
+  __syncthreads();
+
+  if (t == 0) {
+    const int k = st->k;
+    if (breakdown) {
+      st->status = SSCG_BREAKDOWN;
+      st->done = 1;
+      st->nc = 0;
+    } else {
+      // outer-level convergence test when the per-step test is off (reading C15)
+      if (!conv && !st->inner_conv_check && sqrt(rr > 0.0 ? rr : 0.0) / st->normb <= st->tol) conv = 1;
+      st->stilde = stl;
+      st->sk = sk;
+      st->nc = 2 * sk + 1;
+      st->m = m0 + sk;
+      st->converged_est = conv;
+      st->upd_relres = sqrt(rr > 0.0 ? rr : 0.0) / st->normb;
+      if (st->m > 1 && st->basis != SSCG_MONOMIAL) {
+        basis_update(st, leja);
+        st->have_ritz = 1;
+      }
+      int nsb = sk + st->f;
+      st->sbar = nsb < st->sigma ? nsb : st->sigma;
+    }
+    if (hist != nullptr && k < st->hist_cap) {
+      sscg_outer_record& h = hist[k];
+      h.sbar = sbar;
+      h.stilde = stl;
+      h.sk = breakdown ? 0 : sk;
+      h.replaced = 0;
+      h.c_start = c_start;
+      h.c_end = st->c;
+      h.phi = phi;
+      h.lmin = st->lmin;
+      h.lmax = st->lmax;
+      h.relres_est = st->upd_relres;
+      for (int l = 0; l <= kMaxS; ++l) h.kappa[l] = (l >= 1 && l <= sbar) ? st->kappa[l] : 0.0;
+    }
+    st->k = k + 1;
+  }
+  if (t < kMaxCols) {
+    st->xc[t] = t < n ? xc[t] : 0.0;
+    st->rc[t] = t < n ? rc[t] : 0.0;
+    st->pc[t] = t < n ? pc[t] : 0.0;
+  }
+}
+
+// ------------------------------------------------------------------ Leja
+// Leja points of [-1, 1] (eq. newtbasis on the reference interval): t_0 = 1,
+// t_1 = -1, then the maximiser of prod |t - t_m|.  In each gap between sorted
+// points the log-product is concave, so its maximiser is the zero of the
+// derivative sum 1/(t - t_m), found by bisection to the last bit; the gap with
+// the largest product wins, ties (within 1e-13 in log) go to the smaller t.
+__global__ void leja_kernel(double* out, int s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double pts[kMaxS];
+  double srt[kMaxS];
+  int np = 0;
+  if (s >= 1) pts[np++] = 1.0;
+  if (s >= 2) pts[np++] = -1.0;
+  while (np < s) {
+    for (int i = 0; i < np; ++i) srt[i] = pts[i];
+    for (int i = 1; i < np; ++i) {  // insertion sort, ascending
+      double key = srt[i];
+      int j = i - 1;
+      while (j >= 0 && srt[j] > key) {
+        srt[j + 1] = srt[j];
+        --j;
+      }
+      srt[j + 1] = key;
+    }
+    double best_t = 0.0, best_v = -INFINITY;
+    bool have = false;
+    for (int g = 0; g + 1 < np; ++g) {
+      double lo = srt[g], hi = srt[g + 1];
+      while (true) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double dv = 0.0;
+        for (int i = 0; i < np; ++i) dv = dv + 1.0 / (mid - pts[i]);
+        if (dv == 0.0) {
+          lo = hi = mid;
+          break;
+        }
+        if (dv > 0.0) lo = mid;
+        else hi = mid;
+      }
+      const double tt = 0.5 * (lo + hi);
+      double v = 0.0;
+      for (int i = 0; i < np; ++i) v = v + log(fabs(tt - pts[i]));
+      if (!have || v > best_v + 1e-13) {
+        best_t = tt;
+        best_v = v;
+        have = true;
+      } else if (fabs(v - best_v) <= 1e-13 && tt < best_t) {
+        best_t = tt;
+        best_v = fmax(v, best_v);
+      }
+    }
+    pts[np++] = best_t;
+  }
+  for (int i = 0; i < s; ++i) out[i] = pts[i];
+}
+
+}  // namespace
+
+cudaError_t launch_kappa(const double* G, int ldg, const SolveState* state, int sbar_fixed, double kappa_cut,
+                         double* kappa, double* lmin, double* lmax, int grid, cudaStream_t st) {
+  kappa_kernel<<<grid, kKappaThreads, 0, st>>>(G, ldg, state, sbar_fixed, kappa_cut, kappa, lmin, lmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_control(SolveState* state, const double* G, int ldg, const double* leja,
+                           sscg_outer_record* hist, cudaStream_t st) {
+  control_kernel<<<1, kControlThreads, 0, st>>>(state, G, ldg, leja, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leja(double* t, int s, cudaStream_t st) {
+  leja_kernel<<<1, 32, 0, st>>>(t, s);
+  return cudaGetLastError();
+}
+
+}  // namespace sscg

@@ -1,0 +1,128 @@
+// Gram matrix G = Y^T Y of the s-step basis (Carson 2019, Section 2: the one
+// block inner product per outer loop of Algorithm 5, computed once and kept on
+// the device).
+//
+// Design for GB300: a tall-skinny contraction (n rows, at most 33 columns)
+// that is bound by FP64 issue rate (561 DFMA per row at s = 16 against 264
+// bytes per row), so the kernel gives every lane one unique (i <= j) entry of
+// G and streams row tiles of Y through shared memory: each DFMA needs two
+// shared loads and nothing else.  When fewer pairs than threads exist, the
+// spare threads take interleaved rows of the same tile (row lanes) so that all
+// lanes issue DFMAs.  Rows are split into contiguous chunks per block; each
+// block writes one partial sum per pair, and a second kernel adds the partials
+// of every pair in a fixed order, so G is bitwise reproducible run to run.
+#include "sscg_internal.cuh"
+
+namespace sscg {
+
+namespace {
+
+__device__ __forceinline__ void pair_of(int q, int ncols, int* pi, int* pj) {
+  int i = 0, rem = q;
+  while (rem >= ncols - i) {
+    rem -= ncols - i;
+    ++i;
+  }
+  *pi = i;
+  *pj = i + rem;
+}
+
+__global__ void __launch_bounds__(kGramThreads, 2)
+gram_partial_kernel(const double* __restrict__ Y, int64_t n, int64_t ld, const SolveState* __restrict__ st,
+                    int ncols_fixed, double* __restrict__ partials) {
+  int ncols = ncols_fixed;
+  if (ncols <= 0) {
+    if (st->done) return;
+    ncols = 2 * st->sbar + 1;
+  }
+  const int np = ncols * (ncols + 1) / 2;
+  const int R = kGramThreads / np;  // row lanes, >= 1
+  const int t = threadIdx.x;
+  const bool active = t < R * np;
+  const int q = t % np;
+  const int rl = t / np;
+  int pi = 0, pj = 0;
+  pair_of(q, ncols, &pi, &pj);
+
+  __shared__ double tile[kGramTileRows][kMaxCols + 1];
+  __shared__ double red[kGramThreads];
+
+  // contiguous row chunk of this block, a multiple of the tile height
+  const int64_t tiles = (n + kGramTileRows - 1) / kGramTileRows;
+  const int64_t tpb = (tiles + gridDim.x - 1) / gridDim.x;
+  const int64_t r_begin = (int64_t)blockIdx.x * tpb * kGramTileRows;
+  int64_t r_end = r_begin + tpb * kGramTileRows;
+  if (r_end > n) r_end = n;
+
+  double acc = 0.0;
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kGramTileRows) {
+    for (int e = t; e < kGramTileRows * ncols; e += kGramThreads) {
+      const int c = e / kGramTileRows;
+      const int r = e - c * kGramTileRows;
+      const int64_t row = r0 + r;
+      tile[r][c] = row < r_end ? __ldg(Y + (int64_t)c * ld + row) : 0.0;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 8
+      for (int r = rl; r < kGramTileRows; r += R) acc = fma(tile[r][pi], tile[r][pj], acc);
+    }
+    __syncthreads();
+  }
+  red[t] = acc;
+  __syncthreads();
+  if (t < np) {
+    double s = 0.0;
+    for (int l = 0; l < R; ++l) s += red[l * np + t];
+    partials[(int64_t)blockIdx.x * kMaxPairs + t] = s;
+  }
+}
+
+// One warp per pair: fixed-order sum of the per-block partials.
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restrict__ partials, int nblocks,
+                                                          const SolveState* __restrict__ st, int ncols_fixed,
+                                                          double* __restrict__ G, int ldg) {
+  int ncols = ncols_fixed;
+  if (ncols <= 0) {
+    if (st->done) return;
+    ncols = 2 * st->sbar + 1;
+  }
+  const int np = ncols * (ncols + 1) / 2;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= np) return;
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += 32) s += partials[(int64_t)b * kMaxPairs + warp];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    int i, j;
+    pair_of(warp, ncols, &i, &j);
+    G[i * ldg + j] = s;
+    G[j * ldg + i] = s;
+  }
+}
+
+}  // namespace
+
+int gram_blocks(int64_t n) {
+  int64_t tiles = (n + kGramTileRows - 1) / kGramTileRows;
+  int64_t b = 152 * 2;
+  if (tiles < b) b = tiles;
+  return b < 1 ? 1 : (int)b;
+}
+
+cudaError_t launch_gram(const double* Y, int64_t n, int64_t ld, const int* /*ncols_dev*/, int ncols_fixed,
+                        const SolveState* state, double* partials, int nblocks, double* G, int ldg, bool y32,
+                        cudaStream_t st) {
+  if (y32) return cudaErrorNotSupported;
+  gram_partial_kernel<<<nblocks, kGramThreads, 0, st>>>(Y, n, ld, state, ncols_fixed, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int warps_per_block = 256 / 32;
+  gram_reduce_kernel<<<(kMaxPairs + warps_per_block - 1) / warps_per_block, 256, 0, st>>>(
+      partials, nblocks, state, ncols_fixed, G, ldg);
+  return cudaGetLastError();
+}
+
+}  // namespace sscg

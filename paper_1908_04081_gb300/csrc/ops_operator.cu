@@ -1,0 +1,272 @@
+// Sparse operator kernels: SpMV, residual and one matrix-powers level, for the
+// face-coefficient stencil and for CSR.
+//
+// The matrix-powers level implements the three-term recurrence of Carson 2019,
+// eq. (rho), for both chains of eq. (cg-krylovbasis) in one pass over A:
+//   P_{l+1} = ((A - theta_l I) P_l - mu_{l-1} P_{l-1}) / gamma_l   (l < s-bar)
+//   R_{l+1} = ((A - theta_l I) R_l - mu_{l-1} R_{l-1}) / gamma_l   (l + 1 < s-bar)
+// so the coefficients of A are read once per level for both chains.  On GB300
+// these kernels are bound by FP64 issue rate (2 DFMA/clk/SM), not by HBM, so
+// they minimise FP64 instructions: theta is folded into the diagonal once per
+// cell and shared by both chains, 1/gamma is a precomputed multiplier, and the
+// mu term is skipped (uniform branch) when mu = 0.  Every lane of a warp does
+// the same FP64 work (boundary neighbours read as 0 by predication), because
+// masked lanes do not free FP64 issue slots.
+#include "sscg_internal.cuh"
+
+namespace sscg {
+
+namespace {
+
+constexpr int kOpThreads = 256;
+
+__host__ __device__ inline int grid_for(int64_t n, int per_thread) {
+  int64_t g = (n + (int64_t)kOpThreads * per_thread - 1) / ((int64_t)kOpThreads * per_thread);
+  if (g < 1) g = 1;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)g;
+}
+
+template <typename T>
+__device__ __forceinline__ double ld_val(const T* p) { return (double)__ldg(p); }
+
+// (A - shift I) v at cell i of a stencil, v read through `vp` (stride-1 vector).
+// Coordinates (x, y, z) of cell i; boundary neighbours contribute 0.
+template <bool DIM3, typename T>
+__device__ __forceinline__ double stencil_apply(const Operator& A, const T* __restrict__ v, int64_t i,
+                                                int x, int y, int z, double dshift) {
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t fx = ((int64_t)z * ny + y) * (nx + 1) + x;
+  const int64_t fy = ((int64_t)z * (ny + 1) + y) * nx + x;
+  double vi = ld_val(v + i);
+  double vw = x > 0 ? ld_val(v + i - 1) : 0.0;
+  double ve = x < nx - 1 ? ld_val(v + i + 1) : 0.0;
+  double vs = y > 0 ? ld_val(v + i - nx) : 0.0;
+  double vn = y < ny - 1 ? ld_val(v + i + nx) : 0.0;
+  double acc = dshift * vi;
+  acc = fma(-__ldg(A.kx + fx), vw, acc);
+  acc = fma(-__ldg(A.kx + fx + 1), ve, acc);
+  acc = fma(-__ldg(A.ky + fy), vs, acc);
+  acc = fma(-__ldg(A.ky + fy + nx), vn, acc);
+  if (DIM3) {
+    double vd = z > 0 ? ld_val(v + i - plane) : 0.0;
+    double vu = z < nz - 1 ? ld_val(v + i + plane) : 0.0;
+    acc = fma(-__ldg(A.kz + i), vd, acc);
+    acc = fma(-__ldg(A.kz + i + plane), vu, acc);
+  }
+  return acc;
+}
+
+// Launch gates read from the solve state: 0 = always run, 1 = only when a
+// true-residual check is pending, 2 = only while the iteration is running.
+__device__ __forceinline__ bool gate_closed(const SolveState* g, int mode) {
+  if (mode == 0 || g == nullptr) return false;
+  if (g->done) return true;
+  return mode == 1 ? !g->converged_est : g->converged_est != 0;
+}
+
+template <bool DIM3>
+__global__ void __launch_bounds__(kOpThreads) stencil_spmv_kernel(Operator A, const double* __restrict__ v,
+                                                                  double* __restrict__ y, const SolveState* gate,
+                                                                  int gmode) {
+  if (gate_closed(gate, gmode)) return;
+  const int64_t n = A.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int x = (int)(i % A.nx);
+    int64_t t = i / A.nx;
+    int yy = (int)(t % A.ny);
+    int z = (int)(t / A.ny);
+    y[i] = stencil_apply<DIM3>(A, v, i, x, yy, z, __ldg(A.diag + i));
+  }
+}
+
+template <bool DIM3>
+__global__ void __launch_bounds__(kOpThreads) stencil_residual_kernel(Operator A, const double* __restrict__ b,
+                                                                      const double* __restrict__ xv,
+                                                                      double* __restrict__ r, const SolveState* gate,
+                                                                      int gmode) {
+  if (gate_closed(gate, gmode)) return;
+  const int64_t n = A.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int x = (int)(i % A.nx);
+    int64_t t = i / A.nx;
+    int yy = (int)(t % A.ny);
+    int z = (int)(t / A.ny);
+    r[i] = b[i] - stencil_apply<DIM3>(A, xv, i, x, yy, z, __ldg(A.diag + i));
+  }
+}
+
+// One matrix-powers level for a stencil.  `sbar` is read from the solve state
+// (device) unless sbar_fixed > 0.
+template <bool DIM3>
+__global__ void __launch_bounds__(kOpThreads) stencil_mpk_kernel(Operator A, double* __restrict__ Y, int64_t ld,
+                                                                 int level, const SolveState* __restrict__ st,
+                                                                 int sbar_fixed, LevelCoef coef) {
+  int sbar = sbar_fixed;
+  if (sbar <= 0) {
+    if (st->done) return;
+    sbar = st->sbar;
+  }
+  const bool doP = level < sbar;
+  const bool doR = level + 1 < sbar;
+  if (!doP) return;
+  const double theta = coef.theta[level];
+  const double ig = coef.inv_gamma[level];
+  const double mu = level >= 1 ? coef.mu[level - 1] : 0.0;
+  const double* Pl = Y + (int64_t)(2 * level) * ld;
+  const double* Rl = Y + (int64_t)(2 * level + 1) * ld;
+  const double* Pm = level >= 1 ? Y + (int64_t)(2 * level - 2) * ld : nullptr;
+  const double* Rm = level >= 1 ? Y + (int64_t)(2 * level - 1) * ld : nullptr;
+  double* Pn = Y + (int64_t)(2 * level + 2) * ld;
+  double* Rn = Y + (int64_t)(2 * level + 3) * ld;
+  const int64_t n = A.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int x = (int)(i % A.nx);
+    int64_t t = i / A.nx;
+    int yy = (int)(t % A.ny);
+    int z = (int)(t / A.ny);
+    const double ds = __ldg(A.diag + i) - theta;
+    double wp = stencil_apply<DIM3>(A, Pl, i, x, yy, z, ds);
+    if (mu != 0.0) wp = fma(-mu, __ldg(Pm + i), wp);
+    Pn[i] = wp * ig;
+    if (doR) {
+      double wr = stencil_apply<DIM3>(A, Rl, i, x, yy, z, ds);
+      if (mu != 0.0) wr = fma(-mu, __ldg(Rm + i), wr);
+      Rn[i] = wr * ig;
+    }
+  }
+}
+
+// ------------------------------------------------------------------- CSR
+__global__ void __launch_bounds__(kOpThreads) csr_spmv_kernel(Operator A, const double* __restrict__ v,
+                                                              double* __restrict__ y, const SolveState* gate,
+                                                              int gmode) {
+  if (gate_closed(gate, gmode)) return;
+  const int64_t n = A.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = __ldg(A.rowptr + i), e = __ldg(A.rowptr + i + 1);
+    double acc = 0.0;
+    for (int64_t k = b; k < e; ++k) acc = fma(__ldg(A.val + k), __ldg(v + __ldg(A.col + k)), acc);
+    y[i] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kOpThreads) csr_residual_kernel(Operator A, const double* __restrict__ bvec,
+                                                                  const double* __restrict__ xv,
+                                                                  double* __restrict__ r, const SolveState* gate,
+                                                                  int gmode) {
+  if (gate_closed(gate, gmode)) return;
+  const int64_t n = A.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = __ldg(A.rowptr + i), e = __ldg(A.rowptr + i + 1);
+    double acc = 0.0;
+    for (int64_t k = b; k < e; ++k) acc = fma(__ldg(A.val + k), __ldg(xv + __ldg(A.col + k)), acc);
+    r[i] = bvec[i] - acc;
+  }
+}
+
+__global__ void __launch_bounds__(kOpThreads) csr_mpk_kernel(Operator A, double* __restrict__ Y, int64_t ld,
+                                                             int level, const SolveState* __restrict__ st,
+                                                             int sbar_fixed, LevelCoef coef) {
+  int sbar = sbar_fixed;
+  if (sbar <= 0) {
+    if (st->done) return;
+    sbar = st->sbar;
+  }
+  const bool doP = level < sbar;
+  const bool doR = level + 1 < sbar;
+  if (!doP) return;
+  const double theta = coef.theta[level];
+  const double ig = coef.inv_gamma[level];
+  const double mu = level >= 1 ? coef.mu[level - 1] : 0.0;
+  const double* Pl = Y + (int64_t)(2 * level) * ld;
+  const double* Rl = Y + (int64_t)(2 * level + 1) * ld;
+  const double* Pm = level >= 1 ? Y + (int64_t)(2 * level - 2) * ld : nullptr;
+  const double* Rm = level >= 1 ? Y + (int64_t)(2 * level - 1) * ld : nullptr;
+  double* Pn = Y + (int64_t)(2 * level + 2) * ld;
+  double* Rn = Y + (int64_t)(2 * level + 3) * ld;
+  const int64_t n = A.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = __ldg(A.rowptr + i), e = __ldg(A.rowptr + i + 1);
+    double ap = 0.0, ar = 0.0;
+    if (doR) {
+      for (int64_t k = b; k < e; ++k) {
+        const double a = __ldg(A.val + k);
+        const int c = __ldg(A.col + k);
+        ap = fma(a, __ldg(Pl + c), ap);
+        ar = fma(a, __ldg(Rl + c), ar);
+      }
+    } else {
+      for (int64_t k = b; k < e; ++k) ap = fma(__ldg(A.val + k), __ldg(Pl + __ldg(A.col + k)), ap);
+    }
+    double wp = fma(-theta, __ldg(Pl + i), ap);
+    if (mu != 0.0) wp = fma(-mu, __ldg(Pm + i), wp);
+    Pn[i] = wp * ig;
+    if (doR) {
+      double wr = fma(-theta, __ldg(Rl + i), ar);
+      if (mu != 0.0) wr = fma(-mu, __ldg(Rm + i), wr);
+      Rn[i] = wr * ig;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kOpThreads) stencil_diag_kernel(Operator A, double* __restrict__ diag) {
+  const int64_t n = A.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % A.nx);
+    const int64_t t = i / A.nx;
+    const int y = (int)(t % A.ny);
+    const int z = (int)(t / A.ny);
+    const int64_t fx = ((int64_t)z * A.ny + y) * (A.nx + 1) + x;
+    const int64_t fy = ((int64_t)z * (A.ny + 1) + y) * A.nx + x;
+    double d = A.kx[fx] + A.kx[fx + 1] + A.ky[fy] + A.ky[fy + A.nx];
+    if (A.dim == 3) d += A.kz[i] + A.kz[i + (int64_t)A.nx * A.ny];
+    diag[i] = d;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stencil_diag(const Operator& A, double* diag, cudaStream_t st) {
+  stencil_diag_kernel<<<grid_for(A.n, 4), kOpThreads, 0, st>>>(A, diag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(const Operator& A, const double* v, double* y, cudaStream_t st, const SolveState* gate,
+                        int gmode) {
+  int g = grid_for(A.n, 4);
+  if (A.kind == 0) csr_spmv_kernel<<<g, kOpThreads, 0, st>>>(A, v, y, gate, gmode);
+  else if (A.dim == 3) stencil_spmv_kernel<true><<<g, kOpThreads, 0, st>>>(A, v, y, gate, gmode);
+  else stencil_spmv_kernel<false><<<g, kOpThreads, 0, st>>>(A, v, y, gate, gmode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Operator& A, const double* b, const double* x, double* r, cudaStream_t st,
+                            const SolveState* gate, int gmode) {
+  int g = grid_for(A.n, 4);
+  if (A.kind == 0) csr_residual_kernel<<<g, kOpThreads, 0, st>>>(A, b, x, r, gate, gmode);
+  else if (A.dim == 3) stencil_residual_kernel<true><<<g, kOpThreads, 0, st>>>(A, b, x, r, gate, gmode);
+  else stencil_residual_kernel<false><<<g, kOpThreads, 0, st>>>(A, b, x, r, gate, gmode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mpk_level(const Operator& A, double* Y, int64_t ld, int level, const SolveState* state,
+                             int sbar_fixed, LevelCoef coef, bool y32, cudaStream_t st) {
+  if (y32) return cudaErrorNotSupported;
+  int g = grid_for(A.n, 4);
+  if (A.kind == 0) csr_mpk_kernel<<<g, kOpThreads, 0, st>>>(A, Y, ld, level, state, sbar_fixed, coef);
+  else if (A.dim == 3)
+    stencil_mpk_kernel<true><<<g, kOpThreads, 0, st>>>(A, Y, ld, level, state, sbar_fixed, coef);
+  else stencil_mpk_kernel<false><<<g, kOpThreads, 0, st>>>(A, Y, ld, level, state, sbar_fixed, coef);
+  return cudaGetLastError();
+}
+
+}  // namespace sscg

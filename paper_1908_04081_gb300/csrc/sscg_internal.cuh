@@ -1,0 +1,143 @@
+// Internal declarations shared by the libsscg translation units.
+//
+// Layout of the s-step basis in device memory: Y is column major with leading
+// dimension ld (n rounded up to a multiple of 32), 2*sigma+1 columns, stored in
+// the interleaved order [P_0, R_0, P_1, R_1, ..., P_{s-1}, R_{s-1}, P_s]; column
+// 2l is P_l and column 2l+1 is R_l, so the basis of the first l inner steps is
+// the leading 2l+1 columns (Carson 2019, eq. (reqsub)).  Columns 0 and 1 hold
+// the current p and r between outer loops.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sscg.h"
+
+namespace sscg {
+
+constexpr int kMaxS = SSCG_MAX_S;
+constexpr int kMaxCols = 2 * kMaxS + 1;                    // 33
+constexpr int kMaxPairs = kMaxCols * (kMaxCols + 1) / 2;   // 561
+constexpr int kGramThreads = 576;                          // >= kMaxPairs, multiple of 32
+constexpr int kGramTileRows = 32;
+
+// ---------------------------------------------------------------- operator
+// A sparse SPD operator: a CSR matrix or a 2D/3D face-coefficient stencil.
+struct Operator {
+  int kind;            // 0 = CSR, 1 = stencil
+  int64_t n;
+  // CSR
+  const int64_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  // stencil: cells x fastest; kx [nz][ny][nx+1], ky [nz][ny+1][nx], kz [nz+1][ny][nx]
+  int dim, nx, ny, nz;
+  const double* kx;
+  const double* ky;
+  const double* kz;
+  const double* diag;  // sum of the faces of each cell (the diagonal of A)
+};
+
+// ------------------------------------------------------------ solver state
+// Device-resident state of one s-step solve (Algorithm 5).  Only kernels read
+// and write it during a solve; the host reads `done`/`status` to stop.
+struct SolveState {
+  // configuration
+  int sigma, s0, f, basis, c_mode, newton_scale, cheb_params, inner_conv_check, variant;
+  int max_outer, y_fp32, hist_cap;
+  double tol, eps, kappa_cut, c_const;
+  // running scalars
+  int k;              // outer loop index (0-based) of the loop in progress
+  int m;              // inner iterations done (global index of the next alpha)
+  int sbar;           // s-bar_k of the loop in progress
+  int stilde, sk;     // s-tilde_k, s_k of the last finished control step
+  int done, status;
+  int converged_est;  // coordinate estimate <= tol: a true-residual check is pending
+  int replace_pending;
+  int replacements;
+  int have_ritz;      // basis parameters come from Ritz values (m > 1)
+  int zero_rhs;       // b = 0: x = 0 is returned without iterating
+  double c, psi, normb, upd_relres;
+  // Meurant-Tichy state (Algs. 3-4)
+  int mt_n;
+  double up_omega, up_h;
+  double lo_omega, lo_a, lo_d, lo_g, lo_h;
+  double alpha_prev, zeta_prev, beta_prev;
+  double lmin, lmax;
+  // recurrence coefficients of the loop in progress (eq. rho)
+  double theta[kMaxS], gamma[kMaxS], inv_gamma[kMaxS], mu[kMaxS];
+  // control output: coordinates of x - x_m, r, p in the basis (eq. coords)
+  int nc;             // 2 s_k + 1 columns used by the recombination
+  double xc[kMaxCols], rc[kMaxCols], pc[kMaxCols];
+  // kappa step output (entry l = 1..sbar)
+  double kappa[kMaxS + 1], glmin[kMaxS + 1], glmax[kMaxS + 1];
+  // true residual check
+  double rt2;
+  unsigned int red_counter;   // arrival counter of the last-block reductions
+  // HSCG comparator scalars
+  double h_rr, h_pq, h_alpha, h_beta;
+  int h_iters, h_max_iters;
+};
+
+// ----------------------------------------------------------------- launchers
+// operator kernels (ops_stencil.cu / ops_csr.cu)
+// gmode: 0 = always run; 1 = only when a true-residual check is pending
+// (state->converged_est and not done); 2 = only while iterating (not done and
+// no check pending).
+cudaError_t launch_spmv(const Operator& A, const double* v, double* y, cudaStream_t st,
+                        const SolveState* gate = nullptr, int gmode = 0);
+// diag_i = sum of the faces of cell i (the diagonal of a stencil operator)
+cudaError_t launch_stencil_diag(const Operator& A, double* diag, cudaStream_t st);
+// residual r = b - A x, written to r
+cudaError_t launch_residual(const Operator& A, const double* b, const double* x, double* r,
+                            cudaStream_t st, const SolveState* gate = nullptr, int gmode = 0);
+// one matrix-powers level l (computes P_{l+1} and R_{l+1} when within the block size
+// read from st->sbar, or from `sbar_fixed` when > 0, with coefficients from `coef`).
+struct LevelCoef { const double* theta; const double* inv_gamma; const double* mu; };
+cudaError_t launch_mpk_level(const Operator& A, double* Y, int64_t ld, int level,
+                             const SolveState* state, int sbar_fixed, LevelCoef coef, bool y32,
+                             cudaStream_t st);
+
+// gram.cu
+int gram_blocks(int64_t n);
+cudaError_t launch_gram(const double* Y, int64_t n, int64_t ld, const int* ncols_dev, int ncols_fixed,
+                        const SolveState* state, double* partials, int nblocks, double* G, int ldg,
+                        bool y32, cudaStream_t st);
+
+// control.cu
+cudaError_t launch_kappa(const double* G, int ldg, const SolveState* state, int sbar_fixed,
+                         double kappa_cut, double* kappa, double* lmin, double* lmax, int grid,
+                         cudaStream_t st);
+cudaError_t launch_control(SolveState* state, const double* G, int ldg, const double* leja,
+                           sscg_outer_record* hist, cudaStream_t st);
+cudaError_t launch_leja(double* t, int s, cudaStream_t st);
+
+// vec.cu
+cudaError_t launch_recombine(const SolveState* state, double* Y, int64_t ld, double* x, int64_t n,
+                             bool y32, cudaStream_t st);
+cudaError_t launch_init_state(SolveState* state, const Operator& A, const double* b, const double* x,
+                              double* Y, int64_t ld, double* partials, int nblocks, bool y32,
+                              cudaStream_t st);
+cudaError_t launch_true_residual(SolveState* state, const Operator& A, const double* b, const double* x,
+                                 double* rt, double* partials, int nblocks, cudaStream_t st);
+cudaError_t launch_apply_replacement(SolveState* state, const double* rt, double* Y, int64_t ld,
+                                     int64_t n, bool y32, sscg_outer_record* hist, cudaStream_t st);
+cudaError_t launch_final_norm(SolveState* state, const Operator& A, const double* b, const double* x,
+                              double* rt, double* partials, int nblocks, cudaStream_t st);
+// HSCG
+cudaError_t launch_hscg_init(SolveState* state, const Operator& A, const double* b, const double* x,
+                             double* r, double* p, double* partials, int nblocks, cudaStream_t st);
+cudaError_t launch_hscg_iteration(SolveState* state, const Operator& A, double* x, double* r,
+                                  double* p, double* q, double* partials, int nblocks,
+                                  cudaStream_t st);
+cudaError_t launch_hscg_check(SolveState* state, const Operator& A, const double* b, const double* x,
+                              double* r, double* p, double* rt, double* partials, int nblocks,
+                              cudaStream_t st);
+int reduce_blocks(int64_t n);
+
+// adjoint.cu
+cudaError_t launch_face_grad(const Operator& A, const double* lam, const double* x, double* gkx, double* gky,
+                             double* gkz, cudaStream_t st);
+cudaError_t launch_csr_grad(const Operator& A, const double* lam, const double* x, double* gval, cudaStream_t st);
+
+}  // namespace sscg

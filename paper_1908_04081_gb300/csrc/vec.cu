@@ -1,0 +1,409 @@
+// Vector kernels of the solvers: recovery of x, r, p from the basis
+// coordinates (Carson 2019, eq. (coords), Algorithm 5), the initial and true
+// residuals with their norms, residual replacement, and the Hestenes-Stiefel
+// CG comparator (Algorithm 1).
+//
+// Reductions are deterministic: every block writes one partial, and the last
+// block to arrive (atomic ticket) adds the partials in a fixed order.  Each
+// thread first accumulates many rows so the FP64 adds of the reduction tree
+// stay a small fraction of the FP64 work.
+#include <math.h>
+
+#include "sscg_internal.cuh"
+
+namespace sscg {
+
+namespace {
+
+constexpr int kVecThreads = 256;
+
+int vec_grid(int64_t n) {
+  int64_t g = (n + (int64_t)kVecThreads * 8 - 1) / ((int64_t)kVecThreads * 8);
+  if (g < 1) g = 1;
+  if (g > 152 * 4) g = 152 * 4;
+  return (int)g;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum to thread 0 (fixed order).
+__device__ double block_sum(double v) {
+  __shared__ double ws[kVecThreads / 32];
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) ws[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kVecThreads / 32; ++i) s += ws[i];
+  __syncthreads();
+  return s;
+}
+
+// Write the block's partial; returns true (in every thread of the block) if
+// this block is the last one and `*total` holds the fixed-order sum of all
+// partials (valid in thread 0 only).
+__device__ bool last_block_sum(double partial, double* partials, unsigned int* counter, double* total) {
+  __shared__ bool is_last;
+  const double bs = block_sum(partial);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(counter, 1u);
+    is_last = ticket == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kVecThreads) s += __ldcg(partials + b);
+  s = block_sum(s);
+  if (threadIdx.x == 0) {
+    *total = s;
+    *counter = 0u;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------- recovery
+// x += Y x', r = Y r', p = Y p' over the first nc = 2 s_k + 1 columns; the new
+// p and r overwrite columns 0 and 1 of Y (each row reads its own row first).
+__global__ void __launch_bounds__(kVecThreads) recombine_kernel(const SolveState* __restrict__ st,
+                                                                double* __restrict__ Y, int64_t ld,
+                                                                double* __restrict__ x, int64_t n) {
+  if (st->done) return;
+  const int nc = st->nc;
+  __shared__ double cx[kMaxCols], cr[kMaxCols], cp[kMaxCols];
+  if (threadIdx.x < kMaxCols) {
+    cx[threadIdx.x] = st->xc[threadIdx.x];
+    cr[threadIdx.x] = st->rc[threadIdx.x];
+    cp[threadIdx.x] = st->pc[threadIdx.x];
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double sx = 0.0, sr = 0.0, sp = 0.0;
+    for (int c = 0; c < nc; ++c) {
+      const double y = Y[(int64_t)c * ld + i];
+      sx = fma(y, cx[c], sx);
+      sr = fma(y, cr[c], sr);
+      sp = fma(y, cp[c], sp);
+    }
+    x[i] += sx;
+    Y[i] = sp;
+    Y[ld + i] = sr;
+  }
+}
+
+// r0 = b - A x0 into column 1 (and p0 = r0 into column 0) is done by the
+// residual kernel; this kernel copies it and forms ||b||.
+__global__ void __launch_bounds__(kVecThreads) init_norms_kernel(SolveState* __restrict__ st,
+                                                                 const double* __restrict__ b,
+                                                                 double* __restrict__ Y, int64_t ld, int64_t n,
+                                                                 double* __restrict__ partials) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    s = fma(bi, bi, s);
+    Y[i] = Y[ld + i];
+  }
+  double tot;
+  if (last_block_sum(s, partials, &st->red_counter, &tot) && threadIdx.x == 0) {
+    st->normb = sqrt(tot);
+    if (tot == 0.0) {  // b = 0: the solution is x = 0
+      st->zero_rhs = 1;
+      st->done = 1;
+      st->status = SSCG_OK;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) zero_x_kernel(const SolveState* __restrict__ st, double* __restrict__ x,
+                                                             int64_t n) {
+  if (!st->zero_rhs) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = 0.0;
+}
+
+// True residual check after a converged coordinate estimate (reading C16).
+__global__ void __launch_bounds__(kVecThreads) true_norm_kernel(SolveState* __restrict__ st,
+                                                                const double* __restrict__ rt, int64_t n,
+                                                                double* __restrict__ partials, int force) {
+  if (!force && (st->done || !st->converged_est)) return;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = rt[i];
+    s = fma(v, v, s);
+  }
+  double tot;
+  if (last_block_sum(s, partials, &st->red_counter, &tot) && threadIdx.x == 0) {
+    st->rt2 = tot;
+    if (!force) {
+      if (sqrt(tot) / st->normb <= st->tol) {
+        st->done = 1;
+        st->status = SSCG_OK;
+      } else {
+        st->replace_pending = 1;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) replacement_kernel(const SolveState* __restrict__ st,
+                                                                  const double* __restrict__ rt,
+                                                                  double* __restrict__ Y, int64_t ld, int64_t n) {
+  if (st->done || !st->replace_pending) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = rt[i];
+    Y[i] = v;
+    Y[ld + i] = v;
+  }
+}
+
+// Bookkeeping at the end of one outer loop: finish a replacement, enforce the
+// outer-loop cap.
+__global__ void end_of_loop_kernel(SolveState* st, sscg_outer_record* hist) {
+  if (threadIdx.x != 0 || st->done) return;
+  if (st->replace_pending) {
+    st->replace_pending = 0;
+    st->converged_est = 0;
+    st->psi = 1.0;
+    st->replacements += 1;
+    const int k = st->k - 1;
+    if (hist != nullptr && k >= 0 && k < st->hist_cap) hist[k].replaced = 1;
+  }
+  if (st->k >= st->max_outer) {
+    st->status = SSCG_NOT_CONVERGED;
+    st->done = 1;
+  }
+}
+
+// ------------------------------------------------------------------ HSCG
+// Algorithm 1 with the updated-residual test ||r||/||b|| <= tol, confirmed by
+// the true residual (readings C16, C20).  One iteration:
+//   K1: q = A p, alpha = (r, r) / (p, q)          (reduction)
+//   K2: x += alpha p, r -= alpha q, beta = (r+, r+)/(r, r)   (reduction)
+//   K3: p = r + beta p
+__global__ void __launch_bounds__(kVecThreads) hscg_pq_kernel(SolveState* __restrict__ st, const double* __restrict__ p,
+                                                              const double* __restrict__ q, int64_t n,
+                                                              double* __restrict__ partials) {
+  if (st->done || st->converged_est) return;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(p[i], q[i], s);
+  double tot;
+  if (last_block_sum(s, partials, &st->red_counter, &tot) && threadIdx.x == 0) {
+    st->h_pq = tot;
+    st->h_alpha = st->h_rr / tot;
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) hscg_update_kernel(SolveState* __restrict__ st, double* __restrict__ x,
+                                                                  double* __restrict__ r, const double* __restrict__ p,
+                                                                  const double* __restrict__ q, int64_t n,
+                                                                  double* __restrict__ partials) {
+  if (st->done || st->converged_est) return;
+  const double alpha = st->h_alpha;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    s = fma(ri, ri, s);
+  }
+  double tot;
+  if (last_block_sum(s, partials, &st->red_counter, &tot) && threadIdx.x == 0) {
+    st->h_beta = tot / st->h_rr;
+    st->h_rr = tot;
+    st->h_iters += 1;
+    st->m = st->h_iters;
+    if (sqrt(tot) / st->normb <= st->tol) st->converged_est = 1;
+    if (st->h_iters >= st->h_max_iters && !st->converged_est) {
+      st->status = SSCG_NOT_CONVERGED;
+      st->done = 1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) hscg_pupdate_kernel(const SolveState* __restrict__ st,
+                                                                   const double* __restrict__ r, double* __restrict__ p,
+                                                                   int64_t n) {
+  if (st->done || st->converged_est) return;
+  const double beta = st->h_beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], r[i]);
+}
+
+__global__ void __launch_bounds__(kVecThreads) hscg_init_kernel(SolveState* __restrict__ st,
+                                                                const double* __restrict__ b,
+                                                                const double* __restrict__ r, double* __restrict__ p,
+                                                                int64_t n, double* __restrict__ partials,
+                                                                double* __restrict__ partials2) {
+  double sb = 0.0, sr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    p[i] = ri;
+    sr = fma(ri, ri, sr);
+    sb = fma(b[i], b[i], sb);
+  }
+  // two fixed-order sums: ||b||^2 into partials, ||r||^2 into partials2
+  const double bsb = block_sum(sb);
+  const double bsr = block_sum(sr);
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = bsb;
+    partials2[blockIdx.x] = bsr;
+    __threadfence();
+    is_last = atomicAdd(&st->red_counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double a = 0.0, c = 0.0;
+  for (int bi = threadIdx.x; bi < (int)gridDim.x; bi += kVecThreads) {
+    a += __ldcg(partials + bi);
+    c += __ldcg(partials2 + bi);
+  }
+  a = block_sum(a);
+  c = block_sum(c);
+  if (threadIdx.x == 0) {
+    st->normb = sqrt(a);
+    st->h_rr = c;
+    st->red_counter = 0u;
+    if (a == 0.0) {
+      st->zero_rhs = 1;
+      st->done = 1;
+      st->status = SSCG_OK;
+    } else if (sqrt(c) / st->normb <= st->tol) {
+      st->converged_est = 1;
+    }
+  }
+}
+
+// HSCG true-residual confirmation: if converged_est, rt = b - A x was formed
+// by the caller's residual launch; decide done or replace (r = p = rt).
+__global__ void __launch_bounds__(kVecThreads) hscg_confirm_kernel(SolveState* __restrict__ st,
+                                                                   const double* __restrict__ rt,
+                                                                   double* __restrict__ r, double* __restrict__ p,
+                                                                   int64_t n, double* __restrict__ partials) {
+  if (st->done || !st->converged_est) return;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = rt[i];
+    s = fma(v, v, s);
+  }
+  double tot;
+  if (last_block_sum(s, partials, &st->red_counter, &tot) && threadIdx.x == 0) {
+    st->rt2 = tot;
+    if (sqrt(tot) / st->normb <= st->tol) {
+      st->done = 1;
+      st->status = SSCG_OK;
+    } else {
+      st->replace_pending = 1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) hscg_replace_kernel(SolveState* __restrict__ st,
+                                                                   const double* __restrict__ rt,
+                                                                   double* __restrict__ r, double* __restrict__ p,
+                                                                   int64_t n) {
+  if (st->done || !st->replace_pending) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    r[i] = rt[i];
+    p[i] = rt[i];
+  }
+}
+
+__global__ void hscg_replace_finish_kernel(SolveState* st) {
+  if (st->done || !st->replace_pending) return;
+  st->replace_pending = 0;
+  st->converged_est = 0;
+  st->h_rr = st->rt2;
+  st->replacements += 1;
+}
+
+}  // namespace
+
+int reduce_blocks(int64_t n) { return vec_grid(n); }
+
+cudaError_t launch_recombine(const SolveState* state, double* Y, int64_t ld, double* x, int64_t n, bool y32,
+                             cudaStream_t st) {
+  if (y32) return cudaErrorNotSupported;
+  recombine_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(state, Y, ld, x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(SolveState* state, const Operator& A, const double* b, const double* x, double* Y,
+                              int64_t ld, double* partials, int nblocks, bool y32, cudaStream_t st) {
+  if (y32) return cudaErrorNotSupported;
+  cudaError_t e = launch_residual(A, b, x, Y + ld, st);  // r0 into column 1
+  if (e != cudaSuccess) return e;
+  init_norms_kernel<<<nblocks, kVecThreads, 0, st>>>(state, b, Y, ld, A.n, partials);
+  zero_x_kernel<<<vec_grid(A.n), kVecThreads, 0, st>>>(state, const_cast<double*>(x), A.n);
+  return cudaGetLastError();
+}
+
+}  // namespace sscg
+
+namespace sscg {
+
+cudaError_t launch_true_residual(SolveState* state, const Operator& A, const double* b, const double* x, double* rt,
+                                 double* partials, int nblocks, cudaStream_t st) {
+  cudaError_t e = launch_residual(A, b, x, rt, st, state, 1);
+  if (e != cudaSuccess) return e;
+  true_norm_kernel<<<nblocks, kVecThreads, 0, st>>>(state, rt, A.n, partials, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final_norm(SolveState* state, const Operator& A, const double* b, const double* x, double* rt,
+                              double* partials, int nblocks, cudaStream_t st) {
+  cudaError_t e = launch_residual(A, b, x, rt, st);
+  if (e != cudaSuccess) return e;
+  true_norm_kernel<<<nblocks, kVecThreads, 0, st>>>(state, rt, A.n, partials, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_replacement(SolveState* state, const double* rt, double* Y, int64_t ld, int64_t n,
+                                     bool y32, sscg_outer_record* hist, cudaStream_t st) {
+  if (y32) return cudaErrorNotSupported;
+  replacement_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(state, rt, Y, ld, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  end_of_loop_kernel<<<1, 32, 0, st>>>(state, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hscg_init(SolveState* state, const Operator& A, const double* b, const double* x, double* r,
+                             double* p, double* partials, int nblocks, cudaStream_t st) {
+  cudaError_t e = launch_residual(A, b, x, r, st);
+  if (e != cudaSuccess) return e;
+  hscg_init_kernel<<<nblocks, kVecThreads, 0, st>>>(state, b, r, p, A.n, partials, partials + nblocks);
+  zero_x_kernel<<<vec_grid(A.n), kVecThreads, 0, st>>>(state, const_cast<double*>(x), A.n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hscg_iteration(SolveState* state, const Operator& A, double* x, double* r, double* p, double* q,
+                                  double* partials, int nblocks, cudaStream_t st) {
+  cudaError_t e = launch_spmv(A, p, q, st, state, 2);
+  if (e != cudaSuccess) return e;
+  hscg_pq_kernel<<<nblocks, kVecThreads, 0, st>>>(state, p, q, A.n, partials);
+  hscg_update_kernel<<<nblocks, kVecThreads, 0, st>>>(state, x, r, p, q, A.n, partials);
+  hscg_pupdate_kernel<<<nblocks, kVecThreads, 0, st>>>(state, r, p, A.n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hscg_check(SolveState* state, const Operator& A, const double* b, const double* x, double* r,
+                              double* p, double* rt, double* partials, int nblocks, cudaStream_t st) {
+  cudaError_t e = launch_residual(A, b, x, rt, st, state, 1);
+  if (e != cudaSuccess) return e;
+  hscg_confirm_kernel<<<nblocks, kVecThreads, 0, st>>>(state, rt, r, p, A.n, partials);
+  hscg_replace_kernel<<<vec_grid(A.n), kVecThreads, 0, st>>>(state, rt, r, p, A.n);
+  hscg_replace_finish_kernel<<<1, 1, 0, st>>>(state);
+  return cudaGetLastError();
+}
+
+}  // namespace sscg

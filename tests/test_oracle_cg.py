@@ -136,3 +136,26 @@ def test_c_modes():
     assert cg.c_value("kappa_ratio", 0.1, 4.0, 0.5) == 40.0
     assert cg.c_value("one", 0.1, 4.0, 0.5) == 1.0
     assert cg.c_value("xi_scaled", 0.1, 4.0, 0.01) == max(1.0, 4.0 * 0.1 / 0.1)
+
+
+def test_replay_of_own_log_is_identity():
+    st = gen.varcoef_stencil((12, 10, 9), seed=11)
+    b = gen.random_rhs(st.n, 12)
+    A = as_matrix(st)
+    x1, i1 = cg.sstep_cg(A, b, np.zeros(st.n), 1e-10, cg.Options(smax=8, basis="newton"))
+    log = [dict(stilde=h["stilde"], sk=h["sk"], replaced=h.get("replaced", False)) for h in i1["hist"]]
+    x2, i2 = cg.sstep_cg(A, b, np.zeros(st.n), 1e-10, cg.Options(smax=8, basis="newton", replay=log))
+    assert np.array_equal(x1, x2) and i1["outer"] == i2["outer"]
+    assert all(not h["margins"] for h in i2["hist"])
+
+
+def test_replay_records_margin_of_a_forced_decision():
+    st = gen.varcoef_stencil((12, 10, 9), seed=11)
+    b = gen.random_rhs(st.n, 12)
+    A = as_matrix(st)
+    _, i1 = cg.sstep_cg(A, b, np.zeros(st.n), 1e-10, cg.Options(smax=8, basis="newton"))
+    log = [dict(stilde=h["stilde"], sk=h["sk"]) for h in i1["hist"]]
+    k = next(i for i, h in enumerate(log) if h["stilde"] >= 3 and h["sk"] >= 2)
+    log[k] = dict(stilde=log[k]["stilde"] - 1, sk=min(log[k]["sk"], log[k]["stilde"] - 1))
+    _, i2 = cg.sstep_cg(A, b, np.zeros(st.n), 1e-10, cg.Options(smax=8, basis="newton", replay=log[:k + 1]))
+    assert "stilde" in i2["hist"][k]["margins"]
