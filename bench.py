@@ -33,6 +33,10 @@ WORKLOADS = {
                                "b~N(0,1), x0=0", smax=16, basis="newton", tol=1e-10),
     "poisson2d_64": dict(desc="FP64 2D 5-pt Poisson 64x64 CSR (N=4096), b=A x*, x*~U(-1,1), x0=0",
                          smax=8, basis="chebyshev", tol=1e-10),
+    # a smaller grid of the same stencil family, used for kernel profiles
+    "varcoef3d_96": dict(desc="FP64 3D 7-pt var-coef diffusion 96^3 (N=884,736), k=exp(N(0,1)) per face, "
+                              "b~N(0,1), x0=0", smax=16, basis="newton", tol=1e-10, base="varcoef3d_160",
+                         scale=96),
 }
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -51,12 +55,14 @@ def parse_args():
     ap.add_argument("--cpu-outer", type=int, default=3, help="outer loops in the oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--max-outer", type=int, default=0, help="cap outer loops (profiling runs only)")
     return ap.parse_args()
 
 
 def load_inputs(name):
     from sscg_inputs import generators as gen
-    return gen.config_problem(name)
+    cfg = WORKLOADS[name]
+    return gen.config_problem(cfg.get("base", name), scale=cfg.get("scale"))
 
 
 def oracle_counts(name):
@@ -198,8 +204,9 @@ def main():
 
     def solve(profile=1):
         x.zero_()
+        extra = {"max_outer": args.max_outer} if args.max_outer > 0 else {}
         return solver.solve(b, x, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], hist_cap=20000,
-                            profile=profile)
+                            profile=profile, **extra)
 
     for _ in range(args.warmup):
         solve()

@@ -65,7 +65,9 @@ typedef struct {
   int newton_scale;      /* 0: gamma_l = (lmax - lmin)/4 (interval capacity); 1: gamma_l = 1 as printed; default 0 */
   int cheb_params;       /* 0: rho_l(z) = T_l((z-c)/h); 1: eq. (chebbasis) as printed; default 0 */
   int inner_conv_check;  /* 1: test sqrt(r'^T G r')/||b|| <= tol after every inner step; default 1 */
-  int y_fp32;            /* 1: store the basis Y in binary32 (arithmetic stays binary64); default 0 */
+  int y_fp32;            /* 1: store the basis Y in binary32 (recurrence, Gram, x, r, p stay binary64;
+                            r := b - A x whenever the residual estimate has fallen by 2^-4 since the
+                            last such replacement); default 0 */
   int variant;           /* 0: Algorithm 5; 1: fixed s-step CG (s_k = sigma, no break test); default 0 */
   int check_every;       /* outer loops enqueued between two polls of the done flag; default 4 */
   int use_graph;         /* 1: replay one outer loop as a CUDA graph; default 1 */
@@ -80,7 +82,8 @@ typedef struct {
  * coordinate residual estimate, and kappa_l ~ kappa(Y_l) for l = 1..s-bar_k
  * (kappa[0] unused; +inf when numerically singular). */
 typedef struct {
-  int sbar, stilde, sk, replaced;
+  int sbar, stilde, sk;
+  int replaced;          /* bit 0: true-residual replacement (convergence check failed); bit 1: FP32-basis replacement */
   double c_start, c_end, phi, lmin, lmax, relres_est;
   double kappa[SSCG_MAX_S + 1];
 } sscg_outer_record;
@@ -93,6 +96,7 @@ typedef struct {
   int inner_iters;       /* total CG iterations m */
   int host_syncs;        /* times the host waited on the device during the solve */
   int replacements;      /* residual replacements after a failed true-residual check */
+  int fp32_replacements; /* y_fp32 only: r := b - A x after the residual fell by 2^-4 since the last one */
   int kernel_launches;   /* kernels of this library launched by the solve (graph nodes counted) */
   double lambda_min, lambda_max; /* final Ritz estimates (Algs. 3-4) */
   double c_last;         /* final c */
@@ -152,7 +156,10 @@ void sscg_opts_default(sscg_opts* opts);
  * opts may be NULL (defaults); stats may be NULL.
  * Convergence is declared on the coordinate residual estimate and confirmed by
  * a true residual computed on the device; if that check fails, r := b - A x,
- * p := r and the iteration continues (counted in stats->replacements).
+ * p := r and the iteration continues (counted in stats->replacements).  A
+ * failed check whose true residual has not halved since the previous failed
+ * check ends the solve with SSCG_NOT_CONVERGED (tol below the attainable
+ * accuracy).
  * Returns SSCG_OK, SSCG_NOT_CONVERGED, SSCG_BREAKDOWN or a negative error.
  * The call returns after the solve has finished on the device. */
 int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg_basis basis,

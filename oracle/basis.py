@@ -150,16 +150,24 @@ def basis_params(kind: int, s: int, lmin: float | None, lmax: float | None,
 # the basis matrix Y and the change-of-basis matrix B
 # ----------------------------------------------------------------------------
 
-def krylov_basis(A, p: np.ndarray, r: np.ndarray, s: int, theta, gamma, mu) -> np.ndarray:
+def krylov_basis(A, p: np.ndarray, r: np.ndarray, s: int, theta, gamma, mu,
+                 store32: bool = False) -> np.ndarray:
     """Y (N x (2s+1), interleaved) by the three-term recurrence eq. (rho).
 
     P_{l+1} = ((A - theta_l I) P_l - mu_{l-1} P_{l-1}) / gamma_l (no mu term for l = 0),
     the same for R, which stops at R_{s-1} (eq. cg-krylovbasis).
+    store32: every column is rounded to binary32 when it is stored, and the
+    recurrence continues from the stored (rounded) columns in binary64
+    arithmetic (the FP32-stored-basis variant).
     """
     N = p.shape[0]
     Y = np.zeros((N, 2 * s + 1))
-    Y[:, p_index(0)] = p
-    Y[:, r_index(0)] = r
+
+    def put(c, v):
+        Y[:, c] = v.astype(np.float32).astype(np.float64) if store32 else v
+
+    put(p_index(0), p)
+    put(r_index(0), r)
     for l in range(s):
         for chain_len, index in ((s, p_index), (s - 1, r_index)):
             if l + 1 > chain_len:
@@ -168,7 +176,7 @@ def krylov_basis(A, p: np.ndarray, r: np.ndarray, s: int, theta, gamma, mu) -> n
             w = A @ v - theta[l] * v
             if l >= 1:
                 w = w - mu[l - 1] * Y[:, index(l - 1)]
-            Y[:, index(l + 1)] = w / gamma[l]
+            put(index(l + 1), w / gamma[l])
     return Y
 
 

@@ -16,7 +16,10 @@ Readings of the paper used here (the CUDA path takes the same ones):
        every inner step (``inner_conv_check``), ending the block.
   C16  convergence is declared on the updated residual, then confirmed with the
        true residual b - A x; if that is above tol, r := b - A x, p := r,
-       psi := 1 and the iteration continues (a "replacement").
+       psi := 1 and the iteration continues (a "replacement").  A failed check
+       whose true residual has not halved since the previous failed check
+       means the attainable accuracy is above tol: the solve stops with
+       NOT_CONVERGED.
   C17  alpha invalid (p'^T G B p' <= 0 or not finite) at inner step j > 0 ends
        the block with s_k = j; at j = 0 the solve stops with BREAKDOWN.
        r'^T G r' <= 0 after a step reads as "residual estimate zero": the step is
@@ -65,12 +68,17 @@ def hscg(A, b, x0, tol: float, max_iters: int = 100000):
     it = 0
     replacements = 0
     status = NOT_CONVERGED
+    prev_fail = 0.0
     while it < max_iters:
         if math.sqrt(rr) / normb <= tol:
             rt = b - A @ x
-            if _norm(rt) / normb <= tol:
+            rel = _norm(rt) / normb
+            if rel <= tol:
                 status = OK
                 break
+            if prev_fail > 0.0 and rel >= 0.5 * prev_fail:
+                break                       # stagnation above tol (reading C16)
+            prev_fail = rel
             r, p = rt, rt.copy()
             rr = float(r @ r)
             replacements += 1
@@ -105,7 +113,10 @@ class Options:
     inner_conv_check: bool = True      # reading C15
     eps: float = EPS64
     kappa_cut: float = KAPPA_CUT       # reading C14
-    y_fp32: bool = False               # store the basis rounded to FP32
+    y_fp32: bool = False               # store the basis rounded to FP32 (x, r, p stay FP64)
+    # FP32-stored basis: replace r by b - A x at the end of a block once the
+    # residual estimate has fallen by this factor since the last replacement
+    fp32_replace_drop: float = 2.0 ** -4
     variant: str = "improved"          # improved (Alg. 5) | fixed (s_k = sigma)
     # replay: a decision log [{"stilde", "sk", "replaced"}, ...] from another
     # implementation.  The oracle then takes those decisions instead of its own,
@@ -183,11 +194,12 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
     status = NOT_CONVERGED
     s_prev = None
     done = False
+    rho_last = 1.0          # FP32 basis: relative residual at the last replacement
+    fp32_replacements = 0
+    prev_fail = 0.0         # relative true residual at the last failed convergence check
     for k in range(o.max_outer):
         sbar = s0 if k == 0 else min(s_prev + f, sigma)
-        Y = bs.krylov_basis(A, p, r, sbar, theta, gamma, mu)
-        if o.y_fp32:
-            Y = Y.astype(np.float32).astype(np.float64)
+        Y = bs.krylov_basis(A, p, r, sbar, theta, gamma, mu, store32=o.y_fp32)
         G = Y.T @ Y
         kap, _, _ = kappa_estimates(G, sbar, o.kappa_cut)
         normr = math.sqrt(G[1, 1])
@@ -284,6 +296,16 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
             # outer-level test only (reading C15 off): the coordinate estimate
             # of the updated residual at the end of the block
             converged_est = math.sqrt(max(rr, 0.0)) / normb <= tol
+        if o.y_fp32 and not converged_est:
+            # FP32 basis: each block perturbs the updated residual at the 2^-24
+            # level of the largest residual since the last replacement; put the
+            # true residual back once the estimate has fallen far enough (p kept)
+            est = math.sqrt(max(rr, 0.0)) / normb
+            if est <= o.fp32_replace_drop * rho_last:
+                r = b - A @ x
+                rho_last = _norm(r) / normb
+                fp32_replacements += 1
+                hist[-1]["fp32_replaced"] = True
         if o.replay is not None:
             if k + 1 >= len(o.replay):
                 status = OK if _norm(b - A @ x) / normb <= tol else NOT_CONVERGED
@@ -297,10 +319,14 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
             continue
         if converged_est:
             rt = b - A @ x
-            if _norm(rt) / normb <= tol:
+            rel = _norm(rt) / normb
+            if rel <= tol:
                 status = OK
                 done = True
+            elif prev_fail > 0.0 and rel >= 0.5 * prev_fail:
+                break                       # stagnation above tol (reading C16)
             else:
+                prev_fail = rel
                 r, p = rt, rt.copy()
                 psi = 1.0
                 replacements += 1
@@ -310,5 +336,5 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
     relres = _norm(b - A @ x) / normb
     info = dict(status=status, outer=len(hist), inner=m, alphas=alphas, betas=betas,
                 hist=hist, replacements=replacements, relres_true=relres,
-                lmin=ritz.lmin, lmax=ritz.lmax, c=c, psi=psi)
+                lmin=ritz.lmin, lmax=ritz.lmax, c=c, psi=psi, fp32_replacements=fp32_replacements)
     return x, info

@@ -75,6 +75,7 @@ struct sscg_ctx {
   // cached graph of one outer loop
   cudaGraphExec_t graph = nullptr;
   int graph_sigma = -1;
+  bool graph_y32 = false;
   int graph_launches = 0;
   double last_lmin = 0.0, last_lmax = 0.0;
 };
@@ -112,7 +113,7 @@ cudaMemcpyKind kind_of(int on_device) {
   return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 }
 
-int ensure_solve_buffers(sscg_ctx* h, int sigma, int hist_cap) {
+int ensure_solve_buffers(sscg_ctx* h, int sigma, int hist_cap, bool y32 = false) {
   const int64_t n = h->n;
   h->ld = round_up(n, 32);
   const size_t ycount = (size_t)h->ld * (2 * sigma + 1);
@@ -130,6 +131,17 @@ int ensure_solve_buffers(sscg_ctx* h, int sigma, int hist_cap) {
   CK(h->rt.ensure(n));
   CK(h->b.ensure(n));
   CK(h->x.ensure(n));
+  if (y32) {
+    if (h->r.n < (size_t)n || h->p.n < (size_t)n) {
+      if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+        h->graph_sigma = -1;
+      }
+    }
+    CK(h->r.ensure(n));
+    CK(h->p.ensure(n));
+  }
   if (hist_cap > 0 && (size_t)hist_cap > h->hist.n) {
     if (h->graph) {
       cudaGraphExecDestroy(h->graph);
@@ -142,7 +154,7 @@ int ensure_solve_buffers(sscg_ctx* h, int sigma, int hist_cap) {
 }
 
 // Enqueue one outer loop of Algorithm 5.  Returns the number of kernels.
-int enqueue_body(sscg_ctx* h, int sigma, cudaStream_t st, std::vector<cudaEvent_t>* evs, int* nlaunch) {
+int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<cudaEvent_t>* evs, int* nlaunch) {
   SolveState* ds = h->state.p;
   LevelCoef coef{ds->theta, ds->inv_gamma, ds->mu};
   int count = 0;
@@ -153,11 +165,11 @@ int enqueue_body(sscg_ctx* h, int sigma, cudaStream_t st, std::vector<cudaEvent_
   int rc;
   if ((rc = mark(0))) return rc;
   for (int l = 0; l < sigma; ++l) {
-    CK(launch_mpk_level(h->op, h->Y.p, h->ld, l, ds, 0, coef, false, st));
+    CK(launch_mpk_level(h->op, h->Y.p, h->ld, l, ds, 0, coef, y32, st));
     ++count;
   }
   if ((rc = mark(1))) return rc;
-  CK(launch_gram(h->Y.p, h->n, h->ld, nullptr, 0, ds, h->partials.p, gram_blocks(h->n), h->G.p, kMaxCols, false,
+  CK(launch_gram(h->Y.p, h->n, h->ld, nullptr, 0, ds, h->partials.p, gram_blocks(h->n), h->G.p, kMaxCols, y32,
                  st));
   count += 2;
   if ((rc = mark(2))) return rc;
@@ -168,19 +180,25 @@ int enqueue_body(sscg_ctx* h, int sigma, cudaStream_t st, std::vector<cudaEvent_
   CK(launch_control(ds, h->G.p, kMaxCols, h->leja.p, h->hist.n ? h->hist.p : nullptr, st));
   ++count;
   if ((rc = mark(4))) return rc;
-  CK(launch_recombine(ds, h->Y.p, h->ld, h->x.p, h->n, false, st));
+  CK(launch_recombine(ds, h->Y.p, h->ld, h->x.p, y32 ? h->r.p : nullptr, y32 ? h->p.p : nullptr, h->n, y32, st));
   ++count;
   if ((rc = mark(5))) return rc;
+  if (y32) {
+    CK(launch_fp32_replacement(ds, h->op, h->b.p, h->x.p, h->Y.p, h->ld, h->r.p, h->partials.p, reduce_blocks(h->n),
+                               h->hist.n ? h->hist.p : nullptr, st));
+    count += 2;
+  }
   CK(launch_true_residual(ds, h->op, h->b.p, h->x.p, h->rt.p, h->partials.p, reduce_blocks(h->n), st));
-  CK(launch_apply_replacement(ds, h->rt.p, h->Y.p, h->ld, h->n, false, h->hist.n ? h->hist.p : nullptr, st));
+  CK(launch_apply_replacement(ds, h->rt.p, h->Y.p, h->ld, y32 ? h->r.p : nullptr, y32 ? h->p.p : nullptr, h->n, y32,
+                              h->hist.n ? h->hist.p : nullptr, st));
   count += 4;
   if ((rc = mark(6))) return rc;
   *nlaunch = count;
   return SSCG_OK;
 }
 
-int build_graph(sscg_ctx* h, int sigma) {
-  if (h->graph && h->graph_sigma == sigma) return SSCG_OK;
+int build_graph(sscg_ctx* h, int sigma, bool y32) {
+  if (h->graph && h->graph_sigma == sigma && h->graph_y32 == y32) return SSCG_OK;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -188,7 +206,7 @@ int build_graph(sscg_ctx* h, int sigma) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int nl = 0;
-  int rc = enqueue_body(h, sigma, h->stream, nullptr, &nl);
+  int rc = enqueue_body(h, sigma, y32, h->stream, nullptr, &nl);
   cudaError_t e = cudaStreamEndCapture(h->stream, &g);
   if (rc) return rc;
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -196,6 +214,7 @@ int build_graph(sscg_ctx* h, int sigma) {
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   h->graph_sigma = sigma;
+  h->graph_y32 = y32;
   h->graph_launches = nl;
   return SSCG_OK;
 }
@@ -222,6 +241,8 @@ void fill_state_config(SolveState& s, int sigma, double tol, int basis, const ss
   s.status = SSCG_NOT_CONVERGED;
   s.c = 1.0 / std::sqrt(o.eps);  // c_1 = eps^{-1/2} (Alg. 5)
   s.psi = 1.0;
+  s.fp32_drop = std::ldexp(1.0, -4);  // FP32 basis: replace r after a 2^-4 drop
+  s.rho_last = 1.0;
   for (int l = 0; l < kMaxS; ++l) {
     s.theta[l] = 0.0;  // monomial basis until Ritz values exist
     s.gamma[l] = 1.0;
@@ -233,7 +254,6 @@ void fill_state_config(SolveState& s, int sigma, double tol, int basis, const ss
 int validate_opts(const sscg_opts& o) {
   if (o.c_mode < 0 || o.c_mode > SSCG_C_CONST) return SSCG_ERR_INVALID_ARG;
   if (!(o.eps > 0.0) || !(o.kappa_cut >= 0.0)) return SSCG_ERR_INVALID_ARG;
-  if (o.y_fp32) return SSCG_ERR_UNSUPPORTED;
   return SSCG_OK;
 }
 
@@ -414,7 +434,8 @@ int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg
   if (stats && stats->hist && stats->hist_cap > 0) hist_cap = stats->hist_cap;
   if (o.profile && hist_cap == 0) hist_cap = std::min(o.max_outer > 0 ? o.max_outer : 100000, 100000);
   hist_cap = std::min(hist_cap, o.max_outer > 0 ? o.max_outer : 100000);
-  if ((rc = ensure_solve_buffers(h, sigma, hist_cap))) return rc;
+  const bool y32 = o.y_fp32 != 0;
+  if ((rc = ensure_solve_buffers(h, sigma, hist_cap, y32))) return rc;
   if ((rc = join_in(h))) return rc;
   cudaStream_t st = h->stream;
   const int64_t n = h->n;
@@ -425,13 +446,14 @@ int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg
   CK(cudaStreamSynchronize(st));
   fill_state_config(*h->host_state, sigma, tol, (int)basis, o, hist_cap);
   CK(cudaMemcpyAsync(h->state.p, h->host_state, sizeof(SolveState), cudaMemcpyHostToDevice, st));
-  CK(launch_init_state(h->state.p, h->op, h->b.p, h->x.p, h->Y.p, h->ld, h->partials.p, reduce_blocks(n), false, st));
+  CK(launch_init_state(h->state.p, h->op, h->b.p, h->x.p, h->Y.p, h->ld, y32 ? h->r.p : nullptr,
+                       y32 ? h->p.p : nullptr, h->partials.p, reduce_blocks(n), y32, st));
   int launches = 2;
   int host_syncs = 1;
 
   const bool prof = o.profile != 0;
   const bool graph = o.use_graph && !prof;
-  if (graph && (rc = build_graph(h, sigma))) return rc;
+  if (graph && (rc = build_graph(h, sigma, y32))) return rc;
   const int every = std::max(1, o.check_every);
   double tph[6] = {0, 0, 0, 0, 0, 0};
   std::vector<cudaEvent_t> evs;
@@ -449,7 +471,7 @@ int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg
         std::vector<cudaEvent_t> sub;
         if (prof) sub.assign(evs.begin() + 7 * b2, evs.begin() + 7 * b2 + 7);
         int nl = 0;
-        if ((rc = enqueue_body(h, sigma, st, prof ? &sub : nullptr, &nl))) return rc;
+        if ((rc = enqueue_body(h, sigma, y32, st, prof ? &sub : nullptr, &nl))) return rc;
         launches += nl;
       }
       ++bodies;
@@ -493,6 +515,7 @@ int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg
     stats->inner_iters = s.m;
     stats->host_syncs = host_syncs;
     stats->replacements = s.replacements;
+    stats->fp32_replacements = s.fp32_replacements;
     stats->kernel_launches = launches;
     stats->lambda_min = s.lmin;
     stats->lambda_max = s.lmax;

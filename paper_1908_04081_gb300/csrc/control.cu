@@ -490,6 +490,9 @@ __global__ void __launch_bounds__(kControlThreads) control_kernel(SolveState* __
       }
       int nsb = sk + st->f;
       st->sbar = nsb < st->sigma ? nsb : st->sigma;
+      // FP32-stored basis: put the true residual back once the estimate has
+      // fallen by fp32_drop since the last replacement (p is kept)
+      if (st->y_fp32 && !conv && st->upd_relres <= st->fp32_drop * st->rho_last) st->fp32_replace_pending = 1;
     }
     if (hist != nullptr && k < st->hist_cap) {
       sscg_outer_record& h = hist[k];

@@ -27,8 +27,9 @@ __device__ __forceinline__ void pair_of(int q, int ncols, int* pi, int* pj) {
   *pj = i + rem;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kGramThreads, 2)
-gram_partial_kernel(const double* __restrict__ Y, int64_t n, int64_t ld, const SolveState* __restrict__ st,
+gram_partial_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const SolveState* __restrict__ st,
                     int ncols_fixed, double* __restrict__ partials) {
   int ncols = ncols_fixed;
   if (ncols <= 0) {
@@ -60,7 +61,7 @@ gram_partial_kernel(const double* __restrict__ Y, int64_t n, int64_t ld, const S
       const int c = e / kGramTileRows;
       const int r = e - c * kGramTileRows;
       const int64_t row = r0 + r;
-      tile[r][c] = row < r_end ? __ldg(Y + (int64_t)c * ld + row) : 0.0;
+      tile[r][c] = row < r_end ? (double)__ldg(Y + (int64_t)c * ld + row) : 0.0;
     }
     __syncthreads();
     if (active) {
@@ -112,11 +113,15 @@ int gram_blocks(int64_t n) {
   return b < 1 ? 1 : (int)b;
 }
 
-cudaError_t launch_gram(const double* Y, int64_t n, int64_t ld, const int* /*ncols_dev*/, int ncols_fixed,
+cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* /*ncols_dev*/, int ncols_fixed,
                         const SolveState* state, double* partials, int nblocks, double* G, int ldg, bool y32,
                         cudaStream_t st) {
-  if (y32) return cudaErrorNotSupported;
-  gram_partial_kernel<<<nblocks, kGramThreads, 0, st>>>(Y, n, ld, state, ncols_fixed, partials);
+  if (y32)
+    gram_partial_kernel<float><<<nblocks, kGramThreads, 0, st>>>(static_cast<const float*>(Y), n, ld, state,
+                                                                 ncols_fixed, partials);
+  else
+    gram_partial_kernel<double><<<nblocks, kGramThreads, 0, st>>>(static_cast<const double*>(Y), n, ld, state,
+                                                                  ncols_fixed, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int warps_per_block = 256 / 32;

@@ -59,10 +59,12 @@ __device__ __forceinline__ double stencil_apply(const Operator& A, const T* __re
 }
 
 // Launch gates read from the solve state: 0 = always run, 1 = only when a
-// true-residual check is pending, 2 = only while the iteration is running.
+// true-residual check is pending, 2 = only while the iteration is running,
+// 3 = only when an FP32-basis residual replacement is pending.
 __device__ __forceinline__ bool gate_closed(const SolveState* g, int mode) {
   if (mode == 0 || g == nullptr) return false;
   if (g->done) return true;
+  if (mode == 3) return !g->fp32_replace_pending;
   return mode == 1 ? !g->converged_est : g->converged_est != 0;
 }
 
@@ -100,9 +102,11 @@ __global__ void __launch_bounds__(kOpThreads) stencil_residual_kernel(Operator A
 }
 
 // One matrix-powers level for a stencil.  `sbar` is read from the solve state
-// (device) unless sbar_fixed > 0.
-template <bool DIM3>
-__global__ void __launch_bounds__(kOpThreads) stencil_mpk_kernel(Operator A, double* __restrict__ Y, int64_t ld,
+// (device) unless sbar_fixed > 0.  T is the storage type of the basis
+// (double, or float for the FP32-stored variant: loads widen to binary64,
+// the recurrence runs in binary64, stores round to binary32).
+template <bool DIM3, typename T>
+__global__ void __launch_bounds__(kOpThreads) stencil_mpk_kernel(Operator A, T* __restrict__ Y, int64_t ld,
                                                                  int level, const SolveState* __restrict__ st,
                                                                  int sbar_fixed, LevelCoef coef) {
   int sbar = sbar_fixed;
@@ -116,12 +120,12 @@ __global__ void __launch_bounds__(kOpThreads) stencil_mpk_kernel(Operator A, dou
   const double theta = coef.theta[level];
   const double ig = coef.inv_gamma[level];
   const double mu = level >= 1 ? coef.mu[level - 1] : 0.0;
-  const double* Pl = Y + (int64_t)(2 * level) * ld;
-  const double* Rl = Y + (int64_t)(2 * level + 1) * ld;
-  const double* Pm = level >= 1 ? Y + (int64_t)(2 * level - 2) * ld : nullptr;
-  const double* Rm = level >= 1 ? Y + (int64_t)(2 * level - 1) * ld : nullptr;
-  double* Pn = Y + (int64_t)(2 * level + 2) * ld;
-  double* Rn = Y + (int64_t)(2 * level + 3) * ld;
+  const T* Pl = Y + (int64_t)(2 * level) * ld;
+  const T* Rl = Y + (int64_t)(2 * level + 1) * ld;
+  const T* Pm = level >= 1 ? Y + (int64_t)(2 * level - 2) * ld : nullptr;
+  const T* Rm = level >= 1 ? Y + (int64_t)(2 * level - 1) * ld : nullptr;
+  T* Pn = Y + (int64_t)(2 * level + 2) * ld;
+  T* Rn = Y + (int64_t)(2 * level + 3) * ld;
   const int64_t n = A.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -131,12 +135,12 @@ __global__ void __launch_bounds__(kOpThreads) stencil_mpk_kernel(Operator A, dou
     int z = (int)(t / A.ny);
     const double ds = __ldg(A.diag + i) - theta;
     double wp = stencil_apply<DIM3>(A, Pl, i, x, yy, z, ds);
-    if (mu != 0.0) wp = fma(-mu, __ldg(Pm + i), wp);
-    Pn[i] = wp * ig;
+    if (mu != 0.0) wp = fma(-mu, ld_val(Pm + i), wp);
+    Pn[i] = (T)(wp * ig);
     if (doR) {
       double wr = stencil_apply<DIM3>(A, Rl, i, x, yy, z, ds);
-      if (mu != 0.0) wr = fma(-mu, __ldg(Rm + i), wr);
-      Rn[i] = wr * ig;
+      if (mu != 0.0) wr = fma(-mu, ld_val(Rm + i), wr);
+      Rn[i] = (T)(wr * ig);
     }
   }
 }
@@ -171,7 +175,8 @@ __global__ void __launch_bounds__(kOpThreads) csr_residual_kernel(Operator A, co
   }
 }
 
-__global__ void __launch_bounds__(kOpThreads) csr_mpk_kernel(Operator A, double* __restrict__ Y, int64_t ld,
+template <typename T>
+__global__ void __launch_bounds__(kOpThreads) csr_mpk_kernel(Operator A, T* __restrict__ Y, int64_t ld,
                                                              int level, const SolveState* __restrict__ st,
                                                              int sbar_fixed, LevelCoef coef) {
   int sbar = sbar_fixed;
@@ -185,12 +190,12 @@ __global__ void __launch_bounds__(kOpThreads) csr_mpk_kernel(Operator A, double*
   const double theta = coef.theta[level];
   const double ig = coef.inv_gamma[level];
   const double mu = level >= 1 ? coef.mu[level - 1] : 0.0;
-  const double* Pl = Y + (int64_t)(2 * level) * ld;
-  const double* Rl = Y + (int64_t)(2 * level + 1) * ld;
-  const double* Pm = level >= 1 ? Y + (int64_t)(2 * level - 2) * ld : nullptr;
-  const double* Rm = level >= 1 ? Y + (int64_t)(2 * level - 1) * ld : nullptr;
-  double* Pn = Y + (int64_t)(2 * level + 2) * ld;
-  double* Rn = Y + (int64_t)(2 * level + 3) * ld;
+  const T* Pl = Y + (int64_t)(2 * level) * ld;
+  const T* Rl = Y + (int64_t)(2 * level + 1) * ld;
+  const T* Pm = level >= 1 ? Y + (int64_t)(2 * level - 2) * ld : nullptr;
+  const T* Rm = level >= 1 ? Y + (int64_t)(2 * level - 1) * ld : nullptr;
+  T* Pn = Y + (int64_t)(2 * level + 2) * ld;
+  T* Rn = Y + (int64_t)(2 * level + 3) * ld;
   const int64_t n = A.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -200,19 +205,19 @@ __global__ void __launch_bounds__(kOpThreads) csr_mpk_kernel(Operator A, double*
       for (int64_t k = b; k < e; ++k) {
         const double a = __ldg(A.val + k);
         const int c = __ldg(A.col + k);
-        ap = fma(a, __ldg(Pl + c), ap);
-        ar = fma(a, __ldg(Rl + c), ar);
+        ap = fma(a, ld_val(Pl + c), ap);
+        ar = fma(a, ld_val(Rl + c), ar);
       }
     } else {
-      for (int64_t k = b; k < e; ++k) ap = fma(__ldg(A.val + k), __ldg(Pl + __ldg(A.col + k)), ap);
+      for (int64_t k = b; k < e; ++k) ap = fma(__ldg(A.val + k), ld_val(Pl + __ldg(A.col + k)), ap);
     }
-    double wp = fma(-theta, __ldg(Pl + i), ap);
-    if (mu != 0.0) wp = fma(-mu, __ldg(Pm + i), wp);
-    Pn[i] = wp * ig;
+    double wp = fma(-theta, ld_val(Pl + i), ap);
+    if (mu != 0.0) wp = fma(-mu, ld_val(Pm + i), wp);
+    Pn[i] = (T)(wp * ig);
     if (doR) {
-      double wr = fma(-theta, __ldg(Rl + i), ar);
-      if (mu != 0.0) wr = fma(-mu, __ldg(Rm + i), wr);
-      Rn[i] = wr * ig;
+      double wr = fma(-theta, ld_val(Rl + i), ar);
+      if (mu != 0.0) wr = fma(-mu, ld_val(Rm + i), wr);
+      Rn[i] = (T)(wr * ig);
     }
   }
 }
@@ -258,14 +263,22 @@ cudaError_t launch_residual(const Operator& A, const double* b, const double* x,
   return cudaGetLastError();
 }
 
-cudaError_t launch_mpk_level(const Operator& A, double* Y, int64_t ld, int level, const SolveState* state,
+cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level, const SolveState* state,
                              int sbar_fixed, LevelCoef coef, bool y32, cudaStream_t st) {
-  if (y32) return cudaErrorNotSupported;
   int g = grid_for(A.n, 4);
-  if (A.kind == 0) csr_mpk_kernel<<<g, kOpThreads, 0, st>>>(A, Y, ld, level, state, sbar_fixed, coef);
-  else if (A.dim == 3)
-    stencil_mpk_kernel<true><<<g, kOpThreads, 0, st>>>(A, Y, ld, level, state, sbar_fixed, coef);
-  else stencil_mpk_kernel<false><<<g, kOpThreads, 0, st>>>(A, Y, ld, level, state, sbar_fixed, coef);
+  if (y32) {
+    float* Yf = static_cast<float*>(Y);
+    if (A.kind == 0) csr_mpk_kernel<float><<<g, kOpThreads, 0, st>>>(A, Yf, ld, level, state, sbar_fixed, coef);
+    else if (A.dim == 3)
+      stencil_mpk_kernel<true, float><<<g, kOpThreads, 0, st>>>(A, Yf, ld, level, state, sbar_fixed, coef);
+    else stencil_mpk_kernel<false, float><<<g, kOpThreads, 0, st>>>(A, Yf, ld, level, state, sbar_fixed, coef);
+  } else {
+    double* Yd = static_cast<double*>(Y);
+    if (A.kind == 0) csr_mpk_kernel<double><<<g, kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);
+    else if (A.dim == 3)
+      stencil_mpk_kernel<true, double><<<g, kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);
+    else stencil_mpk_kernel<false, double><<<g, kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);
+  }
   return cudaGetLastError();
 }
 

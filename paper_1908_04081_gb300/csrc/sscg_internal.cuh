@@ -57,6 +57,10 @@ struct SolveState {
   int replacements;
   int have_ritz;      // basis parameters come from Ritz values (m > 1)
   int zero_rhs;       // b = 0: x = 0 is returned without iterating
+  // FP32-stored basis: periodic residual replacement (r := b - A x, p kept)
+  double fp32_drop, rho_last;
+  double prev_fail;   // relative true residual at the last failed convergence check
+  int fp32_replace_pending, fp32_replacements;
   double c, psi, normb, upd_relres;
   // Meurant-Tichy state (Algs. 3-4)
   int mt_n;
@@ -83,7 +87,7 @@ struct SolveState {
 // operator kernels (ops_stencil.cu / ops_csr.cu)
 // gmode: 0 = always run; 1 = only when a true-residual check is pending
 // (state->converged_est and not done); 2 = only while iterating (not done and
-// no check pending).
+// no check pending); 3 = only when an FP32-basis replacement is pending.
 cudaError_t launch_spmv(const Operator& A, const double* v, double* y, cudaStream_t st,
                         const SolveState* gate = nullptr, int gmode = 0);
 // diag_i = sum of the faces of cell i (the diagonal of a stencil operator)
@@ -94,13 +98,13 @@ cudaError_t launch_residual(const Operator& A, const double* b, const double* x,
 // one matrix-powers level l (computes P_{l+1} and R_{l+1} when within the block size
 // read from st->sbar, or from `sbar_fixed` when > 0, with coefficients from `coef`).
 struct LevelCoef { const double* theta; const double* inv_gamma; const double* mu; };
-cudaError_t launch_mpk_level(const Operator& A, double* Y, int64_t ld, int level,
+cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level,
                              const SolveState* state, int sbar_fixed, LevelCoef coef, bool y32,
                              cudaStream_t st);
 
 // gram.cu
 int gram_blocks(int64_t n);
-cudaError_t launch_gram(const double* Y, int64_t n, int64_t ld, const int* ncols_dev, int ncols_fixed,
+cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* ncols_dev, int ncols_fixed,
                         const SolveState* state, double* partials, int nblocks, double* G, int ldg,
                         bool y32, cudaStream_t st);
 
@@ -113,15 +117,21 @@ cudaError_t launch_control(SolveState* state, const double* G, int ldg, const do
 cudaError_t launch_leja(double* t, int s, cudaStream_t st);
 
 // vec.cu
-cudaError_t launch_recombine(const SolveState* state, double* Y, int64_t ld, double* x, int64_t n,
-                             bool y32, cudaStream_t st);
+// Basis storage: y32 = false: Y is double and columns 0/1 are p and r
+// themselves; y32 = true: Y is float and p, r live in the binary64 vectors
+// p64, r64 (columns 0/1 of Y hold their binary32 roundings).
+cudaError_t launch_recombine(const SolveState* state, void* Y, int64_t ld, double* x, double* r64, double* p64,
+                             int64_t n, bool y32, cudaStream_t st);
 cudaError_t launch_init_state(SolveState* state, const Operator& A, const double* b, const double* x,
-                              double* Y, int64_t ld, double* partials, int nblocks, bool y32,
-                              cudaStream_t st);
+                              void* Y, int64_t ld, double* r64, double* p64, double* partials, int nblocks,
+                              bool y32, cudaStream_t st);
+cudaError_t launch_fp32_replacement(SolveState* state, const Operator& A, const double* b, const double* x,
+                                    void* Y, int64_t ld, double* r64, double* partials, int nblocks,
+                                    sscg_outer_record* hist, cudaStream_t st);
 cudaError_t launch_true_residual(SolveState* state, const Operator& A, const double* b, const double* x,
                                  double* rt, double* partials, int nblocks, cudaStream_t st);
-cudaError_t launch_apply_replacement(SolveState* state, const double* rt, double* Y, int64_t ld,
-                                     int64_t n, bool y32, sscg_outer_record* hist, cudaStream_t st);
+cudaError_t launch_apply_replacement(SolveState* state, const double* rt, void* Y, int64_t ld, double* r64,
+                                     double* p64, int64_t n, bool y32, sscg_outer_record* hist, cudaStream_t st);
 cudaError_t launch_final_norm(SolveState* state, const Operator& A, const double* b, const double* x,
                               double* rt, double* partials, int nblocks, cudaStream_t st);
 // HSCG

@@ -70,11 +70,15 @@ __device__ bool last_block_sum(double partial, double* partials, unsigned int* c
 }
 
 // ------------------------------------------------------------- recovery
-// x += Y x', r = Y r', p = Y p' over the first nc = 2 s_k + 1 columns; the new
-// p and r overwrite columns 0 and 1 of Y (each row reads its own row first).
+// x += Y x', r = Y r', p = Y p' over the first nc = 2 s_k + 1 columns.  With a
+// binary64 basis the new p and r overwrite columns 0 and 1 of Y (each row
+// reads its own row first); with a binary32 basis they go to the binary64
+// vectors p64, r64 and their roundings to columns 0 and 1.
+template <typename T>
 __global__ void __launch_bounds__(kVecThreads) recombine_kernel(const SolveState* __restrict__ st,
-                                                                double* __restrict__ Y, int64_t ld,
-                                                                double* __restrict__ x, int64_t n) {
+                                                                T* __restrict__ Y, int64_t ld,
+                                                                double* __restrict__ x, double* __restrict__ r64,
+                                                                double* __restrict__ p64, int64_t n) {
   if (st->done) return;
   const int nc = st->nc;
   __shared__ double cx[kMaxCols], cr[kMaxCols], cp[kMaxCols];
@@ -87,28 +91,38 @@ __global__ void __launch_bounds__(kVecThreads) recombine_kernel(const SolveState
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double sx = 0.0, sr = 0.0, sp = 0.0;
     for (int c = 0; c < nc; ++c) {
-      const double y = Y[(int64_t)c * ld + i];
+      const double y = (double)Y[(int64_t)c * ld + i];
       sx = fma(y, cx[c], sx);
       sr = fma(y, cr[c], sr);
       sp = fma(y, cp[c], sp);
     }
     x[i] += sx;
-    Y[i] = sp;
-    Y[ld + i] = sr;
+    if (r64 != nullptr) {
+      r64[i] = sr;
+      p64[i] = sp;
+    }
+    Y[i] = (T)sp;
+    Y[ld + i] = (T)sr;
   }
 }
 
-// r0 = b - A x0 into column 1 (and p0 = r0 into column 0) is done by the
-// residual kernel; this kernel copies it and forms ||b||.
+// After r0 = b - A x0 has been formed: p0 = r0 into the basis columns (and
+// the binary64 vectors of a binary32 basis), and ||b||.
+template <typename T>
 __global__ void __launch_bounds__(kVecThreads) init_norms_kernel(SolveState* __restrict__ st,
                                                                  const double* __restrict__ b,
-                                                                 double* __restrict__ Y, int64_t ld, int64_t n,
+                                                                 const double* __restrict__ r0,
+                                                                 T* __restrict__ Y, int64_t ld,
+                                                                 double* __restrict__ p64, int64_t n,
                                                                  double* __restrict__ partials) {
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double bi = b[i];
     s = fma(bi, bi, s);
-    Y[i] = Y[ld + i];
+    const double ri = r0[i];
+    if (p64 != nullptr) p64[i] = ri;
+    Y[i] = (T)ri;
+    Y[ld + i] = (T)ri;
   }
   double tot;
   if (last_block_sum(s, partials, &st->red_counter, &tot) && threadIdx.x == 0) {
@@ -142,24 +156,60 @@ __global__ void __launch_bounds__(kVecThreads) true_norm_kernel(SolveState* __re
   if (last_block_sum(s, partials, &st->red_counter, &tot) && threadIdx.x == 0) {
     st->rt2 = tot;
     if (!force) {
-      if (sqrt(tot) / st->normb <= st->tol) {
+      const double rel = sqrt(tot) / st->normb;
+      if (rel <= st->tol) {
         st->done = 1;
         st->status = SSCG_OK;
+      } else if (st->prev_fail > 0.0 && rel >= 0.5 * st->prev_fail) {
+        st->done = 1;  // stagnation above tol: the attainable accuracy is reached
+        st->status = SSCG_NOT_CONVERGED;
       } else {
+        st->prev_fail = rel;
         st->replace_pending = 1;
       }
     }
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kVecThreads) replacement_kernel(const SolveState* __restrict__ st,
                                                                   const double* __restrict__ rt,
-                                                                  double* __restrict__ Y, int64_t ld, int64_t n) {
+                                                                  T* __restrict__ Y, int64_t ld,
+                                                                  double* __restrict__ r64, double* __restrict__ p64,
+                                                                  int64_t n) {
   if (st->done || !st->replace_pending) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = rt[i];
-    Y[i] = v;
-    Y[ld + i] = v;
+    if (r64 != nullptr) {
+      r64[i] = v;
+      p64[i] = v;
+    }
+    Y[i] = (T)v;
+    Y[ld + i] = (T)v;
+  }
+}
+
+// FP32-stored basis: r := b - A x (already in r64) rounded into column 1, and
+// the relative residual at this replacement; p is kept.
+__global__ void __launch_bounds__(kVecThreads) fp32_replace_kernel(SolveState* __restrict__ st,
+                                                                   const double* __restrict__ r64,
+                                                                   float* __restrict__ Y, int64_t ld, int64_t n,
+                                                                   double* __restrict__ partials,
+                                                                   sscg_outer_record* __restrict__ hist) {
+  if (st->done || !st->fp32_replace_pending) return;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = r64[i];
+    Y[ld + i] = (float)v;
+    s = fma(v, v, s);
+  }
+  double tot;
+  if (last_block_sum(s, partials, &st->red_counter, &tot) && threadIdx.x == 0) {
+    st->rho_last = sqrt(tot) / st->normb;
+    st->fp32_replace_pending = 0;
+    st->fp32_replacements += 1;
+    const int k = st->k - 1;
+    if (hist != nullptr && k >= 0 && k < st->hist_cap) hist[k].replaced |= 2;
   }
 }
 
@@ -173,7 +223,7 @@ __global__ void end_of_loop_kernel(SolveState* st, sscg_outer_record* hist) {
     st->psi = 1.0;
     st->replacements += 1;
     const int k = st->k - 1;
-    if (hist != nullptr && k >= 0 && k < st->hist_cap) hist[k].replaced = 1;
+    if (hist != nullptr && k >= 0 && k < st->hist_cap) hist[k].replaced |= 1;
   }
   if (st->k >= st->max_outer) {
     st->status = SSCG_NOT_CONVERGED;
@@ -298,10 +348,15 @@ __global__ void __launch_bounds__(kVecThreads) hscg_confirm_kernel(SolveState* _
   double tot;
   if (last_block_sum(s, partials, &st->red_counter, &tot) && threadIdx.x == 0) {
     st->rt2 = tot;
-    if (sqrt(tot) / st->normb <= st->tol) {
+    const double rel = sqrt(tot) / st->normb;
+    if (rel <= st->tol) {
       st->done = 1;
       st->status = SSCG_OK;
+    } else if (st->prev_fail > 0.0 && rel >= 0.5 * st->prev_fail) {
+      st->done = 1;  // stagnation above tol
+      st->status = SSCG_NOT_CONVERGED;
     } else {
+      st->prev_fail = rel;
       st->replace_pending = 1;
     }
   }
@@ -330,19 +385,30 @@ __global__ void hscg_replace_finish_kernel(SolveState* st) {
 
 int reduce_blocks(int64_t n) { return vec_grid(n); }
 
-cudaError_t launch_recombine(const SolveState* state, double* Y, int64_t ld, double* x, int64_t n, bool y32,
-                             cudaStream_t st) {
-  if (y32) return cudaErrorNotSupported;
-  recombine_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(state, Y, ld, x, n);
+cudaError_t launch_recombine(const SolveState* state, void* Y, int64_t ld, double* x, double* r64, double* p64,
+                             int64_t n, bool y32, cudaStream_t st) {
+  if (y32)
+    recombine_kernel<float><<<vec_grid(n), kVecThreads, 0, st>>>(state, static_cast<float*>(Y), ld, x, r64, p64, n);
+  else
+    recombine_kernel<double><<<vec_grid(n), kVecThreads, 0, st>>>(state, static_cast<double*>(Y), ld, x, nullptr,
+                                                                  nullptr, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_state(SolveState* state, const Operator& A, const double* b, const double* x, double* Y,
-                              int64_t ld, double* partials, int nblocks, bool y32, cudaStream_t st) {
-  if (y32) return cudaErrorNotSupported;
-  cudaError_t e = launch_residual(A, b, x, Y + ld, st);  // r0 into column 1
-  if (e != cudaSuccess) return e;
-  init_norms_kernel<<<nblocks, kVecThreads, 0, st>>>(state, b, Y, ld, A.n, partials);
+cudaError_t launch_init_state(SolveState* state, const Operator& A, const double* b, const double* x, void* Y,
+                              int64_t ld, double* r64, double* p64, double* partials, int nblocks, bool y32,
+                              cudaStream_t st) {
+  if (y32) {
+    cudaError_t e = launch_residual(A, b, x, r64, st);  // r0 in binary64
+    if (e != cudaSuccess) return e;
+    init_norms_kernel<float><<<nblocks, kVecThreads, 0, st>>>(state, b, r64, static_cast<float*>(Y), ld, p64, A.n,
+                                                              partials);
+  } else {
+    double* Yd = static_cast<double*>(Y);
+    cudaError_t e = launch_residual(A, b, x, Yd + ld, st);  // r0 into column 1
+    if (e != cudaSuccess) return e;
+    init_norms_kernel<double><<<nblocks, kVecThreads, 0, st>>>(state, b, Yd + ld, Yd, ld, nullptr, A.n, partials);
+  }
   zero_x_kernel<<<vec_grid(A.n), kVecThreads, 0, st>>>(state, const_cast<double*>(x), A.n);
   return cudaGetLastError();
 }
@@ -367,13 +433,26 @@ cudaError_t launch_final_norm(SolveState* state, const Operator& A, const double
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply_replacement(SolveState* state, const double* rt, double* Y, int64_t ld, int64_t n,
-                                     bool y32, sscg_outer_record* hist, cudaStream_t st) {
-  if (y32) return cudaErrorNotSupported;
-  replacement_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(state, rt, Y, ld, n);
+cudaError_t launch_apply_replacement(SolveState* state, const double* rt, void* Y, int64_t ld, double* r64,
+                                     double* p64, int64_t n, bool y32, sscg_outer_record* hist, cudaStream_t st) {
+  if (y32)
+    replacement_kernel<float><<<vec_grid(n), kVecThreads, 0, st>>>(state, rt, static_cast<float*>(Y), ld, r64, p64,
+                                                                   n);
+  else
+    replacement_kernel<double><<<vec_grid(n), kVecThreads, 0, st>>>(state, rt, static_cast<double*>(Y), ld, nullptr,
+                                                                    nullptr, n);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   end_of_loop_kernel<<<1, 32, 0, st>>>(state, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp32_replacement(SolveState* state, const Operator& A, const double* b, const double* x, void* Y,
+                                    int64_t ld, double* r64, double* partials, int nblocks, sscg_outer_record* hist,
+                                    cudaStream_t st) {
+  cudaError_t e = launch_residual(A, b, x, r64, st, state, 3);
+  if (e != cudaSuccess) return e;
+  fp32_replace_kernel<<<nblocks, kVecThreads, 0, st>>>(state, r64, static_cast<float*>(Y), ld, A.n, partials, hist);
   return cudaGetLastError();
 }
 

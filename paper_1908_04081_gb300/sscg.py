@@ -45,7 +45,8 @@ class OuterRecord(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("inner_iters", C.c_int),
-                ("host_syncs", C.c_int), ("replacements", C.c_int), ("kernel_launches", C.c_int),
+                ("host_syncs", C.c_int), ("replacements", C.c_int), ("fp32_replacements", C.c_int),
+                ("kernel_launches", C.c_int),
                 ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("c_last", C.c_double),
                 ("true_relres", C.c_double), ("upd_relres", C.c_double),
                 ("t_mpk_ms", C.c_double), ("t_gram_ms", C.c_double), ("t_kappa_ms", C.c_double),
@@ -290,7 +291,8 @@ def history(st: Stats) -> list[dict]:
     out = []
     for k in range(st.hist_len):
         r = st.hist[k]
-        out.append(dict(sbar=r.sbar, stilde=r.stilde, sk=r.sk, replaced=r.replaced, c_start=r.c_start,
+        out.append(dict(sbar=r.sbar, stilde=r.stilde, sk=r.sk, replaced=bool(r.replaced & 1),
+                        fp32_replaced=bool(r.replaced & 2), c_start=r.c_start,
                         c=r.c_end, phi=r.phi, lmin=r.lmin, lmax=r.lmax, relres_est=r.relres_est,
                         kappa=[r.kappa[i] for i in range(r.sbar + 1)]))
     return out

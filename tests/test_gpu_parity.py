@@ -326,3 +326,33 @@ def test_full_size_varcoef3d_160(pkg):
         if ref:
             assert abs(st.outer_iters - ref["sstep_outer"]) <= 0.1 * ref["sstep_outer"]
             assert abs(st.inner_iters - ref["sstep_inner"]) <= 0.1 * ref["sstep_inner"]
+
+
+@pytest.mark.parametrize("name", ["poisson", "varcoef3d"])
+def test_fp32_stored_basis(pkg, name):
+    """Basis Y stored in binary32 (the recurrence, G, x, r, p in binary64) with
+    residual replacement; against the oracle's run of the same variant, and its
+    error against the binary64 solve reported through the assertions."""
+    if name == "poisson":
+        A, b, x0, _ = gen.config_problem("poisson2d_64")
+        M = as_matrix(A)
+        s = pkg.Solver.csr(A.rowptr, A.col, A.val)
+        smax, basis = 8, "chebyshev"
+    else:
+        st_ = gen.varcoef_stencil((32, 32, 32), seed=1001)
+        b = gen.random_rhs(st_.n, 8)
+        x0 = np.zeros(st_.n)
+        M = as_matrix(st_)
+        s = stencil_solver(pkg, st_)
+        smax, basis = 16, "newton"
+    x_o, info = cg.sstep_cg(M, b, x0, 1e-10, cg.Options(smax=smax, basis=basis, y_fp32=True))
+    x64, info64 = cg.sstep_cg(M, b, x0, 1e-10, cg.Options(smax=smax, basis=basis))
+    xt = dev(x0)
+    st = s.solve(dev(b), xt, tol=1e-10, s_max=smax, basis=basis, hist_cap=4000, y_fp32=1)
+    xg = xt.cpu().numpy()
+    compare_solves(xg, st, pkg.sscg.history(st), x_o, info, 1e-10, strict=(name == "poisson"))
+    assert abs(st.fp32_replacements - info["fp32_replacements"]) <= 1
+    assert st.fp32_replacements >= 1
+    # the binary32 basis costs at most 30 % more iterations than binary64 here
+    assert st.inner_iters <= 1.3 * info64["inner"]
+    assert np.linalg.norm(xg - x64) / np.linalg.norm(x64) <= 1e-7
