@@ -203,6 +203,22 @@ int sscg_build_basis(sscg_t h, const double* p, const double* r, int s, const do
  * allocated and freed inside the call. */
 int sscg_gram(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, void* cuda_stream);
 
+/* Same result as sscg_gram, for callers that cannot allocate device memory
+ * during a call: programs whose device-memory budget is fixed at start-up,
+ * and hosts whose own memory manager owns the device memory (a cudaMalloc or
+ * cudaFree inside a library call bypasses it, and cudaFree waits for the whole
+ * device).  The paper has no counterpart: this is an interface variant.
+ * The block partial sums live in a fixed device array inside the library
+ * (304 x 561 doubles, 1.36 MB, held by every device that loads the library
+ * until exit); the call allocates nothing.  n is unlimited; ncols must be in
+ * [1, 33], else SSCG_ERR_INVALID_ARG.  The first call on a device looks up the
+ * array's device address (with that device current), so make that first call
+ * before any stream capture.  All calls on a device share the array: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  Enqueued on cuda_stream (NULL: legacy
+ * default stream); the call does not wait for the result. */
+int sscg_gram_noalloc(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, void* cuda_stream);
+
 /* kappa_l ~ sqrt(kappa(G_l)) for the leading (2l+1) blocks of G, l = 1..sbar
  * (Section 3), from the extreme eigenvalues of each block.  G: device,
  * ldg x ldg row major, ldg >= 2*sbar+1.  kappa, lmin, lmax: device arrays of

@@ -21,7 +21,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relax
 # the control step evaluates its scalar formulas without FMA contraction so that
 # its decisions follow the written operation order
 PER_FILE = {"control.cu": ["-fmad=false"]}
-SOURCES = ["api.cu", "ops_operator.cu", "gram.cu", "control.cu", "vec.cu", "adjoint.cu"]
+SOURCES = ["api.cu", "ops_operator.cu", "gram.cu", "control.cu", "vec.cu", "adjoint.cu", "gram_noalloc.cu"]
 
 
 def nvcc() -> str:

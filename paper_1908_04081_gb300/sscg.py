@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sscg_spmv": (C.c_int, [_P, _P, _P]),
         "sscg_build_basis": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, _P, _I64]),
         "sscg_gram": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _P]),
+        "sscg_gram_noalloc": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _P]),
         "sscg_kappa": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, _P, _P, _P, _P]),
         "sscg_leja": (C.c_int, [C.c_int, _P]),
         "sscg_stencil_face_grad": (C.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -263,6 +264,12 @@ def sscg_build_basis(h: int, p, r, s: int, theta, gamma, mu, Y, ldy: int) -> Non
 
 def sscg_gram(Y, n: int, ldy: int, ncols: int, G, stream=None) -> None:
     _check(load_library().sscg_gram(_f64(Y), n, ldy, ncols, _f64(G), _stream_ptr(stream)), "sscg_gram")
+
+
+def sscg_gram_noalloc(Y, n: int, ldy: int, ncols: int, G, stream=None) -> None:
+    """G = Y^T Y with the library's fixed scratch (no device allocation)."""
+    _check(load_library().sscg_gram_noalloc(_f64(Y), n, ldy, ncols, _f64(G), _stream_ptr(stream)),
+           "sscg_gram_noalloc")
 
 
 def sscg_kappa(G, ldg: int, sbar: int, kappa_cut: float, kappa, lmin, lmax, stream=None) -> None:
