@@ -33,6 +33,12 @@ WORKLOADS = {
                                "b~N(0,1), x0=0", smax=16, basis="newton", tol=1e-10),
     "poisson2d_64": dict(desc="FP64 2D 5-pt Poisson 64x64 CSR (N=4096), b=A x*, x*~U(-1,1), x0=0",
                          smax=8, basis="chebyshev", tol=1e-10),
+    "rgg_2m": dict(desc="FP64 CSR: Laplacian of a 3D random geometric graph, N=2,000,000, ~27 nnz/row, RCM order, "
+                        "+1e-4*mean-degree*I, diagonal scaling 10^U(0,3); FP64 basis vs FP32-stored basis",
+                   smax=16, basis="newton", tol=1e-10),
+    "batched_256": dict(desc="256 independent 2D/3D log-normal-coefficient Poisson systems, N log-uniform in "
+                             "[1e3, 2.6e5], 1-8 right-hand sides each, one graph launch, sigma per system by the "
+                             "autotuner", smax=16, basis="newton", tol=1e-10),
     # a smaller grid of the same stencil family, used for kernel profiles
     "varcoef3d_96": dict(desc="FP64 3D 7-pt var-coef diffusion 96^3 (N=884,736), k=exp(N(0,1)) per face, "
                               "b~N(0,1), x0=0", smax=16, basis="newton", tol=1e-10, base="varcoef3d_160",
@@ -168,6 +174,104 @@ def run_reference(args, cfg):
     print(json.dumps(line))
 
 
+def run_rgg(args, cfg, pkg, torch, dev):
+    """FP64-stored vs FP32-stored basis on the CSR random-geometric-graph workload."""
+    import numpy as np
+    op, b_np, x0_np, _ = load_inputs(args.workload)
+    n = b_np.size
+    solver = pkg.Solver.csr(op.rowptr, op.col, op.val)
+    b = torch.tensor(b_np, dtype=torch.float64, device=dev)
+    out = {}
+    for y32 in (0, 1):
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            x.zero_()
+            solver.solve(b, x, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], y_fp32=y32)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        sts = []
+        for _ in range(args.steps):
+            x.zero_()
+            sts.append(solver.solve(b, x, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], y_fp32=y32,
+                                    hist_cap=20000))
+        e1.record()
+        torch.cuda.synchronize()
+        el = e0.elapsed_time(e1) / 1e3
+        st = sts[-1]
+        h = pkg.sscg.history(st)
+        out[y32] = dict(value=args.steps / el, ms_per_step=el / args.steps * 1e3, outer=st.outer_iters,
+                        inner=st.inner_iters, status=st.status, true_relres=st.true_relres,
+                        mean_sk=float(np.mean([r["sk"] for r in h])) if h else None,
+                        fp32_replacements=st.fp32_replacements, x=x.clone())
+    err = float(torch.linalg.norm(out[1]["x"] - out[0]["x"]) / torch.linalg.norm(out[0]["x"]))
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    hs = solver.hscg(b, x, tol=cfg["tol"])
+    torch.cuda.synchronize()
+    th = time.perf_counter() - t
+    for d in out.values():
+        d.pop("x")
+    line = {"metric": METRIC, "value": out[0]["value"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out[0]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["desc"], "s_max": cfg["smax"], "basis": cfg["basis"], "tol": cfg["tol"],
+                       "nnz": int(op.val.size)},
+            "fp64_basis": out[0], "fp32_basis": out[1], "fp32_vs_fp64_solution_rel_diff": err,
+            "hscg": {"value": 1.0 / th, "unit": "solves/s", "iters": hs.inner_iters, "status": hs.status,
+                     "true_relres": hs.true_relres}}
+    print(json.dumps(line))
+
+
+def run_batched(args, cfg, pkg, torch, dev):
+    """The batched workload: autotune sigma per size class, then one batched solve per step."""
+    import numpy as np
+    from sscg_inputs import generators as gen
+    systems = gen.batched_stencils(256, 1003)
+    solvers = [pkg.Solver.stencil(st.kx, st.ky, st.kz) for st, _ in systems]
+    nrhs = [B.shape[0] for _, B in systems]
+    b_np = np.concatenate([B.ravel() for _, B in systems])
+    b = torch.tensor(b_np, dtype=torch.float64, device=dev)
+    # autotuner: one trial per size class (dimension, N to the nearest power of 4)
+    classes = {}
+    t_tune = time.perf_counter()
+    for i, (st, B) in enumerate(systems):
+        key = (st.dim, int(round(math.log(st.n, 4))))
+        if key not in classes:
+            bi = torch.tensor(B[0], dtype=torch.float64, device=dev)
+            best, _ = pkg.sscg.sscg_autotune(solvers[i].h, bi, cfg["tol"], [4, 8, 12, 16], trial_outer=12,
+                                             basis=cfg["basis"])
+            classes[key] = best
+    t_tune = time.perf_counter() - t_tune
+    s_max = [classes[(st.dim, int(round(math.log(st.n, 4))))] for st, _ in systems]
+    x = torch.zeros_like(b)
+    for _ in range(args.warmup):
+        x.zero_()
+        pkg.sscg.sscg_solve_batch([s.h for s in solvers], nrhs, b, x, cfg["tol"], s_max, cfg["basis"])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        x.zero_()
+        rc, stats = pkg.sscg.sscg_solve_batch([s.h for s in solvers], nrhs, b, x, cfg["tol"], s_max, cfg["basis"])
+    e1.record()
+    torch.cuda.synchronize()
+    el = e0.elapsed_time(e1) / 1e3
+    pairs = sum(nrhs)
+    line = {"metric": METRIC, "value": pairs * args.steps / el, "unit": "system-rhs solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["desc"], "systems": len(systems), "pairs": pairs,
+                       "unknowns": int(b_np.size), "sigma_by_class": {f"{k[0]}d_4^{k[1]}": v for k, v in classes.items()},
+                       "autotune_s": t_tune},
+            "status": rc, "converged": stats["converged"], "outer_loops": stats["outer_loops"],
+            "inner_iters_total": stats["inner_iters"], "max_true_relres": stats["max_true_relres"],
+            "graph_launches": stats["graph_launches"], "host_syncs": stats["host_syncs"],
+            "gpu_launches": stats["kernel_launches"]}
+    print(json.dumps(line))
+
+
 def main():
     args = parse_args()
     cfg = WORKLOADS[args.workload]
@@ -189,6 +293,12 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
+    if args.workload in ("rgg_2m", "batched_256"):
+        if rank == 0:
+            (run_rgg if args.workload == "rgg_2m" else run_batched)(args, cfg, pkg, torch, dev)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     op, b_np, x0_np, _ = load_inputs(args.workload)
     n = b_np.size

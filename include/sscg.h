@@ -177,6 +177,53 @@ int sscg_solve_host(sscg_t h, const double* b_host, double* x_host, double tol, 
 int sscg_solve_hscg(sscg_t h, const double* b, double* x, double tol, int max_iters,
                     sscg_stats* stats);
 
+/* Statistics of a batched solve.  The per-pair arrays are caller-owned and
+ * optional (length = total number of right-hand sides when non-NULL). */
+typedef struct {
+  int npairs;            /* (system, right-hand side) pairs solved */
+  int converged;         /* pairs that reached tol (true residual) */
+  int outer_loops;       /* outer loops run by the batch (the slowest pair's count) */
+  int host_syncs;        /* host waits inside the call */
+  int kernel_launches;   /* kernels launched (graph nodes counted once per replay) */
+  int graph_launches;    /* CUDA graph launches */
+  int64_t inner_iters;   /* sum over pairs */
+  double max_true_relres;/* largest ||b - A x||/||b|| over the pairs */
+  int* pair_status;      /* optional, per pair */
+  int* pair_outer;       /* optional, per pair */
+  int* pair_inner;       /* optional, per pair */
+} sscg_batch_stats;
+
+/* Solve many independent systems, each with several right-hand sides, by
+ * Algorithm 5 in one batched launch sequence: every (system, right-hand side)
+ * pair keeps its own s-step state (its own s-bar_k, s-tilde_k, basis
+ * parameters, Ritz estimates and c) while all pairs advance through the same
+ * kernels, one outer loop at a time; the loop runs inside one CUDA graph
+ * launch (a device-side WHILE node repeats the outer loop until every pair
+ * has finished), so the host does not take part.
+ * systems: nsys handles (their operators are used, not modified).
+ * nrhs: right-hand sides per system (>= 0).  b, x: device arrays holding the
+ * pairs back to back, system-major then right-hand-side-major: pair (s, k) at
+ * offset sum_{s' < s} nrhs[s'] n_{s'} + k n_s; x holds the initial guesses on
+ * entry and the solutions on exit.  s_max: per-system sigma in
+ * [1, SSCG_MAX_S] (e.g. from sscg_autotune).  opts: as for sscg_solve
+ * (y_fp32 unsupported here; use_graph = 0 replaces the WHILE node by host
+ * polling every check_every outer loops).  Returns SSCG_OK if every pair
+ * converged, SSCG_NOT_CONVERGED / SSCG_BREAKDOWN if some did not, or a
+ * negative error.  Device memory for the batch is allocated for the call. */
+int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double* x,
+                     double tol, const int* s_max, sscg_basis basis, const sscg_opts* opts,
+                     sscg_batch_stats* stats, void* cuda_stream);
+
+/* Autotuner for sigma (the paper leaves sigma to "offline auto-tuning",
+ * Section 3): for each candidate sigma (ncand values in [1, SSCG_MAX_S]) run
+ * at most trial_outer outer loops of Algorithm 5 with tolerance tol on the
+ * handle's operator and right-hand side b (device, length n) from x0 = 0,
+ * time them with CUDA events on the handle's stream, and return in *best the
+ * candidate with the least device time per inner iteration.  times
+ * (optional, host, length ncand) receives milliseconds per inner iteration. */
+int sscg_autotune(sscg_t h, const double* b, double tol, const int* candidates, int ncand, int trial_outer,
+                  sscg_basis basis, int* best, double* times);
+
 /* Ritz estimates (Algs. 3-4, eq. lest) of the handle's last s-step solve. */
 int sscg_ritz(sscg_t h, double* lmin, double* lmax);
 

@@ -197,6 +197,8 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
   return SSCG_OK;
 }
 
+// The whole solve loop as one graph: a kernel arms the loop condition, then a
+// WHILE node repeats one outer loop until the device sets done.
 int build_graph(sscg_ctx* h, int sigma, bool y32) {
   if (h->graph && h->graph_sigma == sigma && h->graph_y32 == y32) return SSCG_OK;
   if (h->graph) {
@@ -204,18 +206,52 @@ int build_graph(sscg_ctx* h, int sigma, bool y32) {
     h->graph = nullptr;
   }
   cudaGraph_t g;
-  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  CK(cudaGraphCreate(&g, 0));
+  auto fail = [&](cudaError_t e, const char* w) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, w);
+  };
+  cudaGraphConditionalHandle cond;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail(e, "cudaGraphConditionalHandleCreate");
+  if ((e = cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess)
+    return fail(e, "capture arm");
+  cudaError_t ea = launch_batch_arm(cond, h->stream);
+  cudaGraph_t tmp;
+  e = cudaStreamEndCapture(h->stream, &tmp);
+  if (ea != cudaSuccess) return fail(ea, "arm kernel");
+  if (e != cudaSuccess) return fail(e, "end capture arm");
+  size_t nn = 1;
+  cudaGraphNode_t arm_node;
+  if ((e = cudaGraphGetNodes(g, &arm_node, &nn)) != cudaSuccess) return fail(e, "cudaGraphGetNodes");
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if ((e = cudaGraphAddNode(&wnode, g, &arm_node, nullptr, 1, &cp)) != cudaSuccess) return fail(e, "while node");
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess)
+    return fail(e, "capture body");
   int nl = 0;
   int rc = enqueue_body(h, sigma, y32, h->stream, nullptr, &nl);
-  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
-  if (rc) return rc;
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaError_t ec = rc ? cudaSuccess : launch_solve_cond(h->state.p, cond, h->stream);
+  e = cudaStreamEndCapture(h->stream, &tmp);
+  if (rc) {
+    cudaGraphDestroy(g);
+    return rc;
+  }
+  if (ec != cudaSuccess) return fail(ec, "cond kernel");
+  if (e != cudaSuccess) return fail(e, "end capture body");
   e = cudaGraphInstantiate(&h->graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   h->graph_sigma = sigma;
   h->graph_y32 = y32;
-  h->graph_launches = nl;
+  h->graph_launches = nl + 1;
   return SSCG_OK;
 }
 
@@ -462,12 +498,13 @@ int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg
     for (auto& e : evs) CK(cudaEventCreate(&e));
   }
   int bodies = 0;
-  while (true) {
+  if (graph) {
+    // one launch runs the whole solve; the host waits once, at the end
+    CK(cudaGraphLaunch(h->graph, st));
+  }
+  while (!graph) {
     for (int b2 = 0; b2 < every; ++b2) {
-      if (graph) {
-        CK(cudaGraphLaunch(h->graph, st));
-        launches += h->graph_launches;
-      } else {
+      {
         std::vector<cudaEvent_t> sub;
         if (prof) sub.assign(evs.begin() + 7 * b2, evs.begin() + 7 * b2 + 7);
         int nl = 0;
@@ -490,6 +527,7 @@ int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg
     if (h->host_state->done) break;
   }
   for (auto& e : evs) cudaEventDestroy(e);
+  if (graph) launches += 1;  // the arm kernel; bodies are counted from the outer-loop count below
   // final true residual for the statistics
   CK(launch_final_norm(h->state.p, h->op, h->b.p, h->x.p, h->rt.p, h->partials.p, reduce_blocks(n), st));
   launches += 2;
@@ -501,6 +539,7 @@ int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg
   ++host_syncs;
   const SolveState s = s0;
   const int outer = s.k;
+  if (graph) launches += std::max(outer, 1) * h->graph_launches;  // one body per outer loop
   const int nh = std::min(outer, hist_cap);
   if (nh > 0) {
     hh.resize(nh);
@@ -595,21 +634,68 @@ int sscg_solve_hscg(sscg_t h, const double* b, double* x, double tol, int max_it
   const int nb = reduce_blocks(n);
   CK(launch_hscg_init(h->state.p, h->op, h->b.p, h->x.p, h->r.p, h->p.p, h->partials.p, nb, st));
   int launches = 2, host_syncs = 1;
-  const int per_check = 8, checks_per_poll = 4;
-  while (true) {
-    for (int c = 0; c < checks_per_poll; ++c) {
-      CK(launch_hscg_check(h->state.p, h->op, h->b.p, h->x.p, h->r.p, h->p.p, h->rt.p, h->partials.p, nb, st));
-      for (int it = 0; it < per_check; ++it)
-        CK(launch_hscg_iteration(h->state.p, h->op, h->x.p, h->r.p, h->p.p, h->q.p, h->partials.p, nb, st));
-      launches += 4 + 4 * per_check;
-    }
-    CK(launch_hscg_check(h->state.p, h->op, h->b.p, h->x.p, h->r.p, h->p.p, h->rt.p, h->partials.p, nb, st));
-    launches += 4;
-    CK(cudaMemcpyAsync(h->host_state, h->state.p, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    ++host_syncs;
-    if (h->host_state->done) break;
+  // Iterations run inside one graph: WHILE (not done) { 8 iterations, then the
+  // true-residual confirmation }.  Kernels of iterations past convergence exit
+  // at once.
+  const int per_check = 8;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  int body_kernels = 0;
+  {
+    cudaError_t e;
+    auto fail = [&](cudaError_t er, const char* w) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(er, w);
+    };
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return fail(e, "cudaGraphCreate");
+    cudaGraphConditionalHandle cond;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+      return fail(e, "cond handle");
+    if ((e = cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+      return fail(e, "capture arm");
+    cudaError_t ea = launch_batch_arm(cond, st);
+    cudaGraph_t tmp;
+    e = cudaStreamEndCapture(st, &tmp);
+    if (ea != cudaSuccess) return fail(ea, "arm");
+    if (e != cudaSuccess) return fail(e, "end capture arm");
+    size_t nn = 1;
+    cudaGraphNode_t arm_node;
+    if ((e = cudaGraphGetNodes(g, &arm_node, &nn)) != cudaSuccess) return fail(e, "nodes");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if ((e = cudaGraphAddNode(&wnode, g, &arm_node, nullptr, 1, &cp)) != cudaSuccess) return fail(e, "while node");
+    if ((e = cudaStreamBeginCaptureToGraph(st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return fail(e, "capture body");
+    cudaError_t eb = cudaSuccess;
+    for (int it = 0; it < per_check && eb == cudaSuccess; ++it)
+      eb = launch_hscg_iteration(h->state.p, h->op, h->x.p, h->r.p, h->p.p, h->q.p, h->partials.p, nb, st);
+    if (eb == cudaSuccess)
+      eb = launch_hscg_check(h->state.p, h->op, h->b.p, h->x.p, h->r.p, h->p.p, h->rt.p, h->partials.p, nb, st);
+    if (eb == cudaSuccess) eb = launch_solve_cond(h->state.p, cond, st);
+    e = cudaStreamEndCapture(st, &tmp);
+    if (eb != cudaSuccess) return fail(eb, "hscg body");
+    if (e != cudaSuccess) return fail(e, "end capture body");
+    body_kernels = 4 * per_check + 4 + 1;
+    if ((e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess) return fail(e, "instantiate");
+    cudaGraphDestroy(g);
+    g = nullptr;
   }
+  cudaError_t el = cudaGraphLaunch(ge, st);
+  if (el != cudaSuccess) {
+    cudaGraphExecDestroy(ge);
+    return cuda_fail(el, "hscg graph launch");
+  }
+  CK(cudaMemcpyAsync(h->host_state, h->state.p, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  cudaGraphExecDestroy(ge);
+  ++host_syncs;
+  launches += 1 + ((h->host_state->h_iters + per_check - 1) / per_check + 1) * body_kernels;
   CK(launch_final_norm(h->state.p, h->op, h->b.p, h->x.p, h->rt.p, h->partials.p, nb, st));
   CK(cudaMemcpyAsync(x, h->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(h->host_state, h->state.p, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
@@ -629,6 +715,267 @@ int sscg_solve_hscg(sscg_t h, const double* b, double* x, double tol, int max_it
     stats->hist_len = 0;
   }
   return s.status;
+}
+
+
+int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double* x, double tol,
+                     const int* s_max, sscg_basis basis, const sscg_opts* opts, sscg_batch_stats* stats,
+                     void* cuda_stream) {
+  if (!systems || nsys <= 0 || !nrhs || !b || !x || !s_max || !(tol > 0.0)) return SSCG_ERR_INVALID_ARG;
+  if (basis < SSCG_MONOMIAL || basis > SSCG_CHEBYSHEV) return SSCG_ERR_INVALID_ARG;
+  sscg_opts o;
+  sscg_opts_default(&o);
+  if (opts) o = *opts;
+  int rc = validate_opts(o);
+  if (rc) return rc;
+  if (o.y_fp32) return SSCG_ERR_UNSUPPORTED;
+  // ---- pairs, chunks and Gram blocks (host)
+  std::vector<BatchPair> pairs;
+  std::vector<int> chunk_pair, gblk_pair, pair_sigma;
+  int64_t off = 0;
+  int sigma_max = 1;
+  for (int s = 0; s < nsys; ++s) {
+    if (!systems[s] || nrhs[s] < 0 || s_max[s] < 1 || s_max[s] > kMaxS) return SSCG_ERR_INVALID_ARG;
+    const int64_t n = systems[s]->n;
+    for (int k = 0; k < nrhs[s]; ++k) {
+      BatchPair bp;
+      bp.op = systems[s]->op;
+      bp.off = off;
+      bp.n = n;
+      bp.chunk0 = (int)chunk_pair.size();
+      bp.nchunk = (int)((n + kBatchChunk - 1) / kBatchChunk);
+      bp.gblk0 = (int)gblk_pair.size();
+      bp.ngblk = (int)((n + kBatchGramRows - 1) / kBatchGramRows);
+      const int j = (int)pairs.size();
+      for (int c = 0; c < bp.nchunk; ++c) chunk_pair.push_back(j);
+      for (int g = 0; g < bp.ngblk; ++g) gblk_pair.push_back(j);
+      pairs.push_back(bp);
+      pair_sigma.push_back(s_max[s]);
+      sigma_max = std::max(sigma_max, s_max[s]);
+      off += n;
+    }
+  }
+  const int P = (int)pairs.size();
+  if (P == 0) return SSCG_OK;
+  const int64_t total = off;
+  const int64_t LD = round_up(total, 32);
+  const int hist_cap = 0;
+  // ---- device buffers for the call
+  DevBuf<BatchPair> d_pairs;
+  DevBuf<int> d_cp, d_gp;
+  DevBuf<SolveState> d_st;
+  DevBuf<double> d_G, d_Y, d_part, d_rt, d_leja;
+  DevBuf<unsigned int> d_cnt;
+  auto release = [&]() {
+    d_pairs.release(); d_cp.release(); d_gp.release(); d_st.release(); d_G.release(); d_Y.release();
+    d_part.release(); d_rt.release(); d_leja.release(); d_cnt.release();
+  };
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int result = SSCG_OK;
+  std::vector<SolveState> hs(P);
+  int launches = 0, host_syncs = 0, graph_launches = 0;
+  unsigned int bodies_run = 0;
+  do {
+    cudaError_t e;
+#define BK(call)                                  \
+  if ((e = (call)) != cudaSuccess) {              \
+    result = cuda_fail(e, #call);                 \
+    break;                                        \
+  }
+    BK(d_pairs.ensure(P));
+    BK(d_cp.ensure(chunk_pair.size()));
+    BK(d_gp.ensure(gblk_pair.size()));
+    BK(d_st.ensure(P));
+    BK(d_G.ensure((size_t)P * kMaxCols * kMaxCols));
+    BK(d_Y.ensure((size_t)LD * (2 * sigma_max + 1)));
+    BK(d_part.ensure(std::max(gblk_pair.size() * (size_t)kMaxPairs, chunk_pair.size())));
+    BK(d_rt.ensure(total));
+    BK(d_leja.ensure(kMaxS));
+    BK(d_cnt.ensure(2));
+    BK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    BK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    BK(cudaEventRecord(ev, (cudaStream_t)cuda_stream));
+    BK(cudaStreamWaitEvent(st, ev, 0));
+    for (int j = 0; j < P; ++j) fill_state_config(hs[j], pair_sigma[j], tol, (int)basis, o, hist_cap);
+    BK(cudaMemcpyAsync(d_pairs.p, pairs.data(), P * sizeof(BatchPair), cudaMemcpyHostToDevice, st));
+    BK(cudaMemcpyAsync(d_cp.p, chunk_pair.data(), chunk_pair.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    BK(cudaMemcpyAsync(d_gp.p, gblk_pair.data(), gblk_pair.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    BK(cudaMemcpyAsync(d_st.p, hs.data(), P * sizeof(SolveState), cudaMemcpyHostToDevice, st));
+    BK(cudaMemsetAsync(d_cnt.p, 0, 2 * sizeof(unsigned int), st));
+    BK(launch_leja(d_leja.p, kMaxS, st));
+    BatchView v;
+    v.pairs = d_pairs.p;
+    v.npairs = P;
+    v.chunk_pair = d_cp.p;
+    v.nchunks = (int)chunk_pair.size();
+    v.gblk_pair = d_gp.p;
+    v.ngblk = (int)gblk_pair.size();
+    v.states = d_st.p;
+    v.G = d_G.p;
+    v.hist = nullptr;
+    v.hist_cap = 0;
+    v.active = d_cnt.p;
+    v.bodies = d_cnt.p + 1;
+    v.max_bodies = (o.max_outer > 0 ? o.max_outer : 100000) + 2;
+    BK(launch_batch_init(v, b, x, d_Y.p, LD, d_part.p, st));
+    launches += 3;
+    auto body = [&](cudaGraphConditionalHandle cond, int use_cond) -> cudaError_t {
+      cudaError_t e2;
+      if ((e2 = launch_batch_begin(v, st)) != cudaSuccess) return e2;
+      for (int l = 0; l < sigma_max; ++l)
+        if ((e2 = launch_batch_mpk(v, d_Y.p, LD, l, st)) != cudaSuccess) return e2;
+      if ((e2 = launch_batch_gram(v, d_Y.p, LD, d_part.p, st)) != cudaSuccess) return e2;
+      if ((e2 = launch_batch_kappa(v, sigma_max, st)) != cudaSuccess) return e2;
+      if ((e2 = launch_batch_control(v, d_leja.p, st)) != cudaSuccess) return e2;
+      if ((e2 = launch_batch_recombine(v, d_Y.p, LD, x, st)) != cudaSuccess) return e2;
+      if ((e2 = launch_batch_check(v, b, x, d_rt.p, d_Y.p, LD, d_part.p, st)) != cudaSuccess) return e2;
+      return launch_batch_end(v, cond, use_cond, st);
+    };
+    const int body_kernels = sigma_max + 9;
+    if (o.use_graph) {
+      // one graph: arm the condition, then WHILE (condition) { one outer loop }
+      BK(cudaGraphCreate(&graph, 0));
+      cudaGraphConditionalHandle cond;
+      BK(cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault));
+      BK(cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      cudaError_t ea = launch_batch_arm(cond, st);
+      cudaGraph_t tmp;
+      cudaError_t ee = cudaStreamEndCapture(st, &tmp);
+      BK(ea);
+      BK(ee);
+      size_t nn = 1;
+      cudaGraphNode_t arm_node;
+      BK(cudaGraphGetNodes(graph, &arm_node, &nn));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t wnode;
+      BK(cudaGraphAddNode(&wnode, graph, &arm_node, nullptr, 1, &cp));
+      cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+      BK(cudaStreamBeginCaptureToGraph(st, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      cudaError_t eb = body(cond, 1);
+      ee = cudaStreamEndCapture(st, &tmp);
+      BK(eb);
+      BK(ee);
+      BK(cudaGraphInstantiate(&gexec, graph, 0));
+      BK(cudaGraphLaunch(gexec, st));
+      ++graph_launches;
+    } else {
+      const int every = std::max(1, o.check_every);
+      unsigned int cnt[2] = {1u, 0u};
+      while (true) {
+        for (int i = 0; i < every; ++i) {
+          cudaError_t eb = body(cudaGraphConditionalHandle(), 0);
+          BK(eb);
+        }
+        if (result) break;
+        BK(cudaMemcpyAsync(cnt, d_cnt.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        BK(cudaStreamSynchronize(st));
+        ++host_syncs;
+        if (cnt[0] == 0u || cnt[1] >= (unsigned)v.max_bodies) break;
+      }
+      if (result) break;
+    }
+    BK(cudaMemcpyAsync(hs.data(), d_st.p, P * sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    BK(cudaMemcpyAsync(&bodies_run, d_cnt.p + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    BK(cudaStreamSynchronize(st));
+    ++host_syncs;
+    launches += (int)bodies_run * body_kernels;
+    BK(cudaEventRecord(ev, st));
+    BK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, ev, 0));
+#undef BK
+  } while (0);
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  if (st) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  if (ev) cudaEventDestroy(ev);
+  release();
+  if (result) return result;
+  int conv = 0, worst = SSCG_OK, max_outer = 0;
+  int64_t inner = 0;
+  double max_rel = 0.0;
+  for (int j = 0; j < P; ++j) {
+    const SolveState& q = hs[j];
+    const int status = q.done ? q.status : SSCG_NOT_CONVERGED;
+    if (status == SSCG_OK) ++conv;
+    else if (worst == SSCG_OK) worst = status;
+    max_outer = std::max(max_outer, q.k);
+    inner += q.m;
+    const double rel = q.normb > 0.0 ? std::sqrt(q.rt2) / q.normb : 0.0;
+    max_rel = std::max(max_rel, rel);
+    if (stats) {
+      if (stats->pair_status) stats->pair_status[j] = status;
+      if (stats->pair_outer) stats->pair_outer[j] = q.k;
+      if (stats->pair_inner) stats->pair_inner[j] = q.m;
+    }
+  }
+  if (stats) {
+    stats->npairs = P;
+    stats->converged = conv;
+    stats->outer_loops = max_outer;
+    stats->host_syncs = host_syncs;
+    stats->kernel_launches = launches;
+    stats->graph_launches = graph_launches;
+    stats->inner_iters = inner;
+    stats->max_true_relres = max_rel;
+  }
+  return worst;
+}
+
+int sscg_autotune(sscg_t h, const double* b, double tol, const int* candidates, int ncand, int trial_outer,
+                  sscg_basis basis, int* best, double* times) {
+  if (!h || !b || !(tol > 0.0) || !candidates || ncand <= 0 || trial_outer <= 0 || !best) return SSCG_ERR_INVALID_ARG;
+  for (int i = 0; i < ncand; ++i)
+    if (candidates[i] < 1 || candidates[i] > kMaxS) return SSCG_ERR_INVALID_ARG;
+  DevBuf<double> dx;
+  CK(dx.ensure(h->n));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best_t = 0.0;
+  int rc = SSCG_OK;
+  for (int i = 0; i < ncand && rc >= 0; ++i) {
+    sscg_opts o;
+    sscg_opts_default(&o);
+    o.max_outer = trial_outer;
+    sscg_stats stt;
+    std::memset(&stt, 0, sizeof(stt));
+    cudaError_t e = cudaMemsetAsync(dx.p, 0, h->n * sizeof(double), h->user_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->user_stream);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "autotune");
+      break;
+    }
+    int r = sscg_solve(h, b, dx.p, tol, candidates[i], basis, &o, &stt);
+    if (r < 0) {
+      rc = r;
+      break;
+    }
+    if ((e = cudaEventRecord(e1, h->user_stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+      rc = cuda_fail(e, "autotune");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = stt.inner_iters > 0 ? ms / stt.inner_iters : 1e30;
+    if (times) times[i] = per;
+    if (i == 0 || per < best_t) {
+      best_t = per;
+      *best = candidates[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dx.release();
+  return rc < 0 ? rc : SSCG_OK;
 }
 
 int sscg_ritz(sscg_t h, double* lmin, double* lmax) {

@@ -76,19 +76,8 @@ __device__ double warp_multisection(const double* d, const double* e2, int n, do
 // One block per l = 1..sbar: Householder tridiagonalisation of the leading
 // (2l+1) block of G, then its extreme eigenvalues by multisection;
 // kappa_l = sqrt(lmax/lmin) (Section 3: kappa(Y_l) ~ sqrt(kappa(G_l))).
-__global__ void __launch_bounds__(kKappaThreads) kappa_kernel(const double* __restrict__ G, int ldg,
-                                                              const SolveState* __restrict__ st, int sbar_fixed,
-                                                              double kappa_cut, double* __restrict__ kap,
-                                                              double* __restrict__ lmin_out,
-                                                              double* __restrict__ lmax_out) {
-  int sbar = sbar_fixed;
-  if (sbar <= 0) {
-    if (st->done) return;
-    sbar = st->sbar;
-    kappa_cut = st->kappa_cut;
-  }
-  const int l = blockIdx.x + 1;
-  if (l > sbar) return;
+__device__ void kappa_body(const double* __restrict__ G, int ldg, int l, double kappa_cut,
+                           double* __restrict__ kap, double* __restrict__ lmin_out, double* __restrict__ lmax_out) {
   const int n = 2 * l + 1;
   const int t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
@@ -218,6 +207,22 @@ __global__ void __launch_bounds__(kKappaThreads) kappa_kernel(const double* __re
     lmax_out[l] = lmx;
     kap[l] = (!(lmx > 0.0) || lmn <= kappa_cut * lmx) ? INFINITY : sqrt(lmx / lmn);
   }
+}
+
+__global__ void __launch_bounds__(kKappaThreads) kappa_kernel(const double* __restrict__ G, int ldg,
+                                                              const SolveState* __restrict__ st, int sbar_fixed,
+                                                              double kappa_cut, double* __restrict__ kap,
+                                                              double* __restrict__ lmin_out,
+                                                              double* __restrict__ lmax_out) {
+  int sbar = sbar_fixed;
+  if (sbar <= 0) {
+    if (st->done) return;
+    sbar = st->sbar;
+    kappa_cut = st->kappa_cut;
+  }
+  const int l = blockIdx.x + 1;
+  if (l > sbar) return;
+  kappa_body(G, ldg, l, kappa_cut, kap, lmin_out, lmax_out);
 }
 
 // --------------------------------------------------------------- control
@@ -361,11 +366,8 @@ __device__ void basis_update(SolveState* st, const double* leja) {
   }
 }
 
-__global__ void __launch_bounds__(kControlThreads) control_kernel(SolveState* __restrict__ st,
-                                                                  const double* __restrict__ G, int ldg,
-                                                                  const double* __restrict__ leja,
-                                                                  sscg_outer_record* __restrict__ hist) {
-  if (st->done) return;
+__device__ void control_body(SolveState* __restrict__ st, const double* __restrict__ G, int ldg,
+                             const double* __restrict__ leja, sscg_outer_record* __restrict__ hist) {
   const int t = threadIdx.x;
   __shared__ double Gs[kMaxCols][kMaxCols + 1];
   __shared__ double xc[kMaxCols], rc[kMaxCols], pc[kMaxCols], bp[kMaxCols], u[kMaxCols];
@@ -517,6 +519,35 @@ __global__ void __launch_bounds__(kControlThreads) control_kernel(SolveState* __
   }
 }
 
+__global__ void __launch_bounds__(kControlThreads) control_kernel(SolveState* __restrict__ st,
+                                                                  const double* __restrict__ G, int ldg,
+                                                                  const double* __restrict__ leja,
+                                                                  sscg_outer_record* __restrict__ hist) {
+  if (st->done) return;
+  control_body(st, G, ldg, leja, hist);
+}
+
+
+// Batched kappa: block (j, l) computes kappa_l of pair j.
+__global__ void __launch_bounds__(kKappaThreads) batch_kappa_kernel(BatchView v, int sigma_max) {
+  const int j = blockIdx.x / sigma_max;
+  const int l = blockIdx.x % sigma_max + 1;
+  SolveState* st = v.states + j;
+  if (st->done || l > st->sbar) return;
+  const double* G = v.G + (int64_t)j * kMaxCols * kMaxCols;
+  kappa_body(G, kMaxCols, l, st->kappa_cut, st->kappa, st->glmin, st->glmax);
+}
+
+// Batched control: one block per pair.
+__global__ void __launch_bounds__(kControlThreads) batch_control_kernel(BatchView v, const double* __restrict__ leja) {
+  const int j = blockIdx.x;
+  SolveState* st = v.states + j;
+  if (st->done) return;
+  const double* G = v.G + (int64_t)j * kMaxCols * kMaxCols;
+  sscg_outer_record* h = v.hist != nullptr ? v.hist + (int64_t)j * v.hist_cap : nullptr;
+  control_body(st, G, kMaxCols, leja, h);
+}
+
 // ------------------------------------------------------------------ Leja
 // Leja points of [-1, 1] (eq. newtbasis on the reference interval): t_0 = 1,
 // t_1 = -1, then the maximiser of prod |t - t_m|.  In each gap between sorted
@@ -585,6 +616,16 @@ cudaError_t launch_kappa(const double* G, int ldg, const SolveState* state, int 
 cudaError_t launch_control(SolveState* state, const double* G, int ldg, const double* leja,
                            sscg_outer_record* hist, cudaStream_t st) {
   control_kernel<<<1, kControlThreads, 0, st>>>(state, G, ldg, leja, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_kappa(const BatchView& v, int sigma_max, cudaStream_t st) {
+  batch_kappa_kernel<<<v.npairs * sigma_max, kKappaThreads, 0, st>>>(v, sigma_max);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_control(const BatchView& v, const double* leja, cudaStream_t st) {
+  batch_control_kernel<<<v.npairs, kControlThreads, 0, st>>>(v, leja);
   return cudaGetLastError();
 }
 

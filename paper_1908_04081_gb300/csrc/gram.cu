@@ -104,7 +104,88 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restri
   }
 }
 
+
+// Batched Gram: each block owns kBatchGramRows rows of one pair and writes the
+// pair's (2s-bar+1)(2s-bar+2)/2 partial sums; the reduction adds each pair's
+// block partials in a fixed order (one block per pair).
+__global__ void __launch_bounds__(kGramThreads, 2)
+batch_gram_partial_kernel(BatchView v, const double* __restrict__ Y, int64_t LD, double* __restrict__ partials) {
+  const int g = blockIdx.x;
+  const int j = v.gblk_pair[g];
+  const BatchPair& bp = v.pairs[j];
+  const SolveState* st = v.states + j;
+  if (st->done) return;
+  const int ncols = 2 * st->sbar + 1;
+  const int np = ncols * (ncols + 1) / 2;
+  const int R = kGramThreads / np;
+  const int t = threadIdx.x;
+  const bool active = t < R * np;
+  const int q = t % np;
+  const int rl = t / np;
+  int pi = 0, pj = 0;
+  pair_of(q, ncols, &pi, &pj);
+  __shared__ double tile[kGramTileRows][kMaxCols + 1];
+  __shared__ double red[kGramThreads];
+  const double* Yp = Y + bp.off;
+  const int64_t r_begin = (int64_t)(g - bp.gblk0) * kBatchGramRows;
+  int64_t r_end = r_begin + kBatchGramRows;
+  if (r_end > bp.n) r_end = bp.n;
+  double acc = 0.0;
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kGramTileRows) {
+    for (int e = t; e < kGramTileRows * ncols; e += kGramThreads) {
+      const int c = e / kGramTileRows;
+      const int r = e - c * kGramTileRows;
+      const int64_t row = r0 + r;
+      tile[r][c] = row < r_end ? __ldg(Yp + (int64_t)c * LD + row) : 0.0;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 8
+      for (int r = rl; r < kGramTileRows; r += R) acc = fma(tile[r][pi], tile[r][pj], acc);
+    }
+    __syncthreads();
+  }
+  red[t] = acc;
+  __syncthreads();
+  if (t < np) {
+    double s = 0.0;
+    for (int l = 0; l < R; ++l) s += red[l * np + t];
+    partials[(int64_t)g * kMaxPairs + t] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) batch_gram_reduce_kernel(BatchView v, const double* __restrict__ partials) {
+  const int j = blockIdx.x;
+  const BatchPair& bp = v.pairs[j];
+  const SolveState* st = v.states + j;
+  if (st->done) return;
+  const int ncols = 2 * st->sbar + 1;
+  const int np = ncols * (ncols + 1) / 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* G = v.G + (int64_t)j * kMaxCols * kMaxCols;
+  for (int q = warp; q < np; q += blockDim.x / 32) {
+    double s = 0.0;
+    for (int b = lane; b < bp.ngblk; b += 32) s += partials[(int64_t)(bp.gblk0 + b) * kMaxPairs + q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      int i, jj;
+      pair_of(q, ncols, &i, &jj);
+      G[i * kMaxCols + jj] = s;
+      G[jj * kMaxCols + i] = s;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_gram(const BatchView& v, const double* Y, int64_t LD, double* partials, cudaStream_t st) {
+  batch_gram_partial_kernel<<<v.ngblk, kGramThreads, 0, st>>>(v, Y, LD, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  batch_gram_reduce_kernel<<<v.npairs, 256, 0, st>>>(v, partials);
+  return cudaGetLastError();
+}
 
 int gram_blocks(int64_t n) {
   int64_t tiles = (n + kGramTileRows - 1) / kGramTileRows;

@@ -238,7 +238,78 @@ __global__ void __launch_bounds__(kOpThreads) stencil_diag_kernel(Operator A, do
   }
 }
 
+
+// Batched matrix-powers level: every chunk belongs to one pair, whose state
+// gives its own s-bar and recurrence coefficients (eq. rho); pairs that are
+// done or whose block is shorter than this level skip their chunks.
+__global__ void __launch_bounds__(kOpThreads) batch_mpk_kernel(BatchView v, double* __restrict__ Y, int64_t LD,
+                                                               int level) {
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    const SolveState* st = v.states + j;
+    if (st->done) continue;
+    const int sbar = st->sbar;
+    if (level >= sbar) continue;
+    const bool doR = level + 1 < sbar;
+    const double theta = st->theta[level];
+    const double ig = st->inv_gamma[level];
+    const double mu = level >= 1 ? st->mu[level - 1] : 0.0;
+    const Operator& A = bp.op;
+    double* base = Y + bp.off;
+    const double* Pl = base + (int64_t)(2 * level) * LD;
+    const double* Rl = base + (int64_t)(2 * level + 1) * LD;
+    const double* Pm = level >= 1 ? base + (int64_t)(2 * level - 2) * LD : nullptr;
+    const double* Rm = level >= 1 ? base + (int64_t)(2 * level - 1) * LD : nullptr;
+    double* Pn = base + (int64_t)(2 * level + 2) * LD;
+    double* Rn = base + (int64_t)(2 * level + 3) * LD;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
+    int64_t r1 = r0 + kBatchChunk;
+    if (r1 > bp.n) r1 = bp.n;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      double wp, wr = 0.0;
+      if (A.kind == 1) {
+        const int x = (int)(i % A.nx);
+        const int64_t t = i / A.nx;
+        const int yy = (int)(t % A.ny);
+        const int z = (int)(t / A.ny);
+        const double ds = __ldg(A.diag + i) - theta;
+        if (A.dim == 3) {
+          wp = stencil_apply<true>(A, Pl, i, x, yy, z, ds);
+          if (doR) wr = stencil_apply<true>(A, Rl, i, x, yy, z, ds);
+        } else {
+          wp = stencil_apply<false>(A, Pl, i, x, yy, z, ds);
+          if (doR) wr = stencil_apply<false>(A, Rl, i, x, yy, z, ds);
+        }
+      } else {
+        const int64_t kb = __ldg(A.rowptr + i), ke = __ldg(A.rowptr + i + 1);
+        double ap = 0.0, ar = 0.0;
+        for (int64_t k = kb; k < ke; ++k) {
+          const double a = __ldg(A.val + k);
+          const int cc = __ldg(A.col + k);
+          ap = fma(a, __ldg(Pl + cc), ap);
+          if (doR) ar = fma(a, __ldg(Rl + cc), ar);
+        }
+        wp = fma(-theta, __ldg(Pl + i), ap);
+        wr = fma(-theta, __ldg(Rl + i), ar);
+      }
+      if (mu != 0.0) wp = fma(-mu, __ldg(Pm + i), wp);
+      Pn[i] = wp * ig;
+      if (doR) {
+        if (mu != 0.0) wr = fma(-mu, __ldg(Rm + i), wr);
+        Rn[i] = wr * ig;
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_mpk(const BatchView& v, double* Y, int64_t LD, int level, cudaStream_t st) {
+  int g = v.nchunks < 152 * 8 ? v.nchunks : 152 * 8;
+  batch_mpk_kernel<<<g < 1 ? 1 : g, kOpThreads, 0, st>>>(v, Y, LD, level);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_stencil_diag(const Operator& A, double* diag, cudaStream_t st) {
   stencil_diag_kernel<<<grid_for(A.n, 4), kOpThreads, 0, st>>>(A, diag);

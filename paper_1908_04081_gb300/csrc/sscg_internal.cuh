@@ -150,4 +150,52 @@ cudaError_t launch_face_grad(const Operator& A, const double* lam, const double*
                              double* gkz, cudaStream_t st);
 cudaError_t launch_csr_grad(const Operator& A, const double* lam, const double* x, double* gval, cudaStream_t st);
 
+
+// ------------------------------------------------------------------ batches
+// A batched solve runs many independent (system, right-hand side) pairs in
+// lock-step outer loops.  Every vector of pair j lives at rows
+// [off, off + n) of the concatenated arrays; basis column c of pair j starts
+// at Y + c * LD + off.  Row work is cut into chunks of kBatchChunk rows, each
+// owned by one pair; the Gram uses its own blocks of kBatchGramRows rows.
+constexpr int kBatchChunk = 2048;
+constexpr int kBatchGramRows = 2048;
+
+struct BatchPair {
+  Operator op;      // the pair's system (operator storage owned by its handle)
+  int64_t off, n;
+  int chunk0, nchunk;
+  int gblk0, ngblk;
+};
+
+struct BatchView {
+  const BatchPair* pairs;
+  int npairs;
+  const int* chunk_pair;  // chunk -> pair
+  int nchunks;
+  const int* gblk_pair;   // Gram block -> pair
+  int ngblk;
+  SolveState* states;     // one per pair
+  double* G;              // kMaxCols x kMaxCols per pair
+  sscg_outer_record* hist;  // hist_cap records per pair, or null
+  int hist_cap;
+  unsigned int* active;   // pairs still iterating after the last outer loop
+  unsigned int* bodies;   // outer loops run so far (all pairs)
+  int max_bodies;
+};
+
+// batch.cu / per-file batched kernels
+cudaError_t launch_batch_mpk(const BatchView& v, double* Y, int64_t LD, int level, cudaStream_t st);
+cudaError_t launch_batch_gram(const BatchView& v, const double* Y, int64_t LD, double* partials, cudaStream_t st);
+cudaError_t launch_batch_kappa(const BatchView& v, int sigma_max, cudaStream_t st);
+cudaError_t launch_batch_control(const BatchView& v, const double* leja, cudaStream_t st);
+cudaError_t launch_batch_recombine(const BatchView& v, double* Y, int64_t LD, double* x, cudaStream_t st);
+cudaError_t launch_batch_check(const BatchView& v, const double* b, const double* x, double* rt, double* Y,
+                               int64_t LD, double* partials, cudaStream_t st);
+cudaError_t launch_batch_init(const BatchView& v, const double* b, double* x, double* Y, int64_t LD,
+                              double* partials, cudaStream_t st);
+cudaError_t launch_batch_begin(const BatchView& v, cudaStream_t st);
+cudaError_t launch_batch_end(const BatchView& v, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+cudaError_t launch_batch_arm(cudaGraphConditionalHandle cond, cudaStream_t st);
+cudaError_t launch_solve_cond(const SolveState* state, cudaGraphConditionalHandle cond, cudaStream_t st);
+
 }  // namespace sscg

@@ -381,9 +381,291 @@ __global__ void hscg_replace_finish_kernel(SolveState* st) {
   st->replacements += 1;
 }
 
+
+// ------------------------------------------------------------------ batches
+// (A v)_i for row i of a pair's operator (stencil or CSR); v is pair-local.
+__device__ __forceinline__ double batch_apply(const Operator& A, const double* __restrict__ v, int64_t i) {
+  if (A.kind == 1) {
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
+    const int x = (int)(i % nx);
+    const int64_t t = i / nx;
+    const int y = (int)(t % ny);
+    const int z = (int)(t / ny);
+    const int64_t plane = (int64_t)nx * ny;
+    const int64_t fx = ((int64_t)z * ny + y) * (nx + 1) + x;
+    const int64_t fy = ((int64_t)z * (ny + 1) + y) * nx + x;
+    double acc = A.diag[i] * v[i];
+    acc = fma(-A.kx[fx], x > 0 ? v[i - 1] : 0.0, acc);
+    acc = fma(-A.kx[fx + 1], x < nx - 1 ? v[i + 1] : 0.0, acc);
+    acc = fma(-A.ky[fy], y > 0 ? v[i - nx] : 0.0, acc);
+    acc = fma(-A.ky[fy + nx], y < ny - 1 ? v[i + nx] : 0.0, acc);
+    if (A.dim == 3) {
+      acc = fma(-A.kz[i], z > 0 ? v[i - plane] : 0.0, acc);
+      acc = fma(-A.kz[i + plane], z < nz - 1 ? v[i + plane] : 0.0, acc);
+    }
+    return acc;
+  }
+  double acc = 0.0;
+  for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) acc = fma(A.val[k], v[A.col[k]], acc);
+  return acc;
+}
+
+// Per-pair fixed-order sum of chunk partials: the last chunk of pair j to
+// arrive (ticket on the pair's counter) adds them; returns true there.
+__device__ bool pair_last_sum(double partial, const BatchPair& bp, SolveState* st, double* partials, int c,
+                              double* total) {
+  __shared__ bool is_last;
+  const double bs = block_sum(partial);
+  if (threadIdx.x == 0) {
+    partials[c] = bs;
+    __threadfence();
+    is_last = atomicAdd(&st->red_counter, 1u) == (unsigned)bp.nchunk - 1;
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < bp.nchunk; b += kVecThreads) s += __ldcg(partials + bp.chunk0 + b);
+  s = block_sum(s);
+  if (threadIdx.x == 0) {
+    *total = s;
+    st->red_counter = 0u;
+  }
+  return true;
+}
+
+// r0 = b - A x0 into basis columns 0 and 1 of every pair, and ||b|| per pair.
+__global__ void __launch_bounds__(kVecThreads) batch_init_kernel(BatchView v, const double* __restrict__ b,
+                                                                 const double* __restrict__ x, double* __restrict__ Y,
+                                                                 int64_t LD, double* __restrict__ partials) {
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    SolveState* st = v.states + j;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
+    int64_t r1 = r0 + kBatchChunk;
+    if (r1 > bp.n) r1 = bp.n;
+    const double* xb = x + bp.off;
+    double s = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double bi = b[bp.off + i];
+      const double r = bi - batch_apply(bp.op, xb, i);
+      Y[bp.off + i] = r;
+      Y[LD + bp.off + i] = r;
+      s = fma(bi, bi, s);
+    }
+    double tot;
+    if (pair_last_sum(s, bp, st, partials, c, &tot) && threadIdx.x == 0) {
+      st->normb = sqrt(tot);
+      if (tot == 0.0) {
+        st->zero_rhs = 1;
+        st->done = 1;
+        st->status = SSCG_OK;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) batch_zero_x_kernel(BatchView v, double* __restrict__ x) {
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    if (!v.states[j].zero_rhs) continue;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
+    int64_t r1 = r0 + kBatchChunk;
+    if (r1 > bp.n) r1 = bp.n;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) x[bp.off + i] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) batch_recombine_kernel(BatchView v, double* __restrict__ Y, int64_t LD,
+                                                                      double* __restrict__ x) {
+  __shared__ double cx[kMaxCols], cr[kMaxCols], cp[kMaxCols];
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    const SolveState* st = v.states + j;
+    if (st->done) continue;
+    const int nc = st->nc;
+    __syncthreads();
+    if (threadIdx.x < kMaxCols) {
+      cx[threadIdx.x] = st->xc[threadIdx.x];
+      cr[threadIdx.x] = st->rc[threadIdx.x];
+      cp[threadIdx.x] = st->pc[threadIdx.x];
+    }
+    __syncthreads();
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
+    int64_t r1 = r0 + kBatchChunk;
+    if (r1 > bp.n) r1 = bp.n;
+    double* Yp = Y + bp.off;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      double sx = 0.0, sr = 0.0, sp = 0.0;
+      for (int k = 0; k < nc; ++k) {
+        const double y = Yp[(int64_t)k * LD + i];
+        sx = fma(y, cx[k], sx);
+        sr = fma(y, cr[k], sr);
+        sp = fma(y, cp[k], sp);
+      }
+      x[bp.off + i] += sx;
+      Yp[i] = sp;
+      Yp[LD + i] = sr;
+    }
+  }
+}
+
+// True-residual confirmation of the pairs whose estimate reached tol (C16).
+__global__ void __launch_bounds__(kVecThreads) batch_true_residual_kernel(BatchView v, const double* __restrict__ b,
+                                                                          const double* __restrict__ x,
+                                                                          double* __restrict__ rt,
+                                                                          double* __restrict__ partials) {
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    SolveState* st = v.states + j;
+    if (st->done || !st->converged_est) continue;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
+    int64_t r1 = r0 + kBatchChunk;
+    if (r1 > bp.n) r1 = bp.n;
+    const double* xb = x + bp.off;
+    double s = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double r = b[bp.off + i] - batch_apply(bp.op, xb, i);
+      rt[bp.off + i] = r;
+      s = fma(r, r, s);
+    }
+    double tot;
+    if (pair_last_sum(s, bp, st, partials, c, &tot) && threadIdx.x == 0) {
+      st->rt2 = tot;
+      const double rel = sqrt(tot) / st->normb;
+      if (rel <= st->tol) {
+        st->done = 1;
+        st->status = SSCG_OK;
+      } else if (st->prev_fail > 0.0 && rel >= 0.5 * st->prev_fail) {
+        st->done = 1;
+        st->status = SSCG_NOT_CONVERGED;
+      } else {
+        st->prev_fail = rel;
+        st->replace_pending = 1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) batch_replacement_kernel(BatchView v, const double* __restrict__ rt,
+                                                                        double* __restrict__ Y, int64_t LD) {
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    const SolveState* st = v.states + j;
+    if (st->done || !st->replace_pending) continue;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
+    int64_t r1 = r0 + kBatchChunk;
+    if (r1 > bp.n) r1 = bp.n;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double r = rt[bp.off + i];
+      Y[bp.off + i] = r;
+      Y[LD + bp.off + i] = r;
+    }
+  }
+}
+
+// End of one outer loop for every pair; counts the pairs still running.
+__global__ void batch_end_kernel(BatchView v) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.npairs; j += gridDim.x * blockDim.x) {
+    SolveState* st = v.states + j;
+    if (st->done) continue;
+    if (st->replace_pending) {
+      st->replace_pending = 0;
+      st->converged_est = 0;
+      st->psi = 1.0;
+      st->replacements += 1;
+      const int k = st->k - 1;
+      if (v.hist != nullptr && k >= 0 && k < v.hist_cap) v.hist[(int64_t)j * v.hist_cap + k].replaced |= 1;
+    }
+    if (st->k >= st->max_outer) {
+      st->status = SSCG_NOT_CONVERGED;
+      st->done = 1;
+      continue;
+    }
+    atomicAdd(v.active, 1u);
+  }
+}
+
+__global__ void batch_begin_kernel(BatchView v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *v.active = 0u;
+    *v.bodies += 1u;
+  }
+}
+
+// Loop condition of the batched graph: continue while a pair is running and
+// the outer-loop budget is not spent.
+__global__ void batch_cond_kernel(BatchView v, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    cudaGraphSetConditional(cond, (*v.active > 0u && *v.bodies < (unsigned)v.max_bodies) ? 1u : 0u);
+}
+
+// Loop condition of a single solve's graph: repeat the outer loop until the
+// device has set done (convergence, breakdown, stagnation or the outer-loop cap).
+__global__ void solve_cond_kernel(const SolveState* st, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
+}
+
+__global__ void batch_arm_kernel(cudaGraphConditionalHandle cond) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, 1u);
+}
+
+int chunk_grid(const BatchView& v) {
+  int g = v.nchunks < 152 * 8 ? v.nchunks : 152 * 8;
+  return g < 1 ? 1 : g;
+}
+
 }  // namespace
 
 int reduce_blocks(int64_t n) { return vec_grid(n); }
+
+cudaError_t launch_batch_init(const BatchView& v, const double* b, double* x, double* Y, int64_t LD,
+                              double* partials, cudaStream_t st) {
+  batch_init_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, b, x, Y, LD, partials);
+  batch_zero_x_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_recombine(const BatchView& v, double* Y, int64_t LD, double* x, cudaStream_t st) {
+  batch_recombine_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, Y, LD, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_check(const BatchView& v, const double* b, const double* x, double* rt, double* Y,
+                               int64_t LD, double* partials, cudaStream_t st) {
+  batch_true_residual_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, b, x, rt, partials);
+  batch_replacement_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, rt, Y, LD);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_begin(const BatchView& v, cudaStream_t st) {
+  batch_begin_kernel<<<1, 32, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_end(const BatchView& v, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
+  const int g = (v.npairs + 255) / 256;
+  batch_end_kernel<<<g < 1 ? 1 : g, 256, 0, st>>>(v);
+  if (use_cond) batch_cond_kernel<<<1, 32, 0, st>>>(v, cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_cond(const SolveState* state, cudaGraphConditionalHandle cond, cudaStream_t st) {
+  solve_cond_kernel<<<1, 32, 0, st>>>(state, cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_arm(cudaGraphConditionalHandle cond, cudaStream_t st) {
+  batch_arm_kernel<<<1, 32, 0, st>>>(cond);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_recombine(const SolveState* state, void* Y, int64_t ld, double* x, double* r64, double* p64,
                              int64_t n, bool y32, cudaStream_t st) {

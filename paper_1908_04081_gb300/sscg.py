@@ -55,6 +55,13 @@ class Stats(C.Structure):
                 ("hist", C.POINTER(OuterRecord)), ("hist_cap", C.c_int), ("hist_len", C.c_int)]
 
 
+class BatchStats(C.Structure):
+    _fields_ = [("npairs", C.c_int), ("converged", C.c_int), ("outer_loops", C.c_int), ("host_syncs", C.c_int),
+                ("kernel_launches", C.c_int), ("graph_launches", C.c_int), ("inner_iters", C.c_int64),
+                ("max_true_relres", C.c_double), ("pair_status", C.POINTER(C.c_int)),
+                ("pair_outer", C.POINTER(C.c_int)), ("pair_inner", C.POINTER(C.c_int))]
+
+
 _lib = None
 _P = C.c_void_p
 _I64 = C.c_int64
@@ -91,6 +98,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sscg_leja": (C.c_int, [C.c_int, _P]),
         "sscg_stencil_face_grad": (C.c_int, [_P, _P, _P, _P, _P, _P]),
         "sscg_csr_value_grad": (C.c_int, [_P, _P, _P, _P]),
+        "sscg_solve_batch": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(C.c_int), _P, _P, C.c_double,
+                                       C.POINTER(C.c_int), C.c_int, C.POINTER(Opts), C.POINTER(BatchStats), _P]),
+        "sscg_autotune": (C.c_int, [_P, _P, C.c_double, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int,
+                                    C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -291,6 +302,41 @@ def sscg_stencil_face_grad(h: int, lam, x, gkx, gky, gkz=None) -> None:
 
 def sscg_csr_value_grad(h: int, lam, x, gval) -> None:
     _check(load_library().sscg_csr_value_grad(h, _f64(lam), _f64(x), _f64(gval)), "sscg_csr_value_grad")
+
+
+def sscg_solve_batch(handles, nrhs, b, x, tol: float, s_max, basis="newton", opts: Opts | None = None,
+                     stream=None):
+    """Batched Algorithm 5 over (system, right-hand side) pairs; b, x are the
+    concatenated device vectors (system-major, right-hand-side-major).
+    Returns (status, stats dict with per-pair arrays)."""
+    nsys = len(handles)
+    hs = (_P * nsys)(*handles)
+    nr = (C.c_int * nsys)(*[int(k) for k in nrhs])
+    sm = (C.c_int * nsys)(*[int(k) for k in s_max])
+    npairs = int(sum(int(k) for k in nrhs))
+    st = BatchStats()
+    ps, po, pi = (C.c_int * max(npairs, 1))(), (C.c_int * max(npairs, 1))(), (C.c_int * max(npairs, 1))()
+    st.pair_status = C.cast(ps, C.POINTER(C.c_int))
+    st.pair_outer = C.cast(po, C.POINTER(C.c_int))
+    st.pair_inner = C.cast(pi, C.POINTER(C.c_int))
+    rc = load_library().sscg_solve_batch(hs, nsys, nr, _f64(b), _f64(x), tol, sm, BASES.get(basis, basis),
+                                         C.byref(opts) if opts is not None else None, C.byref(st),
+                                         _stream_ptr(stream))
+    _check(rc, "sscg_solve_batch", allow_status=True)
+    return rc, dict(npairs=st.npairs, converged=st.converged, outer_loops=st.outer_loops, host_syncs=st.host_syncs,
+                    kernel_launches=st.kernel_launches, graph_launches=st.graph_launches,
+                    inner_iters=st.inner_iters, max_true_relres=st.max_true_relres,
+                    pair_status=list(ps)[:npairs], pair_outer=list(po)[:npairs], pair_inner=list(pi)[:npairs])
+
+
+def sscg_autotune(h: int, b, tol: float, candidates, trial_outer: int = 12, basis="newton"):
+    """Pick sigma among candidates by timed trial outer loops (the library's autotuner)."""
+    cand = (C.c_int * len(candidates))(*candidates)
+    best = C.c_int()
+    times = (C.c_double * len(candidates))()
+    _check(load_library().sscg_autotune(h, _f64(b), tol, cand, len(candidates), trial_outer,
+                                        BASES.get(basis, basis), C.byref(best), times), "sscg_autotune")
+    return best.value, list(times)
 
 
 def history(st: Stats) -> list[dict]:
