@@ -359,6 +359,13 @@ def main():
     hist = pkg.sscg.history(st0)
     alg_bytes = sum(algorithmic_bytes_per_outer(n, h["sbar"], bytes_a) for h in hist)
     hbm_gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
+    # DRAM traffic of a Gram launch, from the ncu capture of the 96^3 case
+    # (profiles/gram_partial_varcoef3d_96.md): 8 B per row and column read once
+    # plus 3.4 MB of block partials; scaled here by the rows and columns each
+    # launch of this run processed (stencil workloads only)
+    gram_traffic = None
+    if hist and hasattr(op, "kx"):
+        gram_traffic = sum(8.0 * n * (2 * h["sbar"] + 1) + 3.4e6 for h in hist) / len(hist)
     launches = sum(s.kernel_launches for s in stats)
 
     # ---- HSCG on the same GPU
@@ -425,7 +432,7 @@ def main():
             "roofline": {"bound": "alu", "kernel": "gram_partial+gram_reduce (G = Y^T Y, FP64)",
                          "achieved": gram_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": (gram_tflops / FP64_PEAK_TFLOPS) if gram_tflops else None,
-                         "traffic": None, "launches": n_gram,
+                         "traffic": gram_traffic, "launches": n_gram,
                          "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 is not in "
                                       "MEASURED_PEAKS.json)"},
             "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,

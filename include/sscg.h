@@ -48,7 +48,8 @@ typedef enum { SSCG_C_XI = 0, SSCG_C_XI_SCALED = 1, SSCG_C_ONE = 2, SSCG_C_KAPPA
 enum {
   SSCG_OK = 0,
   SSCG_BREAKDOWN = 2,        /* p'^T G B p' <= 0 at the first step of a block: A not SPD (numerically) */
-  SSCG_NOT_CONVERGED = 3,    /* max_outer (or max_iters) reached */
+  SSCG_NOT_CONVERGED = 3,    /* max_outer (or max_iters) reached, or stagnation above tol */
+  SSCG_NONFINITE = 4,        /* a NaN or Inf in b, x0, A or the iteration */
   SSCG_ERR_INVALID_ARG = -1,
   SSCG_ERR_CUDA = -2,        /* a CUDA runtime call failed; sscg_last_cuda_error() has the text */
   SSCG_ERR_NO_MEMORY = -3,
@@ -68,7 +69,9 @@ typedef struct {
   int y_fp32;            /* 1: store the basis Y in binary32 (recurrence, Gram, x, r, p stay binary64;
                             r := b - A x whenever the residual estimate has fallen by 2^-4 since the
                             last such replacement); default 0 */
-  int variant;           /* 0: Algorithm 5; 1: fixed s-step CG (s_k = sigma, no break test); default 0 */
+  int variant;           /* 0: Algorithm 5; 1: fixed s-step CG (s_k = sigma, no break test); 2: the previous
+                            adaptive s-step CG, Algorithm 2 (basis never retuned from Ritz values, c = c_const,
+                            break when kappa(Y_{k,s~}) >= tol/(c eps ||r||/||b||)); default 0 */
   int check_every;       /* outer loops enqueued between two polls of the done flag; default 4 */
   int use_graph;         /* 1: replay one outer loop as a CUDA graph; default 1 */
   int profile;           /* 1: time each kernel phase with CUDA events (direct launches); default 0 */

@@ -2,7 +2,12 @@
 
   hscg      Algorithm 1 (Hestenes-Stiefel CG, Section 1)
   sstep_cg  Algorithm 5 (improved adaptive s-step CG, Section 4), with the
-            Algorithm 2 / fixed-s comparators of Section 5 as options
+            comparators of Section 5 as options: fixed s-step CG
+            (variant="fixed": s_k = sigma, no break test) and the previous
+            adaptive s-step CG, Algorithm 2 (variant="old": monomial basis never
+            retuned, the user constant c = c_const, and the pessimistic break
+            test gamma >= eps*/(c eps ||r_{m+j+1}||) with gamma = kappa(Y_{k,s~}),
+            relative residual reading C10)
 
 Readings of the paper used here (the CUDA path takes the same ones):
   C9   Y is stored interleaved, so Y_l is the leading 2l+1 columns.
@@ -42,7 +47,7 @@ from .ritz import RitzTracker
 EPS64 = 2.0 ** -53
 KAPPA_CUT = 2.0 ** -44
 
-OK, NOT_CONVERGED, BREAKDOWN = 0, 3, 2
+OK, NOT_CONVERGED, BREAKDOWN, NONFINITE = 0, 3, 2, 4
 
 
 def _norm(v) -> float:
@@ -117,7 +122,7 @@ class Options:
     # FP32-stored basis: replace r by b - A x at the end of a block once the
     # residual estimate has fallen by this factor since the last replacement
     fp32_replace_drop: float = 2.0 ** -4
-    variant: str = "improved"          # improved (Alg. 5) | fixed (s_k = sigma)
+    variant: str = "improved"          # improved (Alg. 5) | fixed (s_k = sigma) | old (Alg. 2)
     # replay: a decision log [{"stilde", "sk", "replaced"}, ...] from another
     # implementation.  The oracle then takes those decisions instead of its own,
     # evaluates its own ones beside them and records, for each decision, the
@@ -182,6 +187,9 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
             relres_true=0.0, lmin=None, lmax=None, c=None, psi=1.0)
     x = np.array(x0, dtype=np.float64, copy=True)
     r = b - A @ x
+    if not math.isfinite(normb) or not math.isfinite(_norm(r)):   # NaN/Inf in b, x0 or A
+        return x, dict(status=NONFINITE, outer=0, inner=0, alphas=[], betas=[], hist=[], replacements=0,
+                       relres_true=math.nan, lmin=None, lmax=None, c=None, psi=1.0)
     p = r.copy()
     psi = 1.0
     c = 1.0 / math.sqrt(eps)  # c_1 = eps^{-1/2}
@@ -204,6 +212,8 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
         kap, _, _ = kappa_estimates(G, sbar, o.kappa_cut)
         normr = math.sqrt(G[1, 1])
         margins = {}
+        if o.variant == "old":
+            c = o.c_const            # Alg. 2: c_k is supplied by the user
         if o.variant == "fixed":
             stilde = sbar
         else:
@@ -254,12 +264,15 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
             psi = psi / (psi + beta)
             ritz.push(alpha, betas[-1] if betas else None)
             betas.append(beta)
-            if m + j + 1 > 1:
+            if m + j + 1 > 1 and o.variant != "old":
                 c = c_value(o.c_mode, ritz.lmin, ritz.lmax, psi, o.c_const)
             rr = rr_new
             own_conv = o.inner_conv_check and math.sqrt(rr_new) / normb <= tol
-            own_brk = (not own_conv) and o.variant != "fixed" and j < stilde - 1 and \
-                gam[j + 1] >= tol / (c * eps * phi / normb)
+            if o.variant == "old":   # Alg. 2: kappa of the whole block, current residual
+                own_brk = (not own_conv) and kap[stilde] >= tol / (c * eps * math.sqrt(rr_new) / normb)
+            else:
+                own_brk = (not own_conv) and o.variant != "fixed" and j < stilde - 1 and \
+                    gam[j + 1] >= tol / (c * eps * phi / normb)
             if forced_sk is None:
                 if own_conv:
                     converged_est = True
@@ -289,7 +302,7 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
         hist.append(dict(sbar=sbar, stilde=stilde, sk=sk, kappa=kap.tolist(), c_start=c_start,
                          c=c, phi=phi, lmin=ritz.lmin, lmax=ritz.lmax,
                          relres_est=math.sqrt(max(rr, 0.0)) / normb, m=m, margins=margins))
-        if m > 1 and kind != bs.MONOMIAL:
+        if m > 1 and kind != bs.MONOMIAL and o.variant != "old":
             theta, gamma, mu = bs.basis_params(kind, sigma, ritz.lmin, ritz.lmax,
                                                o.newton_scale, o.cheb_params)
         if not converged_est and not o.inner_conv_check:
@@ -320,6 +333,9 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
         if converged_est:
             rt = b - A @ x
             rel = _norm(rt) / normb
+            if not math.isfinite(rel):
+                status = NONFINITE
+                break
             if rel <= tol:
                 status = OK
                 done = True

@@ -306,7 +306,8 @@ const char* sscg_strerror(int code) {
   switch (code) {
     case SSCG_OK: return "ok";
     case SSCG_BREAKDOWN: return "breakdown: p'^T G B p' <= 0 at the first step of a block (A not SPD?)";
-    case SSCG_NOT_CONVERGED: return "not converged within the iteration cap";
+    case SSCG_NOT_CONVERGED: return "not converged (iteration cap, or stagnation above tol)";
+    case SSCG_NONFINITE: return "non-finite value (NaN or Inf) in b, x0, A or the iteration";
     case SSCG_ERR_INVALID_ARG: return "invalid argument";
     case SSCG_ERR_CUDA: return "CUDA runtime error (see sscg_last_cuda_error)";
     case SSCG_ERR_NO_MEMORY: return "out of device memory";

@@ -7,7 +7,10 @@
 //
 // This file is compiled with FMA contraction disabled: its scalar formulas are
 // evaluated operation by operation in the order they are written, so equal
-// inputs give equal decisions on any IEEE binary64 implementation.
+// inputs give equal decisions on any IEEE binary64 implementation.  Fused
+// multiply-adds appear only where written out (fma()): in the small matrix
+// kernels (Householder, Sturm sequences, G times a vector), whose summation
+// order differs from any reference anyway.
 #include <math.h>
 
 #include "sscg_internal.cuh"
@@ -36,7 +39,7 @@ __device__ int sturm_count(const double* d, const double* e2, int n, double x) {
   if (p == 0.0) p = -1e-300;
   int cnt = p < 0.0 ? 1 : 0;
   for (int i = 1; i < n; ++i) {
-    double q = (d[i] - x) * p - e2[i - 1] * pm;
+    double q = fma(d[i] - x, p, -(e2[i - 1] * pm));
     if (q == 0.0) q = p < 0.0 ? 1e-300 : -1e-300;
     cnt += ((q < 0.0) != (p < 0.0)) ? 1 : 0;
     // keep the sequence in range (both terms by the same power of two)
@@ -125,7 +128,7 @@ __device__ void kappa_body(const double* __restrict__ G, int ldg, int l, double 
       const int i = t >> 2;
       double s = 0.0;
       if (i < m)
-        for (int j = t & 3; j < m; j += 4) s += A[k + 1 + i][k + 1 + j] * v[j];
+        for (int j = t & 3; j < m; j += 4) s = fma(A[k + 1 + i][k + 1 + j], v[j], s);
       s += __shfl_xor_sync(0xffffffffu, s, 1);
       s += __shfl_xor_sync(0xffffffffu, s, 2);
       if (i < m && (t & 3) == 0) p[i] = tau * s;
@@ -147,7 +150,7 @@ __device__ void kappa_body(const double* __restrict__ G, int ldg, int l, double 
         ++i;
       }
       const int j = rem;
-      const double val = A[k + 1 + i][k + 1 + j] - (v[i] * w[j] + w[i] * v[j]);
+      const double val = fma(-v[i], w[j], fma(-w[i], v[j], A[k + 1 + i][k + 1 + j]));
       A[k + 1 + i][k + 1 + j] = val;
       A[k + 1 + j][k + 1 + i] = val;
     }
@@ -252,7 +255,7 @@ __device__ double gmv_dot(const double (*Gs)[kMaxCols + 1], const double* x, con
     const int i = base + (t >> 2);
     double s = 0.0;
     if (i < n)
-      for (int j = t & 3; j < n; j += 4) s += Gs[i][j] * x[j];
+      for (int j = t & 3; j < n; j += 4) s = fma(Gs[i][j], x[j], s);
     s += __shfl_xor_sync(0xffffffffu, s, 1);
     s += __shfl_xor_sync(0xffffffffu, s, 2);
     if (i < n && (t & 3) == 0) {
@@ -378,6 +381,7 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
 
   const int sbar = st->sbar;
   if (t == 0) {
+    if (st->variant == 2) st->c = st->c_const;  // Alg. 2: c_k supplied by the user
     int stl = 1;
     if (st->variant == 1) {
       stl = sbar;
@@ -451,11 +455,15 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
         st->psi = st->psi / (st->psi + beta);
         ritz_push(st, alpha, st->beta_prev);
         st->beta_prev = beta;
-        if (m0 + j + 1 > 1) st->c = c_value(st->c_mode, st->lmin, st->lmax, st->psi, st->c_const);
+        if (m0 + j + 1 > 1 && st->variant != 2)
+          st->c = c_value(st->c_mode, st->lmin, st->lmax, st->psi, st->c_const);
         rr = rr_new;
         if (st->inner_conv_check && sqrt(rr_new) / st->normb <= st->tol) {
           conv = 1;
           s_flag = 2;
+        } else if (st->variant == 2) {
+          // Alg. 2's break test: kappa of the whole block against the current residual
+          if (st->kappa[stl] >= st->tol / (st->c * st->eps * sqrt(rr_new) / st->normb)) s_flag = 2;
         } else if (st->variant != 1 && j < stl - 1 &&
                    st->kappa[j + 2] >= st->tol / (st->c * st->eps * phi / st->normb)) {
           s_flag = 2;
@@ -486,7 +494,7 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
       st->m = m0 + sk;
       st->converged_est = conv;
       st->upd_relres = sqrt(rr > 0.0 ? rr : 0.0) / st->normb;
-      if (st->m > 1 && st->basis != SSCG_MONOMIAL) {
+      if (st->m > 1 && st->basis != SSCG_MONOMIAL && st->variant != 2) {
         basis_update(st, leja);
         st->have_ritz = 1;
       }

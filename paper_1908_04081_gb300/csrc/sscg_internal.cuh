@@ -19,7 +19,7 @@ constexpr int kMaxS = SSCG_MAX_S;
 constexpr int kMaxCols = 2 * kMaxS + 1;                    // 33
 constexpr int kMaxPairs = kMaxCols * (kMaxCols + 1) / 2;   // 561
 constexpr int kGramThreads = 576;                          // >= kMaxPairs, multiple of 32
-constexpr int kGramTileRows = 32;
+constexpr int kGramTileRows = 128;
 
 // ---------------------------------------------------------------- operator
 // A sparse SPD operator: a CSR matrix or a 2D/3D face-coefficient stencil.

@@ -131,6 +131,9 @@ __global__ void __launch_bounds__(kVecThreads) init_norms_kernel(SolveState* __r
       st->zero_rhs = 1;
       st->done = 1;
       st->status = SSCG_OK;
+    } else if (!isfinite(tot)) {
+      st->done = 1;
+      st->status = SSCG_NONFINITE;
     }
   }
 }
@@ -157,7 +160,10 @@ __global__ void __launch_bounds__(kVecThreads) true_norm_kernel(SolveState* __re
     st->rt2 = tot;
     if (!force) {
       const double rel = sqrt(tot) / st->normb;
-      if (rel <= st->tol) {
+      if (!isfinite(rel)) {
+        st->done = 1;
+        st->status = SSCG_NONFINITE;
+      } else if (rel <= st->tol) {
         st->done = 1;
         st->status = SSCG_OK;
       } else if (st->prev_fail > 0.0 && rel >= 0.5 * st->prev_fail) {
@@ -327,6 +333,9 @@ __global__ void __launch_bounds__(kVecThreads) hscg_init_kernel(SolveState* __re
       st->zero_rhs = 1;
       st->done = 1;
       st->status = SSCG_OK;
+    } else if (!isfinite(a) || !isfinite(c)) {
+      st->done = 1;
+      st->status = SSCG_NONFINITE;
     } else if (sqrt(c) / st->normb <= st->tol) {
       st->converged_est = 1;
     }
@@ -349,7 +358,10 @@ __global__ void __launch_bounds__(kVecThreads) hscg_confirm_kernel(SolveState* _
   if (last_block_sum(s, partials, &st->red_counter, &tot) && threadIdx.x == 0) {
     st->rt2 = tot;
     const double rel = sqrt(tot) / st->normb;
-    if (rel <= st->tol) {
+    if (!isfinite(rel)) {
+      st->done = 1;
+      st->status = SSCG_NONFINITE;
+    } else if (rel <= st->tol) {
       st->done = 1;
       st->status = SSCG_OK;
     } else if (st->prev_fail > 0.0 && rel >= 0.5 * st->prev_fail) {
@@ -461,6 +473,9 @@ __global__ void __launch_bounds__(kVecThreads) batch_init_kernel(BatchView v, co
         st->zero_rhs = 1;
         st->done = 1;
         st->status = SSCG_OK;
+      } else if (!isfinite(tot)) {
+        st->done = 1;
+        st->status = SSCG_NONFINITE;
       }
     }
     __syncthreads();
@@ -538,7 +553,10 @@ __global__ void __launch_bounds__(kVecThreads) batch_true_residual_kernel(BatchV
     if (pair_last_sum(s, bp, st, partials, c, &tot) && threadIdx.x == 0) {
       st->rt2 = tot;
       const double rel = sqrt(tot) / st->normb;
-      if (rel <= st->tol) {
+      if (!isfinite(rel)) {
+        st->done = 1;
+        st->status = SSCG_NONFINITE;
+      } else if (rel <= st->tol) {
         st->done = 1;
         st->status = SSCG_OK;
       } else if (st->prev_fail > 0.0 && rel >= 0.5 * st->prev_fail) {

@@ -21,7 +21,7 @@ SSCG_MAX_S = 16
 MONOMIAL, NEWTON, CHEBYSHEV = 0, 1, 2
 BASES = {"monomial": MONOMIAL, "newton": NEWTON, "chebyshev": CHEBYSHEV}
 C_MODES = {"xi": 0, "xi_scaled": 1, "one": 2, "kappa_ratio": 3, "const": 4}
-OK, BREAKDOWN, NOT_CONVERGED = 0, 2, 3
+OK, BREAKDOWN, NOT_CONVERGED, NONFINITE = 0, 2, 3, 4
 
 
 class SscgError(RuntimeError):
@@ -161,7 +161,7 @@ def sscg_opts_default(**kw) -> Opts:
         if k == "cheb_params" and isinstance(v, str):
             v = {"standard": 0, "paper_printed": 1}[v]
         if k == "variant" and isinstance(v, str):
-            v = {"improved": 0, "fixed": 1}[v]
+            v = {"improved": 0, "fixed": 1, "old": 2}[v]
         setattr(o, k, v)
     return o
 

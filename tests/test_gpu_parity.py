@@ -214,7 +214,8 @@ def test_varcoef3d_stencil_solve(pkg, basis, smax):
 
 @pytest.mark.parametrize("opts", [dict(c_mode="one"), dict(c_mode="kappa_ratio"), dict(c_mode="xi_scaled"),
                                   dict(newton_scale="paper_unit"), dict(cheb_params="paper_printed"),
-                                  dict(inner_conv_check=0), dict(s0=2, f=3), dict(variant="fixed")])
+                                  dict(inner_conv_check=0), dict(s0=2, f=3), dict(variant="fixed"),
+                                  dict(variant="old", c_const=1.0)])
 def test_option_readings(pkg, opts):
     st_ = gen.varcoef_stencil((30, 30), seed=4)
     b = gen.random_rhs(st_.n, 5)
@@ -356,3 +357,25 @@ def test_fp32_stored_basis(pkg, name):
     # the binary32 basis costs at most 30 % more iterations than binary64 here
     assert st.inner_iters <= 1.3 * info64["inner"]
     assert np.linalg.norm(xg - x64) / np.linalg.norm(x64) <= 1e-7
+
+
+def test_failure_detection_injected_on_the_host(pkg):
+    """Faults are injected through the inputs (host side), never into the GPU:
+    a NaN in b, a non-SPD operator, an outer-loop cap."""
+    A, b, x0, _ = gen.config_problem("poisson2d_64", scale=12)
+    s = pkg.Solver.csr(A.rowptr, A.col, A.val)
+    bn = b.copy()
+    bn[5] = np.nan
+    st = s.solve(dev(bn), dev(x0), tol=1e-10, s_max=4)
+    assert st.status == pkg.sscg.NONFINITE
+    sh = s.hscg(dev(bn), dev(x0), tol=1e-10)
+    assert sh.status == pkg.sscg.NONFINITE
+    neg = pkg.Solver.csr(A.rowptr, A.col, -A.val)
+    st2 = neg.solve(dev(b), dev(x0), tol=1e-10, s_max=4)
+    assert st2.status == pkg.sscg.BREAKDOWN
+    st3 = s.solve(dev(b), dev(x0), tol=1e-14, s_max=4, max_outer=3)
+    assert st3.status == pkg.sscg.NOT_CONVERGED and st3.outer_iters == 3
+    # the handle stays usable after each of these
+    xt = dev(x0)
+    st4 = s.solve(dev(b), xt, tol=1e-10, s_max=4)
+    assert st4.status == 0 and st4.true_relres <= 1e-10

@@ -159,3 +159,37 @@ def test_replay_records_margin_of_a_forced_decision():
     log[k] = dict(stilde=log[k]["stilde"] - 1, sk=min(log[k]["sk"], log[k]["stilde"] - 1))
     _, i2 = cg.sstep_cg(A, b, np.zeros(st.n), 1e-10, cg.Options(smax=8, basis="newton", replay=log[:k + 1]))
     assert "stilde" in i2["hist"][k]["margins"]
+
+
+def test_old_adaptive_alg2_reduces_to_hscg_with_huge_c():
+    # with c so large that condy admits no l, every block is one step: HSCG again
+    A, b, x0, _ = gen.config_problem("poisson2d_64", scale=24)
+    M = as_matrix(A)
+    _, h = cg.hscg(M, b, x0, 1e-10)
+    _, s = cg.sstep_cg(M, b, x0, 1e-10, cg.Options(smax=8, basis="monomial", variant="old", c_const=1e30))
+    assert all(hh["sk"] == 1 for hh in s["hist"])
+    assert np.allclose(s["alphas"], h["alphas"][: len(s["alphas"])], rtol=1e-10)
+
+
+def test_old_adaptive_alg2_converges_with_c_one():
+    A, b, x0, _ = gen.config_problem("poisson2d_64")
+    x, s = cg.sstep_cg(as_matrix(A), b, x0, 1e-10, cg.Options(smax=8, basis="monomial", variant="old", c_const=1.0))
+    assert s["status"] == cg.OK and s["relres_true"] <= 1e-10
+    assert all(h["c"] == 1.0 for h in s["hist"])
+    # the basis is never retuned: a Chebyshev request stays monomial
+    _, s2 = cg.sstep_cg(as_matrix(A), b, x0, 1e-10, cg.Options(smax=8, basis="chebyshev", variant="old", c_const=1.0))
+    assert [h["sk"] for h in s2["hist"]] == [h["sk"] for h in s["hist"]]
+
+
+def test_failure_detection_on_the_host():
+    # injected on the host: NaN in b, a non-SPD operator, an iteration cap
+    A, b, x0, _ = gen.config_problem("poisson2d_64", scale=12)
+    M = as_matrix(A)
+    bn = b.copy()
+    bn[5] = np.nan
+    _, i1 = cg.sstep_cg(M, bn, x0, 1e-10, cg.Options(smax=4))
+    assert i1["status"] == cg.NONFINITE
+    _, i2 = cg.sstep_cg(-M, b, x0, 1e-10, cg.Options(smax=4))
+    assert i2["status"] == cg.BREAKDOWN
+    _, i3 = cg.sstep_cg(M, b, x0, 1e-14, cg.Options(smax=4, max_outer=3))
+    assert i3["status"] == cg.NOT_CONVERGED and i3["outer"] == 3
