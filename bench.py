@@ -39,6 +39,9 @@ WORKLOADS = {
     "batched_256": dict(desc="256 independent 2D/3D log-normal-coefficient Poisson systems, N log-uniform in "
                              "[1e3, 2.6e5], 1-8 right-hand sides each, one graph launch, sigma per system by the "
                              "autotuner", smax=16, basis="newton", tol=1e-10),
+    "adjoint2d_512": dict(desc="differentiable solve: 2D 5-pt var-coef Poisson 512^2 (N=262,144), theta=exp(g) per "
+                               "edge, loss ||x(theta)-x_t||^2; forward s-step solve + adjoint s-step solve + "
+                               "face-gradient gather", smax=16, basis="newton", tol=1e-10),
     # a smaller grid of the same stencil family, used for kernel profiles
     "varcoef3d_96": dict(desc="FP64 3D 7-pt var-coef diffusion 96^3 (N=884,736), k=exp(N(0,1)) per face, "
                               "b~N(0,1), x0=0", smax=16, basis="newton", tol=1e-10, base="varcoef3d_160",
@@ -141,6 +144,19 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def aggregate_ranks(elapsed_s, steps, dist=None, device=None):
+    """Whole-job throughput of a replicas run: every rank solved `steps` systems
+    in `elapsed_s` seconds; the job's time is the slowest rank's (all-reduce
+    MAX), and the value is the total number of solves over that time."""
+    import torch
+    world = dist.get_world_size() if dist is not None and dist.is_initialized() else 1
+    t = torch.tensor([float(elapsed_s)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    worst = float(t.item())
+    return world * steps / worst, worst
 
 
 def algorithmic_bytes_per_outer(n, s, bytes_a):
@@ -272,6 +288,40 @@ def run_batched(args, cfg, pkg, torch, dev):
     print(json.dumps(line))
 
 
+def run_adjoint(args, cfg, pkg, torch, dev):
+    """Forward + backward of the differentiable solve (autograd through the C ABI)."""
+    from paper_1908_04081_gb300.autograd import stencil_solve
+    op, b_np, x0_np, extra = load_inputs(args.workload)
+    kx = torch.tensor(op.kx, device=dev)
+    ky = torch.tensor(op.ky, device=dev)
+    b = torch.tensor(b_np, device=dev)
+    xt = torch.tensor(extra["x_target"], device=dev)
+
+    def step():
+        kxr, kyr = kx.clone().requires_grad_(), ky.clone().requires_grad_()
+        x = stencil_solve(kxr, kyr, None, b, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"])
+        loss = ((x - xt) ** 2).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        loss = step()
+    e1.record()
+    torch.cuda.synchronize()
+    el = e0.elapsed_time(e1) / 1e3
+    line = {"metric": METRIC, "value": args.steps / el, "unit": "forward+backward/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["desc"], "s_max": cfg["smax"], "basis": cfg["basis"], "tol": cfg["tol"]},
+            "loss": float(loss.item())}
+    print(json.dumps(line))
+
+
 def main():
     args = parse_args()
     cfg = WORKLOADS[args.workload]
@@ -293,9 +343,10 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
-    if args.workload in ("rgg_2m", "batched_256"):
+    if args.workload in ("rgg_2m", "batched_256", "adjoint2d_512"):
         if rank == 0:
-            (run_rgg if args.workload == "rgg_2m" else run_batched)(args, cfg, pkg, torch, dev)
+            {"rgg_2m": run_rgg, "batched_256": run_batched, "adjoint2d_512": run_adjoint}[args.workload](
+                args, cfg, pkg, torch, dev)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -337,14 +388,9 @@ def main():
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed = float(t.item())
+    value, elapsed = aggregate_ranks(e0.elapsed_time(e1) / 1e3, args.steps, dist if world > 1 else None, dev)
     clocks = clk.summary()
     ok = all(s.status == 0 and s.true_relres <= cfg["tol"] for s in stats)
-    value = world * args.steps / elapsed
     ms_per_step = elapsed / args.steps * 1e3
 
     # roofline of the dominant kernel (the Gram contraction: FP64 ALU bound)
