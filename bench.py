@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--max-outer", type=int, default=0, help="cap outer loops (profiling runs only)")
+    ap.add_argument("--gram-mode", type=int, default=0,
+                    help="0: binary64 Gram (the method as written); 1: binary32-pair products on the FP32 pipes")
     return ap.parse_args()
 
 
@@ -366,6 +368,8 @@ def main():
     def solve(profile=1):
         x.zero_()
         extra = {"max_outer": args.max_outer} if args.max_outer > 0 else {}
+        if args.gram_mode:
+            extra["gram_mode"] = args.gram_mode
         return solver.solve(b, x, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], hist_cap=20000,
                             profile=profile, **extra)
 
@@ -445,7 +449,8 @@ def main():
         te = time.perf_counter()
         for _ in range(e2e_steps):
             xn[:] = 0.0
-            solver.solve_host(bn, xn, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"])
+            solver.solve_host(bn, xn, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"],
+                              **({"gram_mode": args.gram_mode} if args.gram_mode else {}))
         te = time.perf_counter() - te
         e2e = {"value": world * e2e_steps / te, "unit": "solves/s", "h2d_bytes_per_step": 16 * n,
                "d2h_bytes_per_step": 8 * n, "steps": e2e_steps}
@@ -469,7 +474,8 @@ def main():
             "config": {"workload": cfg["desc"], "s_max": cfg["smax"], "basis": cfg["basis"], "tol": cfg["tol"],
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "l2": "inputs larger than L2 (basis Y 1.08 GB, coefficients 99 MB)",
-                       "timing": "CUDA events around K solves; per-phase CUDA events inside each solve"},
+                       "timing": "CUDA events around K solves; per-phase CUDA events inside each solve",
+                       "gram": "binary64 FMA" if args.gram_mode == 0 else "binary32-pair products, binary64 accumulation"},
             "converged": ok, "true_relres": max(s.true_relres for s in stats),
             "outer_loops": st0.outer_iters, "inner_iters": st0.inner_iters, "host_syncs": st0.host_syncs,
             "ms_per_outer_loop": ms_per_step / st0.outer_iters,

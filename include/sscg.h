@@ -78,6 +78,9 @@ typedef struct {
   double c_const;        /* c for SSCG_C_CONST; default 1 */
   double eps;            /* unit roundoff in (condy)/(newcondy); default 2^-53 */
   double kappa_cut;      /* kappa_l = inf when lambda_min(G_l) <= kappa_cut * lambda_max(G_l); default 2^-44 */
+  int gram_mode;         /* 0: G by binary64 FMAs (the method as written); 1: binary32-pair products on the
+                            FP32 pipes, compensated binary32 sums over 128-row tiles, binary64 across tiles
+                            (|error| ~ 2^-46 of |Y_i||Y_j| per term); default 0 */
 } sscg_opts;
 
 /* Per-outer-loop decision record (Alg. 5): s-bar_k, s-tilde_k, s_k, c at the
@@ -252,6 +255,14 @@ int sscg_build_basis(sscg_t h, const double* p, const double* r, int s, const do
  * cuda_stream: cudaStream_t or NULL.  Scratch for the block partial sums is
  * allocated and freed inside the call. */
 int sscg_gram(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, void* cuda_stream);
+
+/* sscg_gram with a choice of product arithmetic: mode 0 as sscg_gram; mode 1
+ * forms every product from binary32 pairs on the FP32 pipes (each value split
+ * exactly into two 24-bit parts after a per-tile power-of-two column scale,
+ * compensated binary32 sums over 128-row tiles, binary64 across tiles), which
+ * GB300 executes far faster than binary64 FMAs.  Same arguments and
+ * allocation behaviour as sscg_gram otherwise. */
+int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, int mode, void* cuda_stream);
 
 /* Same result as sscg_gram, for callers that cannot allocate device memory
  * during a call: programs whose device-memory budget is fixed at start-up,

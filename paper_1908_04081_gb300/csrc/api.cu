@@ -76,6 +76,7 @@ struct sscg_ctx {
   cudaGraphExec_t graph = nullptr;
   int graph_sigma = -1;
   bool graph_y32 = false;
+  int graph_gram_mode = 0;
   int graph_launches = 0;
   double last_lmin = 0.0, last_lmax = 0.0;
 };
@@ -170,7 +171,7 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
   }
   if ((rc = mark(1))) return rc;
   CK(launch_gram(h->Y.p, h->n, h->ld, nullptr, 0, ds, h->partials.p, gram_blocks(h->n), h->G.p, kMaxCols, y32,
-                 st));
+                 st, h->host_state->gram_mode));
   count += 2;
   if ((rc = mark(2))) return rc;
   CK(launch_kappa(h->G.p, kMaxCols, ds, 0, 0.0 /* taken from the state */, ds->kappa, ds->glmin,
@@ -200,7 +201,8 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
 // The whole solve loop as one graph: a kernel arms the loop condition, then a
 // WHILE node repeats one outer loop until the device sets done.
 int build_graph(sscg_ctx* h, int sigma, bool y32) {
-  if (h->graph && h->graph_sigma == sigma && h->graph_y32 == y32) return SSCG_OK;
+  if (h->graph && h->graph_sigma == sigma && h->graph_y32 == y32 && h->graph_gram_mode == h->host_state->gram_mode)
+    return SSCG_OK;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -251,6 +253,7 @@ int build_graph(sscg_ctx* h, int sigma, bool y32) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   h->graph_sigma = sigma;
   h->graph_y32 = y32;
+  h->graph_gram_mode = h->host_state->gram_mode;
   h->graph_launches = nl + 1;
   return SSCG_OK;
 }
@@ -278,6 +281,7 @@ void fill_state_config(SolveState& s, int sigma, double tol, int basis, const ss
   s.c = 1.0 / std::sqrt(o.eps);  // c_1 = eps^{-1/2} (Alg. 5)
   s.psi = 1.0;
   s.fp32_drop = std::ldexp(1.0, -4);  // FP32 basis: replace r after a 2^-4 drop
+  s.gram_mode = o.gram_mode;
   s.rho_last = 1.0;
   for (int l = 0; l < kMaxS; ++l) {
     s.theta[l] = 0.0;  // monomial basis until Ritz values exist
@@ -289,6 +293,7 @@ void fill_state_config(SolveState& s, int sigma, double tol, int basis, const ss
 
 int validate_opts(const sscg_opts& o) {
   if (o.c_mode < 0 || o.c_mode > SSCG_C_CONST) return SSCG_ERR_INVALID_ARG;
+  if (o.gram_mode < 0 || o.gram_mode > 1) return SSCG_ERR_INVALID_ARG;
   if (!(o.eps > 0.0) || !(o.kappa_cut >= 0.0)) return SSCG_ERR_INVALID_ARG;
   return SSCG_OK;
 }
@@ -334,6 +339,7 @@ void sscg_opts_default(sscg_opts* o) {
   o->c_const = 1.0;
   o->eps = std::ldexp(1.0, -53);
   o->kappa_cut = std::ldexp(1.0, -44);
+  o->gram_mode = 0;
 }
 
 int sscg_create_csr(sscg_t* out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
@@ -1030,6 +1036,19 @@ int sscg_gram(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, voi
   DevBuf<double> part;
   CK(part.ensure((size_t)nb * kMaxPairs));
   CK(launch_gram(Y, n, ldy, nullptr, ncols, nullptr, part.p, nb, G, ncols, false, st));
+  CK(cudaStreamSynchronize(st));
+  part.release();
+  return SSCG_OK;
+}
+
+int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, int mode, void* cuda_stream) {
+  if (!Y || !G || n <= 0 || ldy < n || ncols < 1 || ncols > kMaxCols || mode < 0 || mode > 1)
+    return SSCG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int nb = gram_blocks(n);
+  DevBuf<double> part;
+  CK(part.ensure((size_t)nb * kMaxPairs));
+  CK(launch_gram(Y, n, ldy, nullptr, ncols, nullptr, part.p, nb, G, ncols, false, st, mode));
   CK(cudaStreamSynchronize(st));
   part.release();
   return SSCG_OK;

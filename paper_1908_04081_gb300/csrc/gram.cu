@@ -79,6 +79,147 @@ gram_partial_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const SolveS
   }
 }
 
+
+// ------------------------------------------------------------------------
+// Gram with binary32-pair products (gram_mode = 1).
+//
+// GB300 issues binary32 FMAs 62 times faster than binary64 ones, so this
+// variant forms each product y_i y_j on the FP32 pipes and keeps binary64 only
+// for the accumulation across tiles.  Per 128-row tile every column c gets a
+// power-of-two scale 2^-e_c (e_c = its largest exponent in the tile); each
+// scaled value is split exactly by integer operations into hi (its leading 24
+// bits) + lo (the next 24 bits, truncated; |y - hi - lo| < 2^-46 |y|).  Then
+//   y_i y_j ~ hi_i hi_j + (hi_i lo_j + lo_i hi_j + lo_i lo_j),
+// with hi_i hi_j exact as the pair (p, fma(hi_i, hi_j, -p)); the tile sum is a
+// compensated (TwoSum) binary32 pair, added into the binary64 accumulator times
+// 2^(e_i + e_j) once per tile.  Values more than 2^125 below their column's
+// largest in the tile are dropped (they are below binary64's resolution of
+// the sum).
+__device__ __forceinline__ void split_scaled(double y, int cexp, float* hi, float* lo) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(y);
+  const unsigned int sign = (unsigned int)(bits >> 32) & 0x80000000u;
+  const int E = (int)((bits >> 52) & 0x7ff);
+  if (E == 0) {  // zero (and subnormals, far below any column's largest value)
+    *hi = 0.f;
+    *lo = 0.f;
+    return;
+  }
+  if (E == 0x7ff) {  // Inf/NaN propagate
+    *hi = (float)y;
+    *lo = 0.f;
+    return;
+  }
+  const int e = E - 1023 - cexp;  // <= 0
+  if (e < -125) {
+    *hi = 0.f;
+    *lo = 0.f;
+    return;
+  }
+  const unsigned long long m = bits & ((1ull << 52) - 1);
+  *hi = __uint_as_float(sign | ((unsigned int)(e + 127) << 23) | (unsigned int)(m >> 29));
+  const unsigned int rem = (unsigned int)(m & ((1u << 29) - 1));
+  if (rem == 0u) {
+    *lo = 0.f;
+    return;
+  }
+  const int lz = __clz(rem) - 3;       // leading zeros inside the 29-bit remainder
+  const int el = e - 24 - lz;          // exponent of the remainder's leading bit
+  if (el < -126) {
+    *lo = 0.f;
+    return;
+  }
+  const unsigned int ml = (rem << (lz + 4)) >> 9;  // bits after the leading one, 23 kept
+  *lo = __uint_as_float(sign | ((unsigned int)(el + 127) << 23) | ml);
+}
+
+__device__ __forceinline__ int exp_of(double y) {
+  return (int)(((unsigned long long)__double_as_longlong(y) >> 52) & 0x7ff) - 1023;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGramThreads, 2)
+gram_partial_ff_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const SolveState* __restrict__ st,
+                       int ncols_fixed, double* __restrict__ partials) {
+  int ncols = ncols_fixed;
+  if (ncols <= 0) {
+    if (st->done) return;
+    ncols = 2 * st->sbar + 1;
+  }
+  const int np = ncols * (ncols + 1) / 2;
+  const int R = kGramThreads / np;
+  const int t = threadIdx.x;
+  const bool active = t < R * np;
+  const int q = t % np;
+  const int rl = t / np;
+  int pi = 0, pj = 0;
+  pair_of(q, ncols, &pi, &pj);
+
+  // one 8-byte slot per element: first the binary64 value, then (in place) its
+  // (hi, lo) binary32 pair
+  __shared__ double tile[kGramTileRows][kMaxCols + 1];
+  __shared__ int cexp[kMaxCols];
+  __shared__ double red[kGramThreads];
+
+  const int64_t tiles = (n + kGramTileRows - 1) / kGramTileRows;
+  const int64_t tpb = (tiles + gridDim.x - 1) / gridDim.x;
+  const int64_t r_begin = (int64_t)blockIdx.x * tpb * kGramTileRows;
+  int64_t r_end = r_begin + tpb * kGramTileRows;
+  if (r_end > n) r_end = n;
+
+  double acc = 0.0;
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kGramTileRows) {
+    if (t < kMaxCols) cexp[t] = -1100;
+    for (int e = t; e < kGramTileRows * ncols; e += kGramThreads) {
+      const int c = e / kGramTileRows;
+      const int r = e - c * kGramTileRows;
+      const int64_t row = r0 + r;
+      tile[r][c] = row < r_end ? (double)__ldg(Y + (int64_t)c * ld + row) : 0.0;
+    }
+    __syncthreads();
+    for (int e = t; e < kGramTileRows * ncols; e += kGramThreads) {
+      const int c = e / kGramTileRows;
+      const int r = e - c * kGramTileRows;
+      const double y = tile[r][c];
+      if (y != 0.0) atomicMax(&cexp[c], exp_of(y));
+    }
+    __syncthreads();
+    for (int e = t; e < kGramTileRows * ncols; e += kGramThreads) {
+      const int c = e / kGramTileRows;
+      const int r = e - c * kGramTileRows;
+      float h, l;
+      split_scaled(tile[r][c], cexp[c], &h, &l);
+      *reinterpret_cast<float2*>(&tile[r][c]) = make_float2(h, l);
+    }
+    __syncthreads();
+    if (active) {
+      float shi = 0.f, slo = 0.f;
+#pragma unroll 4
+      for (int r = rl; r < kGramTileRows; r += R) {
+        const float2 a = *reinterpret_cast<const float2*>(&tile[r][pi]);
+        const float2 b = *reinterpret_cast<const float2*>(&tile[r][pj]);
+        const float p = a.x * b.x;
+        const float pe = fmaf(a.x, b.x, -p);
+        const float cr = fmaf(a.x, b.y, fmaf(a.y, b.x, a.y * b.y));
+        const float s = shi + p;  // TwoSum(shi, p)
+        const float bb = s - shi;
+        const float err = (shi - (s - bb)) + (p - bb);
+        shi = s;
+        slo = slo + (err + (pe + cr));
+      }
+      const int sc = cexp[pi] + cexp[pj];
+      if (sc > -2100) acc = fma(ldexp(1.0, sc), (double)shi + (double)slo, acc);
+    }
+    __syncthreads();
+  }
+  red[t] = acc;
+  __syncthreads();
+  if (t < np) {
+    double s = 0.0;
+    for (int l = 0; l < R; ++l) s += red[l * np + t];
+    partials[(int64_t)blockIdx.x * kMaxPairs + t] = s;
+  }
+}
+
 // One warp per pair: fixed-order sum of the per-block partials.
 __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restrict__ partials, int nblocks,
                                                           const SolveState* __restrict__ st, int ncols_fixed,
@@ -196,8 +337,14 @@ int gram_blocks(int64_t n) {
 
 cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* /*ncols_dev*/, int ncols_fixed,
                         const SolveState* state, double* partials, int nblocks, double* G, int ldg, bool y32,
-                        cudaStream_t st) {
-  if (y32)
+                        cudaStream_t st, int gram_mode) {
+  if (gram_mode == 1 && y32)
+    gram_partial_ff_kernel<float><<<nblocks, kGramThreads, 0, st>>>(static_cast<const float*>(Y), n, ld, state,
+                                                                    ncols_fixed, partials);
+  else if (gram_mode == 1)
+    gram_partial_ff_kernel<double><<<nblocks, kGramThreads, 0, st>>>(static_cast<const double*>(Y), n, ld, state,
+                                                                     ncols_fixed, partials);
+  else if (y32)
     gram_partial_kernel<float><<<nblocks, kGramThreads, 0, st>>>(static_cast<const float*>(Y), n, ld, state,
                                                                  ncols_fixed, partials);
   else

@@ -60,6 +60,7 @@ struct SolveState {
   // FP32-stored basis: periodic residual replacement (r := b - A x, p kept)
   double fp32_drop, rho_last;
   double prev_fail;   // relative true residual at the last failed convergence check
+  int gram_mode;      // 0: binary64 Gram; 1: binary32-pair products
   int fp32_replace_pending, fp32_replacements;
   double c, psi, normb, upd_relres;
   // Meurant-Tichy state (Algs. 3-4)
@@ -104,9 +105,11 @@ cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level,
 
 // gram.cu
 int gram_blocks(int64_t n);
+// gram_mode 0: binary64 products and sums; 1: binary32-pair products on the
+// FP32 pipes, compensated binary32 sums per tile, binary64 across tiles.
 cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* ncols_dev, int ncols_fixed,
                         const SolveState* state, double* partials, int nblocks, double* G, int ldg,
-                        bool y32, cudaStream_t st);
+                        bool y32, cudaStream_t st, int gram_mode = 0);
 
 // control.cu
 cudaError_t launch_kappa(const double* G, int ldg, const SolveState* state, int sbar_fixed,

@@ -33,7 +33,7 @@ class Opts(C.Structure):
                 ("newton_scale", C.c_int), ("cheb_params", C.c_int), ("inner_conv_check", C.c_int),
                 ("y_fp32", C.c_int), ("variant", C.c_int), ("check_every", C.c_int),
                 ("use_graph", C.c_int), ("profile", C.c_int), ("c_const", C.c_double),
-                ("eps", C.c_double), ("kappa_cut", C.c_double)]
+                ("eps", C.c_double), ("kappa_cut", C.c_double), ("gram_mode", C.c_int)]
 
 
 class OuterRecord(C.Structure):
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sscg_build_basis": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, _P, _I64]),
         "sscg_gram": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _P]),
         "sscg_gram_noalloc": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _P]),
+        "sscg_gram_ex": (C.c_int, [_P, _I64, _I64, C.c_int, _P, C.c_int, _P]),
         "sscg_kappa": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, _P, _P, _P, _P]),
         "sscg_leja": (C.c_int, [C.c_int, _P]),
         "sscg_stencil_face_grad": (C.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -275,6 +276,11 @@ def sscg_build_basis(h: int, p, r, s: int, theta, gamma, mu, Y, ldy: int) -> Non
 
 def sscg_gram(Y, n: int, ldy: int, ncols: int, G, stream=None) -> None:
     _check(load_library().sscg_gram(_f64(Y), n, ldy, ncols, _f64(G), _stream_ptr(stream)), "sscg_gram")
+
+
+def sscg_gram_ex(Y, n: int, ldy: int, ncols: int, G, mode: int, stream=None) -> None:
+    """G = Y^T Y with binary64 products (mode 0) or binary32-pair products (mode 1)."""
+    _check(load_library().sscg_gram_ex(_f64(Y), n, ldy, ncols, _f64(G), mode, _stream_ptr(stream)), "sscg_gram_ex")
 
 
 def sscg_gram_noalloc(Y, n: int, ldy: int, ncols: int, G, stream=None) -> None:

@@ -379,3 +379,45 @@ def test_failure_detection_injected_on_the_host(pkg):
     xt = dev(x0)
     st4 = s.solve(dev(b), xt, tol=1e-10, s_max=4)
     assert st4.status == 0 and st4.true_relres <= 1e-10
+
+
+@pytest.mark.parametrize("n,ncols", [(1, 1), (777, 5), (10007, 33), (300000, 33)])
+def test_gram_binary32_pair_mode(pkg, n, ncols):
+    """gram_mode 1 against binary64: each term carries at most ~2^-46 relative
+    error, so G agrees to 1e-13 relative to sqrt(G_ii G_jj), including columns
+    whose scales differ by 10^8 and a column of exact zeros."""
+    rng = np.random.default_rng(n + 7 * ncols)
+    Y = rng.standard_normal((n, ncols)) * np.logspace(-4, 4, ncols)[None, :]
+    if ncols > 2:
+        Y[:, 1] = 0.0
+    ld = n + 1
+    Yd = torch.zeros(ld * ncols, dtype=torch.float64, device="cuda")
+    Yd.reshape(ncols, ld)[:, :n] = dev(Y.T)
+    G1 = torch.zeros(ncols * ncols, dtype=torch.float64, device="cuda")
+    pkg.sscg.sscg_gram_ex(Yd, n, ld, ncols, G1, 1)
+    Gg = G1.reshape(ncols, ncols).cpu().numpy()
+    Go = Y.T @ Y
+    d = np.sqrt(np.outer(np.diag(Go), np.diag(Go)))
+    d[d == 0] = 1.0
+    assert np.max(np.abs(Gg - Go) / d) <= 1e-13
+    assert np.array_equal(Gg, Gg.T)
+
+
+@pytest.mark.parametrize("name", ["poisson", "varcoef3d"])
+def test_solve_with_binary32_pair_gram(pkg, name):
+    if name == "poisson":
+        A, b, x0, _ = gen.config_problem("poisson2d_64")
+        M = as_matrix(A)
+        s = pkg.Solver.csr(A.rowptr, A.col, A.val)
+        smax, basis = 8, "chebyshev"
+    else:
+        st_ = gen.varcoef_stencil((32, 32, 32), seed=1001)
+        b = gen.random_rhs(st_.n, 8)
+        x0 = np.zeros(st_.n)
+        M = as_matrix(st_)
+        s = stencil_solver(pkg, st_)
+        smax, basis = 16, "newton"
+    x_o, info = cg.sstep_cg(M, b, x0, 1e-10, cg.Options(smax=smax, basis=basis))
+    xt = dev(x0)
+    st = s.solve(dev(b), xt, tol=1e-10, s_max=smax, basis=basis, hist_cap=4000, gram_mode=1)
+    compare_solves(xt.cpu().numpy(), st, pkg.sscg.history(st), x_o, info, 1e-10, strict=(name == "poisson"))
