@@ -48,6 +48,8 @@ WORKLOADS = {
                          scale=96),
 }
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
+FP32_PEAK_TINST = 152 * 128 * 2.070e9 / 1e12  # 152 SMs x 128 binary32 lanes/clk x 2070 MHz
+FF_OPS_PER_PRODUCT = 13                       # binary32 instructions per pair and row (gram_mode 1)
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -417,6 +419,23 @@ def main():
     if hist and hasattr(op, "kx"):
         gram_traffic = sum(8.0 * n * (2 * h["sbar"] + 1) + 3.4e6 for h in hist) / len(hist)
     launches = sum(s.kernel_launches for s in stats)
+    if args.gram_mode == 0:
+        roofline = {"bound": "alu", "kernel": "gram_partial+gram_reduce (G = Y^T Y, FP64)",
+                    "achieved": gram_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": (gram_tflops / FP64_PEAK_TFLOPS) if gram_tflops else None,
+                    "traffic": gram_traffic, "launches": n_gram,
+                    "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 is not in "
+                                 "MEASURED_PEAKS.json)"}
+    else:
+        # binary32-pair Gram: 13 binary32 instructions per unique (i <= j) pair and row
+        # (one binary64 FMA is 2 flop, so gram_flops / 2 is pairs x rows)
+        tinst = FF_OPS_PER_PRODUCT * (f_gram / 2) / t_gram / 1e12 if t_gram > 0 else None
+        roofline = {"bound": "alu", "kernel": "gram_partial_ff+gram_reduce (G = Y^T Y, binary32 pairs)",
+                    "achieved": tinst, "peak": FP32_PEAK_TINST, "unit": "T binary32 inst/s",
+                    "frac": (tinst / FP32_PEAK_TINST) if tinst else None,
+                    "traffic": gram_traffic, "launches": n_gram,
+                    "gram_fp64_equiv_tflops": gram_tflops,
+                    "peak_note": "derived: 152 SMs x 128 binary32 lanes/clk x 2070 MHz"}
 
     # ---- HSCG on the same GPU
     hs = []
@@ -481,12 +500,7 @@ def main():
             "ms_per_outer_loop": ms_per_step / st0.outer_iters,
             "hbm_gbs_alg": hbm_gbs, "phase_ms_per_solve": phase_ms,
             "hscg": hscg,
-            "roofline": {"bound": "alu", "kernel": "gram_partial+gram_reduce (G = Y^T Y, FP64)",
-                         "achieved": gram_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": (gram_tflops / FP64_PEAK_TFLOPS) if gram_tflops else None,
-                         "traffic": gram_traffic, "launches": n_gram,
-                         "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 is not in "
-                                      "MEASURED_PEAKS.json)"},
+            "roofline": roofline,
             "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line))

@@ -128,6 +128,7 @@ int ensure_solve_buffers(sscg_ctx* h, int sigma, int hist_cap, bool y32 = false)
   CK(h->Y.ensure(ycount));
   const int gb = gram_blocks(n);
   const int rb = reduce_blocks(n);
+  CK(gram_prepare());
   CK(h->partials.ensure(std::max((size_t)gb * kMaxPairs, (size_t)4 * rb)));
   CK(h->rt.ensure(n));
   CK(h->b.ensure(n));
@@ -1046,6 +1047,7 @@ int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, 
     return SSCG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int nb = gram_blocks(n);
+  CK(gram_prepare());
   DevBuf<double> part;
   CK(part.ensure((size_t)nb * kMaxPairs));
   CK(launch_gram(Y, n, ldy, nullptr, ncols, nullptr, part.p, nb, G, ncols, false, st, mode));

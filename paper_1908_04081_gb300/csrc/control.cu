@@ -29,21 +29,38 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // ------------------------------------------------------------------ kappa
+// On GB300 every binary64 instruction occupies its SM sub-partition's FP64
+// unit for about 64 cycles per warp, whether 1 or 32 lanes are active, so the
+// latency of these one-block kernels is the count of binary64 instructions on
+// each warp's path.  The kappa step therefore keeps sign and zero tests in
+// integer arithmetic, brackets each extreme eigenvalue with a cheap binary32
+// Sturm multisection first, and spends binary64 Sturm sequences only on the
+// last ~35 bits.
+
 // Number of eigenvalues of the symmetric tridiagonal (d, e2 = squared
 // off-diagonals) that are smaller than x: sign changes of the Sturm sequence
-// p_0 = 1, p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2}.  Division free; an
-// exact zero p_i is replaced by a tiny value of the opposite sign of p_{i-1}.
-__device__ int sturm_count(const double* d, const double* e2, int n, double x) {
+// p_0 = 1, p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2}.  Division free, three
+// binary64 operations per step; an exact zero p_i is replaced by a tiny value
+// of the opposite sign of p_{i-1}; the sequence is rescaled by a power of two
+// when it leaves [2^-600, 2^600].
+__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int n, double x) {
   double pm = 1.0;
   double p = d[0] - x;
-  if (p == 0.0) p = -1e-300;
-  int cnt = p < 0.0 ? 1 : 0;
+  long long pb = __double_as_longlong(p);
+  if ((pb << 1) == 0) {
+    p = -1e-300;
+    pb = __double_as_longlong(p);
+  }
+  int cnt = (int)((unsigned long long)pb >> 63);
   for (int i = 1; i < n; ++i) {
     double q = fma(d[i] - x, p, -(e2[i - 1] * pm));
-    if (q == 0.0) q = p < 0.0 ? 1e-300 : -1e-300;
-    cnt += ((q < 0.0) != (p < 0.0)) ? 1 : 0;
-    // keep the sequence in range (both terms by the same power of two)
-    const int ex = (int)((__double_as_longlong(q) >> 52) & 0x7ff);
+    long long qb = __double_as_longlong(q);
+    if ((qb << 1) == 0) {
+      q = pb < 0 ? 1e-300 : -1e-300;
+      qb = __double_as_longlong(q);
+    }
+    cnt += (int)((unsigned long long)(qb ^ pb) >> 63);
+    const int ex = (int)((qb >> 52) & 0x7ff);
     if (ex > 1023 + 600 || ex < 1023 - 600) {
       const double sc = ex > 1023 ? 0x1p-600 : 0x1p600;
       q *= sc;
@@ -51,36 +68,56 @@ __device__ int sturm_count(const double* d, const double* e2, int n, double x) {
     }
     pm = p;
     p = q;
+    pb = qb;
   }
   return cnt;
 }
 
-// Multisection by one warp: 32 points per round in (lo, hi).  `target` is the
-// count threshold: the result is the point where count(x) first reaches it.
-__device__ double warp_multisection(const double* d, const double* e2, int n, double lo, double hi, int target) {
+// The same count in binary32 with the ratio form q_i = (d_i - x) - e2_{i-1} / q_{i-1}
+// (negative q_i counted; |q_i| below pivmin replaced by -pivmin).  Used only to
+// bracket an eigenvalue; the bracket is checked in binary64 before use.
+__device__ __forceinline__ int sturm_count32(const float* d, const float* e2, int n, float x) {
+  const float pivmin = 1e-30f;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int cnt = q < 0.f ? 1 : 0;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q < 0.f ? 1 : 0;
+  }
+  return cnt;
+}
+
+// binary32 multisection by one warp: 32 points per round in (lo, hi); the
+// result brackets the point where count first reaches `target`.
+__device__ void warp_bracket32(const float* d, const float* e2, int n, float lo, float hi, int target, int rounds,
+                               float* out_lo, float* out_hi) {
   const int lane = threadIdx.x & 31;
-  for (int round = 0; round < 16; ++round) {
-    const double step = (hi - lo) * (1.0 / 33.0);
-    const double x = lo + step * (double)(lane + 1);
-    const int c = sturm_count(d, e2, n, x);
-    const unsigned ball = __ballot_sync(0xffffffffu, c >= target);
+  for (int round = 0; round < rounds; ++round) {
+    const float step = (hi - lo) * (1.0f / 33.0f);
+    const float x = lo + step * (float)(lane + 1);
+    const unsigned ball = __ballot_sync(0xffffffffu, sturm_count32(d, e2, n, x) >= target);
     const int f = ball ? __ffs(ball) - 1 : 32;
-    const double xf = __shfl_sync(0xffffffffu, x, f & 31);
-    const double xfm = __shfl_sync(0xffffffffu, x, (f - 1) & 31);
-    const double nlo = f == 0 ? lo : xfm;
-    const double nhi = f == 32 ? hi : xf;
+    const float xf = __shfl_sync(0xffffffffu, x, f & 31);
+    const float xfm = __shfl_sync(0xffffffffu, x, (f - 1) & 31);
+    const float nlo = f == 0 ? lo : xfm;
+    const float nhi = f == 32 ? hi : xf;
     lo = nlo;
     hi = nhi;
-    if (hi - lo <= 0x1p-56) break;  // absolute, on the normalised matrix
   }
-  return 0.5 * (lo + hi);
+  *out_lo = lo;
+  *out_hi = hi;
 }
 
 // One block per l = 1..sbar: Householder tridiagonalisation of the leading
 // (2l+1) block of G, then its extreme eigenvalues by multisection;
 // kappa_l = sqrt(lmax/lmin) (Section 3: kappa(Y_l) ~ sqrt(kappa(G_l))).
+// Four warps: the Householder steps use all of them; in the multisection warps
+// 0-1 find lambda_min and warps 2-3 lambda_max (64 binary64 points per round).
 __device__ void kappa_body(const double* __restrict__ G, int ldg, int l, double kappa_cut,
                            double* __restrict__ kap, double* __restrict__ lmin_out, double* __restrict__ lmax_out) {
+  static_assert(kKappaThreads == 128, "four warps");
   const int n = 2 * l + 1;
   const int t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
@@ -88,7 +125,10 @@ __device__ void kappa_body(const double* __restrict__ G, int ldg, int l, double 
   __shared__ double A[kMaxCols][kMaxCols + 1];
   __shared__ double v[kMaxCols], p[kMaxCols], w[kMaxCols];
   __shared__ double dd[kMaxCols], ee[kMaxCols], e2[kMaxCols];
+  __shared__ float df[kMaxCols], ef2[kMaxCols];
   __shared__ double sh[4];
+  __shared__ int sh_skip;
+  __shared__ unsigned masks[2][4];
 
   for (int e = t; e < n * n; e += kKappaThreads) {
     const int i = e / n, j = e - (e / n) * n;
@@ -97,32 +137,34 @@ __device__ void kappa_body(const double* __restrict__ G, int ldg, int l, double 
   __syncthreads();
 
   for (int k = 0; k + 2 < n; ++k) {
-    const int m = n - k - 1;  // trailing block rows k+1..n-1
+    const int m = n - k - 1;  // trailing block rows k+1..n-1, m <= 32
     if (warp == 0) {
       const double xi = lane < m ? A[k + 1 + lane][k] : 0.0;
-      const double all = warp_sum(xi * xi);
-      const double rest = warp_sum(lane >= 1 && lane < m ? xi * xi : 0.0);
+      const double rest = warp_sum(lane >= 1 ? xi * xi : 0.0);
       if (lane == 0) {
-        sh[0] = all;
-        sh[1] = rest;
+        if (rest == 0.0) {  // already tridiagonal in this column
+          sh_skip = 1;
+          dd[k] = A[k][k];
+          ee[k] = xi;
+        } else {
+          const double sig2 = fma(xi, xi, rest);
+          const double alpha = xi >= 0.0 ? -sqrt(sig2) : sqrt(sig2);
+          const double v0 = xi - alpha;
+          sh_skip = 0;
+          sh[0] = 2.0 / (rest + v0 * v0);  // tau
+          sh[1] = alpha;
+          v[0] = v0;
+        }
+      } else if (lane < m) {
+        v[lane] = xi;
       }
     }
     __syncthreads();
-    const double sig2 = sh[0], rest = sh[1];
-    const double x0 = A[k + 1][k];
-    if (rest == 0.0) {  // already tridiagonal in this column
-      if (t == 0) {
-        dd[k] = A[k][k];
-        ee[k] = x0;
-      }
-      __syncthreads();
+    if (sh_skip) {
+      __syncthreads();  // the next step's warp 0 reads what thread 0 wrote
       continue;
     }
-    const double alpha = x0 >= 0.0 ? -sqrt(sig2) : sqrt(sig2);
-    const double v0 = x0 - alpha;
-    const double tau = 2.0 / (rest + v0 * v0);
-    if (t < m) v[t] = t == 0 ? v0 : A[k + 1 + t][k];
-    __syncthreads();
+    const double tau = sh[0];
     // p = tau * A_sub v, four threads per row (m <= 32: one pass, all lanes shuffle)
     {
       const int i = t >> 2;
@@ -136,27 +178,26 @@ __device__ void kappa_body(const double* __restrict__ G, int ldg, int l, double 
     __syncthreads();
     if (warp == 0) {
       const double pv = warp_sum(lane < m ? p[lane] * v[lane] : 0.0);
-      if (lane == 0) sh[2] = 0.5 * tau * pv;
+      const double K = 0.5 * tau * pv;
+      if (lane < m) w[lane] = fma(-K, v[lane], p[lane]);
     }
     __syncthreads();
-    const double K = sh[2];
-    if (t < m) w[t] = p[t] - K * v[t];
-    __syncthreads();
-    // A_sub -= v w^T + w v^T on the lower triangle, mirrored to the upper one
-    for (int e = t; e < m * (m + 1) / 2; e += kKappaThreads) {
-      int i = 0, rem = e;
-      while (rem > i) {
-        rem -= i + 1;
-        ++i;
+    // A_sub -= v w^T + w v^T on the lower triangle, mirrored: four threads per
+    // row, columns j = (t & 3) + 4c <= i
+    {
+      const int i = t >> 2;
+      if (i < m) {
+        const double vi = v[i], wi = w[i];
+        for (int j = t & 3; j <= i; j += 4) {
+          const double val = fma(-vi, w[j], fma(-wi, v[j], A[k + 1 + i][k + 1 + j]));
+          A[k + 1 + i][k + 1 + j] = val;
+          A[k + 1 + j][k + 1 + i] = val;
+        }
       }
-      const int j = rem;
-      const double val = fma(-v[i], w[j], fma(-w[i], v[j], A[k + 1 + i][k + 1 + j]));
-      A[k + 1 + i][k + 1 + j] = val;
-      A[k + 1 + j][k + 1 + i] = val;
     }
     if (t == 0) {
       dd[k] = A[k][k];
-      ee[k] = alpha;
+      ee[k] = sh[1];
     }
     __syncthreads();
   }
@@ -167,42 +208,102 @@ __device__ void kappa_body(const double* __restrict__ G, int ldg, int l, double 
   }
   __syncthreads();
 
-  // normalise by a power of two near the Gershgorin bound (exact scaling)
+  // Gershgorin interval (warp 0, lanes over rows), then normalisation by a
+  // power of two near its largest magnitude (exact scaling)
   __shared__ double glo, ghi;
   __shared__ int sc_exp;
-  if (t == 0) {
+  if (warp == 0) {
     double lo = 1e308, hi = -1e308;
-    for (int i = 0; i < n; ++i) {
+    for (int i = lane; i < n; i += 32) {
       const double r = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i < n - 1 ? fabs(ee[i]) : 0.0);
       lo = fmin(lo, dd[i] - r);
       hi = fmax(hi, dd[i] + r);
     }
-    const double mag = fmax(fabs(lo), fabs(hi));
-    int ex = mag > 0.0 ? (int)((__double_as_longlong(mag) >> 52) & 0x7ff) - 1023 : 0;
-    sc_exp = ex;
-    const double sc = ldexp(1.0, -ex);
-    glo = lo * sc;
-    ghi = hi * sc;
-  }
-  __syncthreads();
-  const double sc = ldexp(1.0, -sc_exp);
-  if (t < n) {
-    dd[t] = dd[t] * sc;
-    if (t < n - 1) {
-      const double es = ee[t] * sc;
-      e2[t] = es * es;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      const double mag = fmax(fabs(lo), fabs(hi));
+      const int ex = mag > 0.0 ? (int)((__double_as_longlong(mag) >> 52) & 0x7ff) - 1023 : 0;
+      sc_exp = ex;
+      const double sc = ldexp(1.0, -ex);
+      glo = lo * sc - 0x1p-50;
+      ghi = hi * sc + 0x1p-50;
     }
   }
   __syncthreads();
-  const double lo0 = glo - 0x1p-50, hi0 = ghi + 0x1p-50;
-  __shared__ double ev[2];
-  if (warp == 0) {
-    const double r = warp_multisection(dd, e2, n, lo0, hi0, 1);
-    if (lane == 0) ev[0] = r;
-  } else if (warp == 1) {
-    const double r = warp_multisection(dd, e2, n, lo0, hi0, n);
-    if (lane == 0) ev[1] = r;
+  {
+    const double sc = ldexp(1.0, -sc_exp);
+    if (t < n) {
+      dd[t] = dd[t] * sc;
+      df[t] = (float)dd[t];
+      if (t < n - 1) {
+        const double es = ee[t] * sc;
+        e2[t] = es * es;
+        ef2[t] = (float)e2[t];
+      }
+    }
   }
+  __syncthreads();
+
+  // warps 0-1: lambda_min (count reaches 1); warps 2-3: lambda_max (count reaches n)
+  const int pair = warp >> 1;
+  const int target = pair == 0 ? 1 : n;
+  const double g_lo = glo, g_hi = ghi;
+  __shared__ double br[2][2];
+  if ((warp & 1) == 0) {  // binary32 bracket by the pair's first warp
+    float blo, bhi;
+    warp_bracket32(df, ef2, n, (float)g_lo, (float)g_hi, target, 4, &blo, &bhi);
+    if (lane == 0) {
+      br[pair][0] = fmax(g_lo, (double)blo - 0x1p-16);
+      br[pair][1] = fmin(g_hi, (double)bhi + 0x1p-16);
+    }
+  }
+  __syncthreads();
+  double lo = br[pair][0], hi = br[pair][1];
+  const int k64 = lane + 32 * (warp & 1);  // this thread's point, 0..63
+  bool done = false;
+  constexpr int kRounds = 10;
+  for (int round = 0; round < kRounds; ++round) {
+    // round 0: points lo + (hi - lo) k / 63 including both ends (checks the
+    // binary32 bracket); later rounds: interior points lo + (hi - lo)(k + 1) / 65
+    const double step = round == 0 ? (hi - lo) * (1.0 / 63.0) : (hi - lo) * (1.0 / 65.0);
+    const double x = lo + step * (double)(round == 0 ? k64 : k64 + 1);
+    if (!done) {
+      const unsigned ball = __ballot_sync(0xffffffffu, sturm_count(dd, e2, n, x) >= target);
+      if (lane == 0) masks[round & 1][warp] = ball;
+    }
+    __syncthreads();
+    if (!done) {
+      const unsigned long long M = (unsigned long long)masks[round & 1][2 * pair] |
+                                   ((unsigned long long)masks[round & 1][2 * pair + 1] << 32);
+      if (round == 0) {
+        if ((M & 1ull) || !(M >> 63)) {  // the bracket does not hold: start from Gershgorin
+          lo = g_lo;
+          hi = g_hi;
+        } else {
+          const int f = __ffsll((long long)M) - 1;  // >= 1
+          const double nlo = lo + step * (double)(f - 1);
+          const double nhi = lo + step * (double)f;
+          lo = nlo;
+          hi = nhi;
+        }
+      } else {
+        const int f = M ? __ffsll((long long)M) - 1 : 64;
+        const double nlo = f == 0 ? lo : lo + step * (double)f;
+        const double nhi = f == 64 ? hi : lo + step * (double)(f + 1);
+        lo = nlo;
+        hi = nhi;
+      }
+      // 2^-56 absolute on the normalised matrix (small lambda_min keeps its
+      // relative accuracy), or 4 ulps of the larger endpoint
+      done = hi - lo <= fmax(0x1p-56, 0x1p-50 * fmax(fabs(lo), fabs(hi)));
+    }
+  }
+  __shared__ double ev[2];
+  if ((warp & 1) == 0 && lane == 0) ev[pair] = 0.5 * (lo + hi);
   __syncthreads();
   if (t == 0) {
     const double lmn = ldexp(ev[0], sc_exp), lmx = ldexp(ev[1], sc_exp);

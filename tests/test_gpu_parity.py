@@ -381,7 +381,8 @@ def test_failure_detection_injected_on_the_host(pkg):
     assert st4.status == 0 and st4.true_relres <= 1e-10
 
 
-@pytest.mark.parametrize("n,ncols", [(1, 1), (777, 5), (10007, 33), (300000, 33)])
+@pytest.mark.parametrize("n,ncols", [(1, 1), (2, 2), (777, 5), (513, 4), (10007, 33), (70001, 17),
+                                     (300000, 33), (1000003, 9)])
 def test_gram_binary32_pair_mode(pkg, n, ncols):
     """gram_mode 1 against binary64: each term carries at most ~2^-46 relative
     error, so G agrees to 1e-13 relative to sqrt(G_ii G_jj), including columns
@@ -403,7 +404,26 @@ def test_gram_binary32_pair_mode(pkg, n, ncols):
     assert np.array_equal(Gg, Gg.T)
 
 
-@pytest.mark.parametrize("name", ["poisson", "varcoef3d"])
+def test_gram_binary32_pair_nonfinite(pkg):
+    """A NaN or Inf in Y reaches the entries of G that it touches in
+    gram_mode 1, as it does in binary64 (the solver's non-finite check relies
+    on it)."""
+    n, ncols = 5000, 7
+    rng = np.random.default_rng(3)
+    Y = rng.standard_normal((n, ncols))
+    Y[1234, 2] = np.inf
+    Y[4321, 5] = np.nan
+    Yd = dev(np.ascontiguousarray(Y.T).ravel())
+    G1 = torch.zeros(ncols * ncols, dtype=torch.float64, device="cuda")
+    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G1, 1)
+    Gg = G1.reshape(ncols, ncols).cpu().numpy()
+    for j in range(ncols):
+        assert not np.isfinite(Gg[2, j]) and not np.isfinite(Gg[5, j])
+    keep = [0, 1, 3, 4, 6]
+    assert np.all(np.isfinite(Gg[np.ix_(keep, keep)]))
+
+
+@pytest.mark.parametrize("name", ["poisson", "varcoef3d", "varcoef3d_y32"])
 def test_solve_with_binary32_pair_gram(pkg, name):
     if name == "poisson":
         A, b, x0, _ = gen.config_problem("poisson2d_64")
@@ -417,7 +437,9 @@ def test_solve_with_binary32_pair_gram(pkg, name):
         M = as_matrix(st_)
         s = stencil_solver(pkg, st_)
         smax, basis = 16, "newton"
-    x_o, info = cg.sstep_cg(M, b, x0, 1e-10, cg.Options(smax=smax, basis=basis))
+    y32 = name.endswith("_y32")
+    x_o, info = cg.sstep_cg(M, b, x0, 1e-10, cg.Options(smax=smax, basis=basis, y_fp32=y32))
     xt = dev(x0)
-    st = s.solve(dev(b), xt, tol=1e-10, s_max=smax, basis=basis, hist_cap=4000, gram_mode=1)
+    st = s.solve(dev(b), xt, tol=1e-10, s_max=smax, basis=basis, hist_cap=4000, gram_mode=1,
+                 y_fp32=int(y32))
     compare_solves(xt.cpu().numpy(), st, pkg.sscg.history(st), x_o, info, 1e-10, strict=(name == "poisson"))
