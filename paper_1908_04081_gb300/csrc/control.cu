@@ -40,9 +40,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Number of eigenvalues of the symmetric tridiagonal (d, e2 = squared
 // off-diagonals) that are smaller than x: sign changes of the Sturm sequence
 // p_0 = 1, p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2}.  Division free, three
-// binary64 operations per step; an exact zero p_i is replaced by a tiny value
-// of the opposite sign of p_{i-1}; the sequence is rescaled by a power of two
-// when it leaves [2^-600, 2^600].
+// binary64 operations per step.  The guards stay off the binary64 unit: one
+// integer test of q's exponent (outside [2^-600, 2^600], or zero) leads to a
+// warp-uniform rare branch that replaces an exact zero by a tiny value of the
+// opposite sign of p_{i-1} and rescales the sequence by a power of two; sign
+// changes are counted on the sign bits.  Called by whole warps.
 __device__ __forceinline__ int sturm_count(const double* d, const double* e2, int n, double x) {
   double pm = 1.0;
   double p = d[0] - x;
@@ -55,17 +57,19 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
   for (int i = 1; i < n; ++i) {
     double q = fma(d[i] - x, p, -(e2[i - 1] * pm));
     long long qb = __double_as_longlong(q);
-    if ((qb << 1) == 0) {
-      q = pb < 0 ? 1e-300 : -1e-300;
-      qb = __double_as_longlong(q);
+    const unsigned ex = (unsigned)(qb >> 52) & 0x7ffu;
+    const bool odd = ex - 423u > 1200u;  // biased exponent outside [423, 1623]
+    if (__any_sync(0xffffffffu, odd)) {
+      if (odd) {
+        if ((qb << 1) == 0) q = pb < 0 ? 1e-300 : -1e-300;
+        const unsigned eq = (unsigned)(__double_as_longlong(q) >> 52) & 0x7ffu;
+        const double sc = eq > 1023u ? 0x1p-600 : 0x1p600;
+        q *= sc;
+        p *= sc;
+        qb = __double_as_longlong(q);
+      }
     }
     cnt += (int)((unsigned long long)(qb ^ pb) >> 63);
-    const int ex = (int)((qb >> 52) & 0x7ff);
-    if (ex > 1023 + 600 || ex < 1023 - 600) {
-      const double sc = ex > 1023 ? 0x1p-600 : 0x1p600;
-      q *= sc;
-      p *= sc;
-    }
     pm = p;
     p = q;
     pb = qb;
@@ -123,32 +127,48 @@ __device__ void kappa_body(const double* __restrict__ G, int ldg, int l, double 
   const int lane = t & 31, warp = t >> 5;
 
   __shared__ double A[kMaxCols][kMaxCols + 1];
-  __shared__ double v[kMaxCols], p[kMaxCols], w[kMaxCols];
+  __shared__ double v[kMaxCols], w[kMaxCols], spart[3][32];
   __shared__ double dd[kMaxCols], ee[kMaxCols], e2[kMaxCols];
   __shared__ float df[kMaxCols], ef2[kMaxCols];
-  __shared__ double sh[4];
+  __shared__ double sh[2];
   __shared__ int sh_skip;
   __shared__ unsigned masks[2][4];
+  constexpr int kTri = 32 * 33 / 2;  // lower triangle of the largest trailing block
+  __shared__ unsigned char tri_i[kTri], tri_j[kTri];
 
   for (int e = t; e < n * n; e += kKappaThreads) {
     const int i = e / n, j = e - (e / n) * n;
     A[i][j] = G[i * ldg + j];
   }
+  if (t < 32) {  // entry e = i (i + 1) / 2 + j of the lower triangle, j <= i; thread t fills row t
+    const int base = t * (t + 1) / 2;
+    for (int j = 0; j <= t; ++j) {
+      tri_i[base + j] = (unsigned char)t;
+      tri_j[base + j] = (unsigned char)j;
+    }
+  }
   __syncthreads();
 
+  // Householder step k with x = A(k+1:n-1, k), v = x - alpha e_0:
+  //   warp 0:    rest = |x(1:)|^2, alpha = -sign(x_0) |x|, tau = 2 / (v^T v)
+  //   warps 1-3: s = A_sub x, concurrently (3 threads per row)
+  //   warp 0:    p = tau (s - alpha A_sub e_0) = tau A_sub v, K = tau p^T v / 2, w = p - K v
+  //   all:       A_sub -= v w^T + w v^T on the lower triangle (balanced), mirrored
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;  // trailing block rows k+1..n-1, m <= 32
     if (warp == 0) {
       const double xi = lane < m ? A[k + 1 + lane][k] : 0.0;
       const double rest = warp_sum(lane >= 1 ? xi * xi : 0.0);
       if (lane == 0) {
-        if (rest == 0.0) {  // already tridiagonal in this column
+        if (__double_as_longlong(rest) == 0) {  // already tridiagonal in this column
           sh_skip = 1;
           dd[k] = A[k][k];
           ee[k] = xi;
         } else {
+          const long long xb = __double_as_longlong(xi);
           const double sig2 = fma(xi, xi, rest);
-          const double alpha = xi >= 0.0 ? -sqrt(sig2) : sqrt(sig2);
+          const double r = sqrt(sig2);
+          const double alpha = (xb >= 0 || (xb << 1) == 0) ? -r : r;
           const double v0 = xi - alpha;
           sh_skip = 0;
           sh[0] = 2.0 / (rest + v0 * v0);  // tau
@@ -158,42 +178,37 @@ __device__ void kappa_body(const double* __restrict__ G, int ldg, int l, double 
       } else if (lane < m) {
         v[lane] = xi;
       }
+    } else {
+      const int u = t - 32, i = u / 3, slot = u - 3 * i;
+      if (i < m) {
+        double sacc = 0.0;
+        for (int j = slot; j < m; j += 3) sacc = fma(A[k + 1 + i][k + 1 + j], A[k + 1 + j][k], sacc);
+        spart[slot][i] = sacc;
+      }
     }
     __syncthreads();
     if (sh_skip) {
-      __syncthreads();  // the next step's warp 0 reads what thread 0 wrote
+      __syncthreads();  // the next step's warp 0 rewrites what every thread just read
       continue;
     }
-    const double tau = sh[0];
-    // p = tau * A_sub v, four threads per row (m <= 32: one pass, all lanes shuffle)
-    {
-      const int i = t >> 2;
-      double s = 0.0;
-      if (i < m)
-        for (int j = t & 3; j < m; j += 4) s = fma(A[k + 1 + i][k + 1 + j], v[j], s);
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      if (i < m && (t & 3) == 0) p[i] = tau * s;
-    }
-    __syncthreads();
     if (warp == 0) {
-      const double pv = warp_sum(lane < m ? p[lane] * v[lane] : 0.0);
+      const double tau = sh[0], alpha = sh[1];
+      double pl = 0.0, vl = 0.0;
+      if (lane < m) {
+        const double sl = (spart[0][lane] + spart[1][lane]) + spart[2][lane];
+        pl = tau * fma(-alpha, A[k + 1 + lane][k + 1], sl);
+        vl = v[lane];
+      }
+      const double pv = warp_sum(pl * vl);
       const double K = 0.5 * tau * pv;
-      if (lane < m) w[lane] = fma(-K, v[lane], p[lane]);
+      if (lane < m) w[lane] = fma(-K, vl, pl);
     }
     __syncthreads();
-    // A_sub -= v w^T + w v^T on the lower triangle, mirrored: four threads per
-    // row, columns j = (t & 3) + 4c <= i
-    {
-      const int i = t >> 2;
-      if (i < m) {
-        const double vi = v[i], wi = w[i];
-        for (int j = t & 3; j <= i; j += 4) {
-          const double val = fma(-vi, w[j], fma(-wi, v[j], A[k + 1 + i][k + 1 + j]));
-          A[k + 1 + i][k + 1 + j] = val;
-          A[k + 1 + j][k + 1 + i] = val;
-        }
-      }
+    for (int e = t; e < m * (m + 1) / 2; e += kKappaThreads) {
+      const int i = tri_i[e], j = tri_j[e];
+      const double val = fma(-v[i], w[j], fma(-w[i], v[j], A[k + 1 + i][k + 1 + j]));
+      A[k + 1 + i][k + 1 + j] = val;
+      A[k + 1 + j][k + 1 + i] = val;
     }
     if (t == 0) {
       dd[k] = A[k][k];
@@ -345,92 +360,107 @@ __device__ __forceinline__ double b_times(const double* pc, int i, int s, const 
   return acc;
 }
 
-// y = G x over the leading n x n block (G in shared memory, 4 threads per row,
-// row passes uniform across the block so every lane joins the shuffles);
-// returns w^T y to thread 0 (other threads get 0).
-__device__ double gmv_dot(const double (*Gs)[kMaxCols + 1], const double* x, const double* w, double* y, int n,
-                          double* red) {
+__device__ __forceinline__ void group_sync(int bar, int nthr) {
+  if (bar == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+}
+
+// w^T G x over the leading n x n block of Gs (shared memory) by threads
+// 0..nthr-1 (whole warps; `bar` = 0: all threads of the block, else a named
+// barrier over those nthr threads).  Every product G_ij x_j is issued once and
+// the binary64 work is spread evenly: rows 0..31 by nthr/32 threads each
+// (columns slot, slot + nthr/32, ...), row 32 (n = 33) one column per thread.
+// The fixed-order reduction returns the sum to thread 0 (others get 0).
+__device__ double gdot(const double (*Gs)[kMaxCols + 1], const double* x, const double* w, int n, int nthr, int bar,
+                       double* red) {
   const int t = threadIdx.x;
+  const int S = nthr >> 5;  // threads per row
+  const int i = t / S, slot = t - i * S;
   double part = 0.0;
-  for (int base = 0; base < n; base += kControlThreads / 4) {
-    const int i = base + (t >> 2);
+  if (i < n) {
     double s = 0.0;
-    if (i < n)
-      for (int j = t & 3; j < n; j += 4) s = fma(Gs[i][j], x[j], s);
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if (i < n && (t & 3) == 0) {
-      y[i] = s;
-      part += w[i] * s;
-    }
+    for (int j = slot; j < n; j += S) s = fma(Gs[i][j], x[j], s);
+    part = w[i] * s;
   }
+  if (n > 32 && t < n) part = fma(w[32] * Gs[32][t], x[t], part);
   part = warp_sum(part);
   if ((t & 31) == 0) red[t >> 5] = part;
-  __syncthreads();
+  group_sync(bar, nthr);
   double q = 0.0;
-  if (t == 0) q = ((red[0] + red[1]) + red[2]) + red[3];
-  __syncthreads();
+  if (t == 0) {
+    q = red[0];
+    for (int k = 1; k < S; ++k) q = q + red[k];
+  }
+  group_sync(bar, nthr);
   return q;
 }
 
 __device__ __forceinline__ double clamp01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
 
-// Algorithms 3-4 fed with alpha_i and beta_{i-1} (thread 0 only).
-__device__ void ritz_push(SolveState* st, double alpha, double beta_prev) {
+// One loop step of Algorithm 3 (upper estimate, xi read as zeta) for alpha_i and
+// beta_{i-1}, with zeta_i = alpha_i^{-1/2} and eta_{i-1} = sqrt(beta_{i-1} /
+// alpha_{i-1}) (eq. lit); the first push initialises.  Reads the state, writes
+// out[0..2] = (omega, h, zeta).
+__device__ void mt_upper(const SolveState* st, double alpha, double beta_prev, double* out) {
+  const double zeta = 1.0 / sqrt(alpha);
+  out[2] = zeta;
+  if (st->mt_n == 0) {
+    out[0] = zeta * zeta;
+    out[1] = 1.0;
+    return;
+  }
+  const double zl = st->zeta_prev, zl1 = zeta;
+  const double eta = sqrt(beta_prev / st->alpha_prev);
+  const double d = zl * zl * eta * eta * st->up_h;
+  const double a = eta * eta + zl1 * zl1;
+  const double dm = st->up_omega - a;
+  const double chi = sqrt(dm * dm + 4.0 * d);
+  if (chi == 0.0) {
+    out[0] = st->up_omega;
+    out[1] = 1.0;
+  } else {
+    const double h = clamp01(0.5 * (1.0 - (st->up_omega - a) / chi));
+    out[1] = h;
+    out[0] = st->up_omega + chi * h;
+  }
+}
+
+// One loop step of Algorithm 4 (lower estimate); out[0..5] = (omega, a, d, g,
+// h, lambda_min = 1/omega).
+__device__ void mt_lower(const SolveState* st, double alpha, double beta_prev, double* out) {
   const double zeta = 1.0 / sqrt(alpha);
   if (st->mt_n == 0) {
-    st->up_omega = zeta * zeta;
-    st->up_h = 1.0;
-    st->lo_omega = 1.0 / (zeta * zeta);
-    st->lo_a = st->lo_omega;
-    st->lo_d = 0.0;
-    st->lo_g = 0.0;
-    st->lo_h = 1.0;
-    st->lmax = st->up_omega;
-    st->lmin = 1.0 / st->lo_omega;
-  } else {
-    const double zl = st->zeta_prev, zl1 = zeta;
-    const double eta = sqrt(beta_prev / st->alpha_prev);
-    // Algorithm 3 (xi read as zeta)
-    {
-      const double d = zl * zl * eta * eta * st->up_h;
-      const double a = eta * eta + zl1 * zl1;
-      const double dm = st->up_omega - a;
-      const double chi = sqrt(dm * dm + 4.0 * d);
-      if (chi == 0.0) {
-        st->up_h = 1.0;
-      } else {
-        st->up_h = clamp01(0.5 * (1.0 - (st->up_omega - a) / chi));
-        st->up_omega = st->up_omega + chi * st->up_h;
-      }
-    }
-    // Algorithm 4
-    {
-      const double d1 = -(eta / zl1) * (st->lo_g * st->lo_d + st->lo_h * st->lo_a);
-      const double a1 = (eta * eta * st->lo_a + 1.0) / (zl1 * zl1);
-      const double dm = st->lo_omega - a1;
-      const double chi = sqrt(dm * dm + 4.0 * d1 * d1);
-      double h, g;
-      if (chi == 0.0) {
-        h = 1.0;
-        g = 0.0;
-      } else {
-        const double h2 = clamp01(0.5 * (1.0 - (st->lo_omega - a1) / chi));
-        st->lo_omega = st->lo_omega + chi * h2;
-        h = sqrt(h2);
-        g = sqrt(clamp01(1.0 - h2));
-      }
-      st->lo_h = fabs(h) * (d1 < 0.0 ? -1.0 : 1.0);
-      st->lo_g = g;
-      st->lo_d = d1;
-      st->lo_a = a1;
-    }
-    st->lmax = st->up_omega;
-    st->lmin = 1.0 / st->lo_omega;
+    const double om = 1.0 / (zeta * zeta);
+    out[0] = om;
+    out[1] = om;
+    out[2] = 0.0;
+    out[3] = 0.0;
+    out[4] = 1.0;
+    out[5] = 1.0 / om;
+    return;
   }
-  st->zeta_prev = zeta;
-  st->alpha_prev = alpha;
-  st->mt_n += 1;
+  const double zl1 = zeta;
+  const double eta = sqrt(beta_prev / st->alpha_prev);
+  const double d1 = -(eta / zl1) * (st->lo_g * st->lo_d + st->lo_h * st->lo_a);
+  const double a1 = (eta * eta * st->lo_a + 1.0) / (zl1 * zl1);
+  const double dm = st->lo_omega - a1;
+  const double chi = sqrt(dm * dm + 4.0 * d1 * d1);
+  double om = st->lo_omega, h, g;
+  if (chi == 0.0) {
+    h = 1.0;
+    g = 0.0;
+  } else {
+    const double h2 = clamp01(0.5 * (1.0 - (st->lo_omega - a1) / chi));
+    om = st->lo_omega + chi * h2;
+    h = sqrt(h2);
+    g = sqrt(clamp01(1.0 - h2));
+  }
+  out[0] = om;
+  out[1] = a1;
+  out[2] = d1;
+  out[3] = g;
+  out[4] = fabs(h) * (d1 < 0.0 ? -1.0 : 1.0);
+  out[5] = 1.0 / om;
 }
 
 __device__ double c_value(int mode, double lmin, double lmax, double psi, double c_const) {
@@ -443,56 +473,67 @@ __device__ double c_value(int mode, double lmin, double lmax, double psi, double
   }
 }
 
-// Recurrence coefficients for the next outer loops from the Ritz estimates.
-__device__ void basis_update(SolveState* st, const double* leja) {
+// Recurrence coefficients of level l for the next outer loops from the Ritz
+// estimates (one thread per level).
+__device__ void basis_update_level(SolveState* st, const double* leja, int l) {
   const double lmin = st->lmin, lmax = st->lmax;
   const double c = 0.5 * (lmax + lmin);
   const double h = 0.5 * (lmax - lmin);
-  for (int l = 0; l < st->sigma; ++l) {
-    double th = 0.0, ga = 1.0, mu = 0.0;
-    if (st->basis == SSCG_NEWTON) {
-      th = c + h * leja[l];
-      ga = st->newton_scale == 0 ? (lmax - lmin) / 4.0 : 1.0;
-    } else if (st->basis == SSCG_CHEBYSHEV) {
-      th = c;
-      if (st->cheb_params == 0) {
-        ga = l == 0 ? h : 0.5 * h;
-        mu = 0.5 * h;
-      } else {
-        ga = l == 0 ? lmax - lmin : 0.5 * (lmax - lmin);
-        mu = 2.0 * (lmax - lmin);
-      }
+  double th = 0.0, ga = 1.0, mu = 0.0;
+  if (st->basis == SSCG_NEWTON) {
+    th = c + h * leja[l];
+    ga = st->newton_scale == 0 ? (lmax - lmin) / 4.0 : 1.0;
+  } else if (st->basis == SSCG_CHEBYSHEV) {
+    th = c;
+    if (st->cheb_params == 0) {
+      ga = l == 0 ? h : 0.5 * h;
+      mu = 0.5 * h;
+    } else {
+      ga = l == 0 ? lmax - lmin : 0.5 * (lmax - lmin);
+      mu = 2.0 * (lmax - lmin);
     }
-    st->theta[l] = th;
-    st->gamma[l] = ga;
-    st->inv_gamma[l] = 1.0 / ga;
-    st->mu[l] = mu;
   }
+  st->theta[l] = th;
+  st->gamma[l] = ga;
+  st->inv_gamma[l] = 1.0 / ga;
+  st->mu[l] = mu;
 }
 
+// Thread roles (128 threads).  Each inner step: all threads form p'^T G (B p');
+// then warps 2 and 3 run the two Meurant-Tichy recurrences (they need only
+// alpha_j and beta_{j-1}) while warps 0-1 update x', r' and form r'^T G r' and
+// thread 0 the scalars that do not depend on the Ritz values; thread 0 then
+// commits the Ritz state and takes the c update and the break test.
 __device__ void control_body(SolveState* __restrict__ st, const double* __restrict__ G, int ldg,
                              const double* __restrict__ leja, sscg_outer_record* __restrict__ hist) {
+  static_assert(kControlThreads == 128, "four warps");
   const int t = threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
   __shared__ double Gs[kMaxCols][kMaxCols + 1];
-  __shared__ double xc[kMaxCols], rc[kMaxCols], pc[kMaxCols], bp[kMaxCols], u[kMaxCols];
+  __shared__ double xc[kMaxCols], rc[kMaxCols], pc[kMaxCols], bp[kMaxCols];
   __shared__ double th[kMaxS], ga[kMaxS], mu[kMaxS];
-  __shared__ double red[4];
-  __shared__ int s_stilde, s_flag;
+  __shared__ double red[4], red2[2];
+  __shared__ double mt_up[3], mt_lo[6];
+  __shared__ int s_stilde, s_flag, s_valid, s_basis;
   __shared__ double s_alpha, s_beta;
 
   const int sbar = st->sbar;
-  if (t == 0) {
-    if (st->variant == 2) st->c = st->c_const;  // Alg. 2: c_k supplied by the user
+  if (warp == 0) {
+    // s-tilde (eq. condy): the largest l <= s-bar with kappa_l below the threshold
+    const double c0 = st->variant == 2 ? st->c_const : st->c;  // Alg. 2: c_k supplied by the user
     int stl = 1;
     if (st->variant == 1) {
       stl = sbar;
     } else {
       const double normr = sqrt(G[1 * ldg + 1]);
-      const double thr = st->tol / (st->c * st->eps * normr / st->normb);
-      for (int l = 1; l <= sbar; ++l)
-        if (st->kappa[l] <= thr) stl = l;
+      const double thr = st->tol / (c0 * st->eps * normr / st->normb);
+      const unsigned ball = __ballot_sync(0xffffffffu, lane >= 1 && lane <= sbar && st->kappa[lane] <= thr);
+      if (ball) stl = 31 - __clz(ball);
     }
-    s_stilde = stl;
+    if (lane == 0) {
+      if (st->variant == 2) st->c = st->c_const;
+      s_stilde = stl;
+    }
   }
   if (t < kMaxS) {
     th[t] = st->theta[t];
@@ -524,7 +565,7 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
   for (int j = 0; j < stl; ++j) {
     if (t < n) bp[t] = b_times(pc, t, stl, th, ga, mu);
     __syncthreads();
-    const double pGBp = gmv_dot(Gs, bp, pc, u, n, red);  // p'^T G (B p')
+    const double pGBp = gdot(Gs, bp, pc, n, kControlThreads, 0, red);  // p'^T G (B p')
     if (t == 0) {
       const double alpha = pGBp > 0.0 ? rr / pGBp : NAN;
       s_flag = 0;
@@ -537,34 +578,62 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
     __syncthreads();
     if (s_flag) break;
     const double alpha = s_alpha;
-    if (t < n) {
-      xc[t] = xc[t] + alpha * pc[t];
-      rc[t] = rc[t] - alpha * bp[t];
+    double beta = 0.0;
+    if (warp >= 2) {
+      if (lane == 0) {
+        if (warp == 2) mt_upper(st, alpha, st->beta_prev, mt_up);
+        else mt_lower(st, alpha, st->beta_prev, mt_lo);
+      }
+    } else {
+      if (t < n) {
+        xc[t] = xc[t] + alpha * pc[t];
+        rc[t] = rc[t] - alpha * bp[t];
+      }
+      group_sync(1, 64);
+      const double rr_new = gdot(Gs, rc, rc, n, 64, 1, red2);
+      if (t == 0) {
+        sk = j + 1;
+        s_flag = 0;
+        s_valid = 0;
+        if (!(rr_new > 0.0) || !isfinite(rr_new)) {
+          conv = 1;
+          s_flag = 1;
+        } else {
+          s_valid = 1;
+          beta = rr_new / rr;
+          s_beta = beta;
+          phi = fmax(phi, sqrt(rr_new));
+          st->psi = st->psi / (st->psi + beta);
+          rr = rr_new;
+          if (st->inner_conv_check && sqrt(rr_new) / st->normb <= st->tol) {
+            conv = 1;
+            s_flag = 2;
+          }
+        }
+      }
     }
     __syncthreads();
-    const double rr_new = gmv_dot(Gs, rc, rc, u, n, red);
-    if (t == 0) {
-      sk = j + 1;
-      s_flag = 0;
-      if (!(rr_new > 0.0) || !isfinite(rr_new)) {
-        conv = 1;
-        s_flag = 1;
-      } else {
-        const double beta = rr_new / rr;
-        s_beta = beta;
-        phi = fmax(phi, sqrt(rr_new));
-        st->psi = st->psi / (st->psi + beta);
-        ritz_push(st, alpha, st->beta_prev);
-        st->beta_prev = beta;
-        if (m0 + j + 1 > 1 && st->variant != 2)
-          st->c = c_value(st->c_mode, st->lmin, st->lmax, st->psi, st->c_const);
-        rr = rr_new;
-        if (st->inner_conv_check && sqrt(rr_new) / st->normb <= st->tol) {
-          conv = 1;
-          s_flag = 2;
-        } else if (st->variant == 2) {
+    if (t == 0 && s_valid) {
+      // commit Algorithms 3-4 for (alpha_j, beta_{j-1})
+      st->up_omega = mt_up[0];
+      st->up_h = mt_up[1];
+      st->lo_omega = mt_lo[0];
+      st->lo_a = mt_lo[1];
+      st->lo_d = mt_lo[2];
+      st->lo_g = mt_lo[3];
+      st->lo_h = mt_lo[4];
+      st->lmax = mt_up[0];
+      st->lmin = mt_lo[5];
+      st->zeta_prev = mt_up[2];
+      st->alpha_prev = alpha;
+      st->mt_n += 1;
+      st->beta_prev = beta;
+      if (m0 + j + 1 > 1 && st->variant != 2)
+        st->c = c_value(st->c_mode, st->lmin, st->lmax, st->psi, st->c_const);
+      if (s_flag != 2) {
+        if (st->variant == 2) {
           // Alg. 2's break test: kappa of the whole block against the current residual
-          if (st->kappa[stl] >= st->tol / (st->c * st->eps * sqrt(rr_new) / st->normb)) s_flag = 2;
+          if (st->kappa[stl] >= st->tol / (st->c * st->eps * sqrt(rr) / st->normb)) s_flag = 2;
         } else if (st->variant != 1 && j < stl - 1 &&
                    st->kappa[j + 2] >= st->tol / (st->c * st->eps * phi / st->normb)) {
           s_flag = 2;
@@ -573,8 +642,8 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
     }
     __syncthreads();
     if (s_flag == 1) break;
-    const double beta = s_beta;
-    if (t < n) pc[t] = rc[t] + beta * pc[t];
+    const double b_ = s_beta;
+    if (t < n) pc[t] = rc[t] + b_ * pc[t];
     __syncthreads();
     if (s_flag == 2) break;
   }
@@ -582,6 +651,7 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
 
   if (t == 0) {
     const int k = st->k;
+    s_basis = 0;
     if (breakdown) {
       st->status = SSCG_BREAKDOWN;
       st->done = 1;
@@ -596,7 +666,7 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
       st->converged_est = conv;
       st->upd_relres = sqrt(rr > 0.0 ? rr : 0.0) / st->normb;
       if (st->m > 1 && st->basis != SSCG_MONOMIAL && st->variant != 2) {
-        basis_update(st, leja);
+        s_basis = 1;
         st->have_ritz = 1;
       }
       int nsb = sk + st->f;
@@ -626,6 +696,8 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
     st->rc[t] = t < n ? rc[t] : 0.0;
     st->pc[t] = t < n ? pc[t] : 0.0;
   }
+  __syncthreads();
+  if (s_basis && t < st->sigma) basis_update_level(st, leja, t);
 }
 
 __global__ void __launch_bounds__(kControlThreads) control_kernel(SolveState* __restrict__ st,

@@ -22,6 +22,8 @@ from sscg_inputs import generators as gen  # noqa: E402
 WORKLOADS = {
     "varcoef3d_160": dict(smax=16, basis="newton", tol=1e-10),
     "poisson2d_64": dict(smax=8, basis="chebyshev", tol=1e-10),
+    "rgg_2m": dict(smax=16, basis="newton", tol=1e-10),
+    "rgg_2m_fp32": dict(smax=16, basis="newton", tol=1e-10, y_fp32=True, base="rgg_2m", hscg=False),
 }
 
 
@@ -30,17 +32,21 @@ def main(names):
     out = json.load(open(path)) if os.path.exists(path) else {}
     for name in names:
         cfg = WORKLOADS[name]
-        op, b, x0, _ = gen.config_problem(name)
+        op, b, x0, _ = gen.config_problem(cfg.get("base", name))
         A = as_matrix(op)
         t = time.time()
-        x, info = cg.sstep_cg(A, b, x0, cfg["tol"], cg.Options(smax=cfg["smax"], basis=cfg["basis"]))
+        x, info = cg.sstep_cg(A, b, x0, cfg["tol"], cg.Options(smax=cfg["smax"], basis=cfg["basis"],
+                                                              y_fp32=cfg.get("y_fp32", False)))
         ts = time.time() - t
-        t = time.time()
-        _, h = cg.hscg(A, b, x0, cfg["tol"])
-        th = time.time() - t
-        out[name] = dict(sstep_outer=info["outer"], sstep_inner=info["inner"], sstep_status=info["status"],
-                         sstep_relres=info["relres_true"], sstep_seconds=ts, hscg_iters=h["iters"],
-                         hscg_seconds=th, cpu_count=os.cpu_count(), **cfg)
+        rec = dict(sstep_outer=info["outer"], sstep_inner=info["inner"], sstep_status=info["status"],
+                   sstep_relres=info["relres_true"], sstep_seconds=ts, cpu_count=os.cpu_count(), **cfg)
+        if "fp32_replacements" in info:
+            rec["fp32_replacements"] = info["fp32_replacements"]
+        if cfg.get("hscg", True):
+            t = time.time()
+            _, h = cg.hscg(A, b, x0, cfg["tol"])
+            rec.update(hscg_iters=h["iters"], hscg_seconds=time.time() - t)
+        out[name] = rec
         json.dump(out, open(path, "w"), indent=1, sort_keys=True)
         print(name, out[name], flush=True)
 
