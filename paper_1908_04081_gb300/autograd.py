@@ -12,6 +12,9 @@ import torch
 
 from . import sscg
 
+# statistics of the most recent forward and adjoint solves (for reporting)
+last_stats: dict = {}
+
 
 class StencilSolve(torch.autograd.Function):
     @staticmethod
@@ -22,6 +25,7 @@ class StencilSolve(torch.autograd.Function):
         st = solver.solve(b.detach().contiguous(), x, tol=tol, s_max=s_max, basis=basis)
         if st.status != sscg.OK:
             raise sscg.SscgError(f"forward solve status {st.status}")
+        last_stats["forward"] = st
         ctx.solver = solver
         ctx.cfg = (tol, s_max, basis)
         ctx.has_kz = kz is not None
@@ -38,6 +42,7 @@ class StencilSolve(torch.autograd.Function):
         st = solver.solve(gx.contiguous(), lam, tol=tol, s_max=s_max, basis=basis)
         if st.status != sscg.OK:
             raise sscg.SscgError(f"adjoint solve status {st.status}")
+        last_stats["adjoint"] = st
         sx, sy, sz = ctx.shapes
         gkx = torch.empty(sx, dtype=x.dtype, device=x.device)
         gky = torch.empty(sy, dtype=x.dtype, device=x.device)

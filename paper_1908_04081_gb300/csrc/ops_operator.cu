@@ -145,6 +145,89 @@ __global__ void __launch_bounds__(kOpThreads) stencil_mpk_kernel(Operator A, T* 
   }
 }
 
+// ------------------------------------------------- 3D stencil, z-marching
+// The 3D SpMV and residual (the HSCG comparator's operator and the true
+// residual) march along z: a block covers a 32 x 8 tile of (x, y) columns and
+// a chunk of kZChunk planes; each thread keeps its column's values at z-1, z,
+// z+1 (and the face coefficient below z) in registers, so per cell it loads
+// the value above and the four lateral neighbours (L1 hits), and all indices
+// advance by a constant per plane (no division).  The sum is formed in the
+// same order as stencil_apply, so results are the same bits as the
+// cell-parallel kernel.  (For the two-chain matrix-powers level the same
+// scheme needs ~60 registers per thread and measured slower than the
+// cell-parallel kernel, which it therefore keeps.)
+constexpr int kZTx = 32, kZTy = 8, kZChunk = 4;
+
+__host__ inline dim3 zmarch_grid(const Operator& A) {
+  return dim3((unsigned)((A.nx + kZTx - 1) / kZTx), (unsigned)((A.ny + kZTy - 1) / kZTy),
+              (unsigned)((A.nz + kZChunk - 1) / kZChunk));
+}
+
+struct ZCol {  // per-thread column walk
+  int x, y, z0, z1;
+  int64_t i, fx, fy;
+};
+
+__device__ __forceinline__ bool zcol_begin(const Operator& A, ZCol& c) {
+  c.x = blockIdx.x * kZTx + threadIdx.x;
+  c.y = blockIdx.y * kZTy + threadIdx.y;
+  c.z0 = blockIdx.z * kZChunk;
+  if (c.x >= A.nx || c.y >= A.ny || c.z0 >= A.nz) return false;
+  c.z1 = c.z0 + kZChunk < A.nz ? c.z0 + kZChunk : A.nz;
+  c.i = ((int64_t)c.z0 * A.ny + c.y) * A.nx + c.x;
+  c.fx = ((int64_t)c.z0 * A.ny + c.y) * (A.nx + 1) + c.x;
+  c.fy = ((int64_t)c.z0 * (A.ny + 1) + c.y) * A.nx + c.x;
+  return true;
+}
+
+// (A - shift I) v at the current cell from its column registers vd, vc, vu.
+template <typename T>
+__device__ __forceinline__ double zapply(const Operator& A, const T* __restrict__ v, const ZCol& c, double dshift,
+                                         double kw, double ke, double ks, double kn, double kd, double ku,
+                                         double vd, double vc, double vu) {
+  const double vw = c.x > 0 ? ld_val(v + c.i - 1) : 0.0;
+  const double ve = c.x < A.nx - 1 ? ld_val(v + c.i + 1) : 0.0;
+  const double vs = c.y > 0 ? ld_val(v + c.i - A.nx) : 0.0;
+  const double vn = c.y < A.ny - 1 ? ld_val(v + c.i + A.nx) : 0.0;
+  double acc = dshift * vc;
+  acc = fma(-kw, vw, acc);
+  acc = fma(-ke, ve, acc);
+  acc = fma(-ks, vs, acc);
+  acc = fma(-kn, vn, acc);
+  acc = fma(-kd, vd, acc);
+  acc = fma(-ku, vu, acc);
+  return acc;
+}
+
+// y = A v (mode 0) or r = b - A v (mode 1) for a 3D stencil, z-marching.
+template <int MODE>
+__global__ void __launch_bounds__(kZTx * kZTy, 6) stencil3d_apply_kernel(Operator A, const double* __restrict__ v,
+                                                                      const double* __restrict__ b,
+                                                                      double* __restrict__ y,
+                                                                      const SolveState* gate, int gmode) {
+  if (gate_closed(gate, gmode)) return;
+  ZCol c;
+  if (!zcol_begin(A, c)) return;
+  const int64_t plane = (int64_t)A.nx * A.ny;
+  const int64_t dfx = (int64_t)A.ny * (A.nx + 1), dfy = (int64_t)(A.ny + 1) * A.nx;
+  double vd = c.z0 > 0 ? __ldg(v + c.i - plane) : 0.0, vc = __ldg(v + c.i);
+  double kd = __ldg(A.kz + c.i);
+#pragma unroll 2
+  for (int z = c.z0; z < c.z1; ++z) {
+    const double vu = z < A.nz - 1 ? __ldg(v + c.i + plane) : 0.0;
+    const double ku = __ldg(A.kz + c.i + plane);
+    const double av = zapply(A, v, c, __ldg(A.diag + c.i), __ldg(A.kx + c.fx), __ldg(A.kx + c.fx + 1),
+                             __ldg(A.ky + c.fy), __ldg(A.ky + c.fy + A.nx), kd, ku, vd, vc, vu);
+    y[c.i] = MODE == 0 ? av : b[c.i] - av;
+    vd = vc;
+    vc = vu;
+    kd = ku;
+    c.i += plane;
+    c.fx += dfx;
+    c.fy += dfy;
+  }
+}
+
 // ------------------------------------------------------------------- CSR
 __global__ void __launch_bounds__(kOpThreads) csr_spmv_kernel(Operator A, const double* __restrict__ v,
                                                               double* __restrict__ y, const SolveState* gate,
@@ -320,7 +403,8 @@ cudaError_t launch_spmv(const Operator& A, const double* v, double* y, cudaStrea
                         int gmode) {
   int g = grid_for(A.n, 4);
   if (A.kind == 0) csr_spmv_kernel<<<g, kOpThreads, 0, st>>>(A, v, y, gate, gmode);
-  else if (A.dim == 3) stencil_spmv_kernel<true><<<g, kOpThreads, 0, st>>>(A, v, y, gate, gmode);
+  else if (A.dim == 3)
+    stencil3d_apply_kernel<0><<<zmarch_grid(A), dim3(kZTx, kZTy), 0, st>>>(A, v, nullptr, y, gate, gmode);
   else stencil_spmv_kernel<false><<<g, kOpThreads, 0, st>>>(A, v, y, gate, gmode);
   return cudaGetLastError();
 }
@@ -329,7 +413,8 @@ cudaError_t launch_residual(const Operator& A, const double* b, const double* x,
                             const SolveState* gate, int gmode) {
   int g = grid_for(A.n, 4);
   if (A.kind == 0) csr_residual_kernel<<<g, kOpThreads, 0, st>>>(A, b, x, r, gate, gmode);
-  else if (A.dim == 3) stencil_residual_kernel<true><<<g, kOpThreads, 0, st>>>(A, b, x, r, gate, gmode);
+  else if (A.dim == 3)
+    stencil3d_apply_kernel<1><<<zmarch_grid(A), dim3(kZTx, kZTy), 0, st>>>(A, x, b, r, gate, gmode);
   else stencil_residual_kernel<false><<<g, kOpThreads, 0, st>>>(A, b, x, r, gate, gmode);
   return cudaGetLastError();
 }
