@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--max-outer", type=int, default=0, help="cap outer loops (profiling runs only)")
+    ap.add_argument("--s-max", type=int, default=0,
+                    help="override the workload's s_max (sigma) for studies; 0 keeps the configuration's")
     ap.add_argument("--gram-mode", type=int, default=0,
                     help="0: binary64 Gram (the method as written); 1: binary32-pair products on the FP32 pipes")
     return ap.parse_args()
@@ -341,7 +343,9 @@ def run_adjoint(args, cfg, pkg, torch, dev):
 
 def main():
     args = parse_args()
-    cfg = WORKLOADS[args.workload]
+    cfg = dict(WORKLOADS[args.workload])
+    if args.s_max > 0:
+        cfg["smax"] = args.s_max
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -79,8 +79,8 @@ typedef struct {
   double eps;            /* unit roundoff in (condy)/(newcondy); default 2^-53 */
   double kappa_cut;      /* kappa_l = inf when lambda_min(G_l) <= kappa_cut * lambda_max(G_l); default 2^-44 */
   int gram_mode;         /* 0: G by binary64 FMAs (the method as written); 1: binary32-pair products on the
-                            FP32 pipes, compensated binary32 sums over 128-row tiles, binary64 across tiles
-                            (|error| ~ 2^-46 of |Y_i||Y_j| per term); default 0 */
+                            FP32 pipes (each within ~2^-46 of Y_i Y_j), compensated binary32 sums over
+                            256-row tiles, binary64 across tiles; default 0 */
 } sscg_opts;
 
 /* Per-outer-loop decision record (Alg. 5): s-bar_k, s-tilde_k, s_k, c at the
@@ -259,7 +259,7 @@ int sscg_gram(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, voi
 /* sscg_gram with a choice of product arithmetic: mode 0 as sscg_gram; mode 1
  * forms every product from binary32 pairs on the FP32 pipes (each value split
  * exactly into two 24-bit parts after a per-tile power-of-two column scale,
- * compensated binary32 sums over 128-row tiles, binary64 across tiles), which
+ * compensated binary32 sums over 256-row tiles, binary64 across tiles), which
  * GB300 executes far faster than binary64 FMAs.  Same arguments and
  * allocation behaviour as sscg_gram otherwise. */
 int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, int mode, void* cuda_stream);
