@@ -141,6 +141,45 @@ def test_kappa_estimates(pkg, sbar, conditioning):
             assert abs(kap[l] - kap_o[l]) <= 1e-8 * kap_o[l], (l, kap[l], kap_o[l])
 
 
+@pytest.mark.parametrize("sbar", [8, 16])
+@pytest.mark.parametrize("case", ["identity", "diagonal", "block_diagonal", "zero_column"])
+def test_kappa_degenerate_gram(pkg, sbar, case):
+    """kappa on Gram matrices that reach the kernel's rare branches: equal
+    eigenvalues (exact zeros in the Sturm sequence), zero off-diagonals
+    (Householder columns already reduced, decoupled Sturm blocks) and an exact
+    zero eigenvalue (kappa = inf), against the oracle's dense eigensolve."""
+    ncols = 2 * sbar + 1
+    rng = np.random.default_rng(17 + sbar)
+    if case == "identity":
+        G = np.eye(ncols)
+    elif case == "diagonal":
+        G = np.diag(rng.uniform(0.5, 4.0, ncols))
+    elif case == "block_diagonal":
+        h = ncols // 2
+        B1 = rng.standard_normal((50, h))
+        B2 = rng.standard_normal((50, ncols - h)) * 3.0
+        G = np.zeros((ncols, ncols))
+        G[:h, :h] = B1.T @ B1
+        G[h:, h:] = B2.T @ B2
+    else:
+        Y = rng.standard_normal((400, ncols))
+        Y[:, 3] = 0.0
+        G = Y.T @ Y
+    kap_o, lmin_o, lmax_o = cg.kappa_estimates(G, sbar)
+    kap = torch.zeros(sbar + 1, dtype=torch.float64, device="cuda")
+    lmn = torch.zeros_like(kap)
+    lmx = torch.zeros_like(kap)
+    pkg.sscg.sscg_kappa(dev(G.ravel()), ncols, sbar, 2.0 ** -44, kap, lmn, lmx)
+    kap, lmn, lmx = kap.cpu().numpy(), lmn.cpu().numpy(), lmx.cpu().numpy()
+    for l in range(1, sbar + 1):
+        assert abs(lmx[l] - lmax_o[l]) <= 1e-13 * lmax_o[l], (l, lmx[l], lmax_o[l])
+        assert abs(lmn[l] - lmin_o[l]) <= 2e-14 * lmax_o[l], (l, lmn[l], lmin_o[l])
+        if math.isinf(kap_o[l]):
+            assert math.isinf(kap[l]), (l, kap[l])
+        else:
+            assert abs(kap[l] - kap_o[l]) <= 1e-8 * kap_o[l], (l, kap[l], kap_o[l])
+
+
 # ---------------------------------------------------------------- solves
 
 def agreeing_prefix(hist_g, hist_o, rel=1e-8):
