@@ -47,6 +47,15 @@ WORKLOADS = {
                               "b~N(0,1), x0=0", smax=16, basis="newton", tol=1e-10, base="varcoef3d_160",
                          scale=96),
 }
+def _hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0   # fallback: one earlier GB300 copy measurement
+
+
+HBM_PEAK_GBS = _hbm_peak_gbs()
 L2_BYTES = 129 * 2 ** 20
 L2_FLUSH_BYTES = 256 * 2 ** 20
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
@@ -267,18 +276,24 @@ def run_batched(args, cfg, pkg, torch, dev):
             best, _ = pkg.sscg.sscg_autotune(solvers[i].h, bi, cfg["tol"], [4, 8, 12, 16], trial_outer=12,
                                              basis=cfg["basis"])
             classes[key] = best
-    t_tune = time.perf_counter() - t_tune
     s_max = [classes[(st.dim, int(round(math.log(st.n, 4))))] for st, _ in systems]
+    # autotuner, tile shapes: rows per work chunk and per Gram block, by timed trial batches
+    shapes = [(1024, 1024), (2048, 2048), (4096, 4096), (8192, 8192), (2048, 8192)]
+    ib, shape_us = pkg.sscg.sscg_autotune_batch([s.h for s in solvers], nrhs, b, cfg["tol"], s_max, shapes,
+                                                trial_outer=20, basis=cfg["basis"])
+    opts = pkg.sscg.sscg_opts_default(batch_chunk_rows=shapes[ib][0], batch_gram_rows=shapes[ib][1])
+    t_tune = time.perf_counter() - t_tune
     x = torch.zeros_like(b)
     for _ in range(args.warmup):
         x.zero_()
-        pkg.sscg.sscg_solve_batch([s.h for s in solvers], nrhs, b, x, cfg["tol"], s_max, cfg["basis"])
+        pkg.sscg.sscg_solve_batch([s.h for s in solvers], nrhs, b, x, cfg["tol"], s_max, cfg["basis"], opts)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
         x.zero_()
-        rc, stats = pkg.sscg.sscg_solve_batch([s.h for s in solvers], nrhs, b, x, cfg["tol"], s_max, cfg["basis"])
+        rc, stats = pkg.sscg.sscg_solve_batch([s.h for s in solvers], nrhs, b, x, cfg["tol"], s_max, cfg["basis"],
+                                              opts)
     e1.record()
     torch.cuda.synchronize()
     el = e0.elapsed_time(e1) / 1e3
@@ -288,6 +303,8 @@ def run_batched(args, cfg, pkg, torch, dev):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["desc"], "systems": len(systems), "pairs": pairs,
                        "unknowns": int(b_np.size), "sigma_by_class": {f"{k[0]}d_4^{k[1]}": v for k, v in classes.items()},
+                       "tile_rows": {"chunk": shapes[ib][0], "gram": shapes[ib][1]},
+                       "tile_us_per_inner": {f"{c}x{g}": t for (c, g), t in zip(shapes, shape_us)},
                        "autotune_s": t_tune},
             "status": rc, "converged": stats["converged"], "outer_loops": stats["outer_loops"],
             "inner_iters_total": stats["inner_iters"], "max_true_relres": stats["max_true_relres"],
@@ -531,7 +548,10 @@ def main():
             "converged": ok, "true_relres": max(s.true_relres for s in stats),
             "outer_loops": st0.outer_iters, "inner_iters": st0.inner_iters, "host_syncs": st0.host_syncs,
             "ms_per_outer_loop": ms_per_step / st0.outer_iters,
-            "hbm_gbs_alg": hbm_gbs, "phase_ms_per_solve": phase_ms,
+            "hbm_gbs_alg": hbm_gbs, "hbm_frac_alg": hbm_gbs / HBM_PEAK_GBS,
+            "hbm_peak_note": "measured copy peak (MEASURED_PEAKS.json); algorithmic bytes per outer loop: "
+                             "the operator once plus 8 N (4 s-bar + 6)",
+            "phase_ms_per_solve": phase_ms,
             "hscg": hscg,
             "roofline": roofline,
             "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,

@@ -81,6 +81,9 @@ typedef struct {
   int gram_mode;         /* 0: G by binary64 FMAs (the method as written); 1: binary32-pair products on the
                             FP32 pipes (each within ~2^-46 of Y_i Y_j), compensated binary32 sums over
                             256-row tiles, binary64 across tiles; default 0 */
+  int batch_chunk_rows;  /* sscg_solve_batch only: rows per work chunk of the row kernels (matrix powers,
+                            recombination, residual checks); 0 = 2048, else 128..1048576 */
+  int batch_gram_rows;   /* sscg_solve_batch only: rows per Gram block; 0 = 2048, else 128..1048576 */
 } sscg_opts;
 
 /* Per-outer-loop decision record (Alg. 5): s-bar_k, s-tilde_k, s_k, c at the
@@ -194,6 +197,8 @@ typedef struct {
   int graph_launches;    /* CUDA graph launches */
   int64_t inner_iters;   /* sum over pairs */
   double max_true_relres;/* largest ||b - A x||/||b|| over the pairs */
+  double device_ms;      /* device time of the outer loops (CUDA events around the graph launch or the
+                            polled loop; set-up and copies excluded) */
   int* pair_status;      /* optional, per pair */
   int* pair_outer;       /* optional, per pair */
   int* pair_inner;       /* optional, per pair */
@@ -229,6 +234,18 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
  * (optional, host, length ncand) receives milliseconds per inner iteration. */
 int sscg_autotune(sscg_t h, const double* b, double tol, const int* candidates, int ncand, int trial_outer,
                   sscg_basis basis, int* best, double* times);
+
+/* Autotuner for the batched solve's tile shapes (rows per work chunk and per
+ * Gram block, sscg_opts.batch_chunk_rows / batch_gram_rows): for each of the
+ * ncand candidates (chunk_rows[i], gram_rows[i]) run sscg_solve_batch on the
+ * given batch (same arguments as there; x0 = 0 in a scratch array, b
+ * unchanged) for at most trial_outer outer loops, and return in *best the
+ * index of the candidate with the least device time per inner iteration
+ * (summed over pairs).  times (optional, host, length ncand) receives
+ * microseconds per inner iteration.  Device memory is allocated per trial. */
+int sscg_autotune_batch(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double tol,
+                        const int* s_max, sscg_basis basis, const int* chunk_rows, const int* gram_rows, int ncand,
+                        int trial_outer, int* best, double* times, void* cuda_stream);
 
 /* Ritz estimates (Algs. 3-4, eq. lest) of the handle's last s-step solve. */
 int sscg_ritz(sscg_t h, double* lmin, double* lmax);

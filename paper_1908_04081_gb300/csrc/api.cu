@@ -295,6 +295,10 @@ void fill_state_config(SolveState& s, int sigma, double tol, int basis, const ss
 int validate_opts(const sscg_opts& o) {
   if (o.c_mode < 0 || o.c_mode > SSCG_C_CONST) return SSCG_ERR_INVALID_ARG;
   if (o.gram_mode < 0 || o.gram_mode > 1) return SSCG_ERR_INVALID_ARG;
+  if (o.batch_chunk_rows != 0 && (o.batch_chunk_rows < 128 || o.batch_chunk_rows > (1 << 20)))
+    return SSCG_ERR_INVALID_ARG;
+  if (o.batch_gram_rows != 0 && (o.batch_gram_rows < 128 || o.batch_gram_rows > (1 << 20)))
+    return SSCG_ERR_INVALID_ARG;
   if (!(o.eps > 0.0) || !(o.kappa_cut >= 0.0)) return SSCG_ERR_INVALID_ARG;
   return SSCG_OK;
 }
@@ -341,6 +345,8 @@ void sscg_opts_default(sscg_opts* o) {
   o->eps = std::ldexp(1.0, -53);
   o->kappa_cut = std::ldexp(1.0, -44);
   o->gram_mode = 0;
+  o->batch_chunk_rows = 0;
+  o->batch_gram_rows = 0;
 }
 
 int sscg_create_csr(sscg_t* out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
@@ -738,6 +744,8 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
   if (rc) return rc;
   if (o.y_fp32) return SSCG_ERR_UNSUPPORTED;
   // ---- pairs, chunks and Gram blocks (host)
+  const int chunk_rows = o.batch_chunk_rows > 0 ? o.batch_chunk_rows : kBatchChunk;
+  const int gram_rows = o.batch_gram_rows > 0 ? o.batch_gram_rows : kBatchGramRows;
   std::vector<BatchPair> pairs;
   std::vector<int> chunk_pair, gblk_pair, pair_sigma;
   int64_t off = 0;
@@ -751,9 +759,9 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
       bp.off = off;
       bp.n = n;
       bp.chunk0 = (int)chunk_pair.size();
-      bp.nchunk = (int)((n + kBatchChunk - 1) / kBatchChunk);
+      bp.nchunk = (int)((n + chunk_rows - 1) / chunk_rows);
       bp.gblk0 = (int)gblk_pair.size();
-      bp.ngblk = (int)((n + kBatchGramRows - 1) / kBatchGramRows);
+      bp.ngblk = (int)((n + gram_rows - 1) / gram_rows);
       const int j = (int)pairs.size();
       for (int c = 0; c < bp.nchunk; ++c) chunk_pair.push_back(j);
       for (int g = 0; g < bp.ngblk; ++g) gblk_pair.push_back(j);
@@ -779,10 +787,11 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
     d_part.release(); d_rt.release(); d_leja.release(); d_cnt.release();
   };
   cudaStream_t st = nullptr;
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr, t0 = nullptr, t1 = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int result = SSCG_OK;
+  float device_ms = 0.f;
   std::vector<SolveState> hs(P);
   int launches = 0, host_syncs = 0, graph_launches = 0;
   unsigned int bodies_run = 0;
@@ -805,6 +814,8 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
     BK(d_cnt.ensure(2));
     BK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     BK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    BK(cudaEventCreate(&t0));
+    BK(cudaEventCreate(&t1));
     BK(cudaEventRecord(ev, (cudaStream_t)cuda_stream));
     BK(cudaStreamWaitEvent(st, ev, 0));
     for (int j = 0; j < P; ++j) fill_state_config(hs[j], pair_sigma[j], tol, (int)basis, o, hist_cap);
@@ -828,6 +839,8 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
     v.active = d_cnt.p;
     v.bodies = d_cnt.p + 1;
     v.max_bodies = (o.max_outer > 0 ? o.max_outer : 100000) + 2;
+    v.chunk_rows = chunk_rows;
+    v.gram_rows = gram_rows;
     BK(launch_batch_init(v, b, x, d_Y.p, LD, d_part.p, st));
     launches += 3;
     auto body = [&](cudaGraphConditionalHandle cond, int use_cond) -> cudaError_t {
@@ -871,9 +884,12 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
       BK(eb);
       BK(ee);
       BK(cudaGraphInstantiate(&gexec, graph, 0));
+      BK(cudaEventRecord(t0, st));
       BK(cudaGraphLaunch(gexec, st));
+      BK(cudaEventRecord(t1, st));
       ++graph_launches;
     } else {
+      BK(cudaEventRecord(t0, st));
       const int every = std::max(1, o.check_every);
       unsigned int cnt[2] = {1u, 0u};
       while (true) {
@@ -888,12 +904,14 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
         if (cnt[0] == 0u || cnt[1] >= (unsigned)v.max_bodies) break;
       }
       if (result) break;
+      BK(cudaEventRecord(t1, st));
     }
     BK(cudaMemcpyAsync(hs.data(), d_st.p, P * sizeof(SolveState), cudaMemcpyDeviceToHost, st));
     BK(cudaMemcpyAsync(&bodies_run, d_cnt.p + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     BK(cudaStreamSynchronize(st));
     ++host_syncs;
     launches += (int)bodies_run * body_kernels;
+    BK(cudaEventElapsedTime(&device_ms, t0, t1));
     BK(cudaEventRecord(ev, st));
     BK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, ev, 0));
 #undef BK
@@ -905,6 +923,8 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
     cudaStreamDestroy(st);
   }
   if (ev) cudaEventDestroy(ev);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
   release();
   if (result) return result;
   int conv = 0, worst = SSCG_OK, max_outer = 0;
@@ -934,8 +954,67 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
     stats->graph_launches = graph_launches;
     stats->inner_iters = inner;
     stats->max_true_relres = max_rel;
+    stats->device_ms = device_ms;
   }
   return worst;
+}
+
+int sscg_autotune_batch(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double tol,
+                        const int* s_max, sscg_basis basis, const int* chunk_rows, const int* gram_rows, int ncand,
+                        int trial_outer, int* best, double* times, void* cuda_stream) {
+  if (!systems || nsys <= 0 || !nrhs || !b || !s_max || !chunk_rows || !gram_rows || ncand <= 0 ||
+      trial_outer <= 0 || !best || !(tol > 0.0))
+    return SSCG_ERR_INVALID_ARG;
+  int64_t total = 0;
+  for (int s = 0; s < nsys; ++s) {
+    if (!systems[s] || nrhs[s] < 0) return SSCG_ERR_INVALID_ARG;
+    total += (int64_t)nrhs[s] * systems[s]->n;
+  }
+  if (total == 0) {
+    *best = 0;
+    return SSCG_OK;
+  }
+  DevBuf<double> dx;
+  int rc = SSCG_OK;
+  cudaError_t e = dx.ensure(total);
+  if (e != cudaSuccess) rc = cuda_fail(e, "autotune_batch scratch");
+  double best_t = 0.0;
+  *best = -1;
+  for (int i = 0; i < ncand && rc == SSCG_OK; ++i) {
+    sscg_opts o;
+    sscg_opts_default(&o);
+    o.max_outer = trial_outer;
+    o.batch_chunk_rows = chunk_rows[i];
+    o.batch_gram_rows = gram_rows[i];
+    if (validate_opts(o)) {
+      rc = SSCG_ERR_INVALID_ARG;
+      break;
+    }
+    e = cudaMemsetAsync(dx.p, 0, total * sizeof(double), (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "autotune_batch memset");
+      break;
+    }
+    sscg_batch_stats bs;
+    std::memset(&bs, 0, sizeof(bs));
+    const int r = sscg_solve_batch(systems, nsys, nrhs, b, dx.p, tol, s_max, basis, &o, &bs, cuda_stream);
+    if (r < 0) {
+      rc = r;
+      break;
+    }
+    const double t = bs.inner_iters > 0 ? 1e3 * bs.device_ms / (double)bs.inner_iters : 0.0;
+    if (times) times[i] = t;
+    if (*best < 0 || t < best_t) {
+      *best = i;
+      best_t = t;
+    }
+  }
+  if (rc == SSCG_OK) {
+    e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "autotune_batch sync");
+  }
+  dx.release();
+  return rc;
 }
 
 int sscg_autotune(sscg_t h, const double* b, double tol, const int* candidates, int ncand, int trial_outer,

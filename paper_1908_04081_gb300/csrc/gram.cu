@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restri
 }
 
 
-// Batched Gram: each block owns kBatchGramRows rows of one pair and writes the
+// Batched Gram: each block owns gram_rows rows of one pair and writes the
 // pair's (2s-bar+1)(2s-bar+2)/2 partial sums; the reduction adds each pair's
 // block partials in a fixed order (one block per pair).
 __global__ void __launch_bounds__(kGramThreads, 2)
@@ -342,8 +342,8 @@ batch_gram_partial_kernel(BatchView v, const double* __restrict__ Y, int64_t LD,
   __shared__ double tile[kGramTileRows][kMaxCols + 1];
   __shared__ double red[kGramThreads];
   const double* Yp = Y + bp.off;
-  const int64_t r_begin = (int64_t)(g - bp.gblk0) * kBatchGramRows;
-  int64_t r_end = r_begin + kBatchGramRows;
+  const int64_t r_begin = (int64_t)(g - bp.gblk0) * v.gram_rows;
+  int64_t r_end = r_begin + v.gram_rows;
   if (r_end > bp.n) r_end = bp.n;
   double acc = 0.0;
   for (int64_t r0 = r_begin; r0 < r_end; r0 += kGramTileRows) {

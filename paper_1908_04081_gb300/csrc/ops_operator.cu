@@ -346,8 +346,8 @@ __global__ void __launch_bounds__(kOpThreads) batch_mpk_kernel(BatchView v, doub
     const double* Rm = level >= 1 ? base + (int64_t)(2 * level - 1) * LD : nullptr;
     double* Pn = base + (int64_t)(2 * level + 2) * LD;
     double* Rn = base + (int64_t)(2 * level + 3) * LD;
-    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
-    int64_t r1 = r0 + kBatchChunk;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
     if (r1 > bp.n) r1 = bp.n;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
       double wp, wr = 0.0;

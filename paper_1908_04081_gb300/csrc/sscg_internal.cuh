@@ -161,8 +161,9 @@ cudaError_t launch_csr_grad(const Operator& A, const double* lam, const double* 
 // A batched solve runs many independent (system, right-hand side) pairs in
 // lock-step outer loops.  Every vector of pair j lives at rows
 // [off, off + n) of the concatenated arrays; basis column c of pair j starts
-// at Y + c * LD + off.  Row work is cut into chunks of kBatchChunk rows, each
-// owned by one pair; the Gram uses its own blocks of kBatchGramRows rows.
+// at Y + c * LD + off.  Row work is cut into chunks of chunk_rows rows, each
+// owned by one pair; the Gram uses its own blocks of gram_rows rows (both
+// chosen per call, default kBatchChunk / kBatchGramRows).
 constexpr int kBatchChunk = 2048;
 constexpr int kBatchGramRows = 2048;
 
@@ -187,6 +188,8 @@ struct BatchView {
   unsigned int* active;   // pairs still iterating after the last outer loop
   unsigned int* bodies;   // outer loops run so far (all pairs)
   int max_bodies;
+  int chunk_rows;         // rows per work chunk
+  int gram_rows;          // rows per Gram block
 };
 
 // batch.cu / per-file batched kernels

@@ -454,8 +454,8 @@ __global__ void __launch_bounds__(kVecThreads) batch_init_kernel(BatchView v, co
     const int j = v.chunk_pair[c];
     const BatchPair& bp = v.pairs[j];
     SolveState* st = v.states + j;
-    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
-    int64_t r1 = r0 + kBatchChunk;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
     if (r1 > bp.n) r1 = bp.n;
     const double* xb = x + bp.off;
     double s = 0.0;
@@ -487,8 +487,8 @@ __global__ void __launch_bounds__(kVecThreads) batch_zero_x_kernel(BatchView v, 
     const int j = v.chunk_pair[c];
     const BatchPair& bp = v.pairs[j];
     if (!v.states[j].zero_rhs) continue;
-    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
-    int64_t r1 = r0 + kBatchChunk;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
     if (r1 > bp.n) r1 = bp.n;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) x[bp.off + i] = 0.0;
   }
@@ -510,8 +510,8 @@ __global__ void __launch_bounds__(kVecThreads) batch_recombine_kernel(BatchView 
       cp[threadIdx.x] = st->pc[threadIdx.x];
     }
     __syncthreads();
-    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
-    int64_t r1 = r0 + kBatchChunk;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
     if (r1 > bp.n) r1 = bp.n;
     double* Yp = Y + bp.off;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
@@ -539,8 +539,8 @@ __global__ void __launch_bounds__(kVecThreads) batch_true_residual_kernel(BatchV
     const BatchPair& bp = v.pairs[j];
     SolveState* st = v.states + j;
     if (st->done || !st->converged_est) continue;
-    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
-    int64_t r1 = r0 + kBatchChunk;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
     if (r1 > bp.n) r1 = bp.n;
     const double* xb = x + bp.off;
     double s = 0.0;
@@ -578,8 +578,8 @@ __global__ void __launch_bounds__(kVecThreads) batch_replacement_kernel(BatchVie
     const BatchPair& bp = v.pairs[j];
     const SolveState* st = v.states + j;
     if (st->done || !st->replace_pending) continue;
-    const int64_t r0 = (int64_t)(c - bp.chunk0) * kBatchChunk;
-    int64_t r1 = r0 + kBatchChunk;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
     if (r1 > bp.n) r1 = bp.n;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
       const double r = rt[bp.off + i];

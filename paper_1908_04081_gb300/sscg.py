@@ -33,7 +33,8 @@ class Opts(C.Structure):
                 ("newton_scale", C.c_int), ("cheb_params", C.c_int), ("inner_conv_check", C.c_int),
                 ("y_fp32", C.c_int), ("variant", C.c_int), ("check_every", C.c_int),
                 ("use_graph", C.c_int), ("profile", C.c_int), ("c_const", C.c_double),
-                ("eps", C.c_double), ("kappa_cut", C.c_double), ("gram_mode", C.c_int)]
+                ("eps", C.c_double), ("kappa_cut", C.c_double), ("gram_mode", C.c_int),
+                ("batch_chunk_rows", C.c_int), ("batch_gram_rows", C.c_int)]
 
 
 class OuterRecord(C.Structure):
@@ -58,7 +59,7 @@ class Stats(C.Structure):
 class BatchStats(C.Structure):
     _fields_ = [("npairs", C.c_int), ("converged", C.c_int), ("outer_loops", C.c_int), ("host_syncs", C.c_int),
                 ("kernel_launches", C.c_int), ("graph_launches", C.c_int), ("inner_iters", C.c_int64),
-                ("max_true_relres", C.c_double), ("pair_status", C.POINTER(C.c_int)),
+                ("max_true_relres", C.c_double), ("device_ms", C.c_double), ("pair_status", C.POINTER(C.c_int)),
                 ("pair_outer", C.POINTER(C.c_int)), ("pair_inner", C.POINTER(C.c_int))]
 
 
@@ -103,6 +104,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                        C.POINTER(C.c_int), C.c_int, C.POINTER(Opts), C.POINTER(BatchStats), _P]),
         "sscg_autotune": (C.c_int, [_P, _P, C.c_double, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int,
                                     C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "sscg_autotune_batch": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(C.c_int), _P, C.c_double,
+                                          C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                          C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -331,8 +335,28 @@ def sscg_solve_batch(handles, nrhs, b, x, tol: float, s_max, basis="newton", opt
     _check(rc, "sscg_solve_batch", allow_status=True)
     return rc, dict(npairs=st.npairs, converged=st.converged, outer_loops=st.outer_loops, host_syncs=st.host_syncs,
                     kernel_launches=st.kernel_launches, graph_launches=st.graph_launches,
-                    inner_iters=st.inner_iters, max_true_relres=st.max_true_relres,
+                    inner_iters=st.inner_iters, max_true_relres=st.max_true_relres, device_ms=st.device_ms,
                     pair_status=list(ps)[:npairs], pair_outer=list(po)[:npairs], pair_inner=list(pi)[:npairs])
+
+
+def sscg_autotune_batch(handles, nrhs, b, tol: float, s_max, shapes, trial_outer: int = 20, basis="newton",
+                        stream=None):
+    """Pick the batched solve's tile shapes among candidate (chunk_rows,
+    gram_rows) pairs by timed trial batches (the library's autotuner).
+    Returns (index of the best candidate, microseconds per inner iteration
+    for each candidate)."""
+    nsys = len(handles)
+    hs = (_P * nsys)(*handles)
+    nr = (C.c_int * nsys)(*[int(k) for k in nrhs])
+    sm = (C.c_int * nsys)(*[int(k) for k in s_max])
+    cr = (C.c_int * len(shapes))(*[int(c) for c, _ in shapes])
+    gr = (C.c_int * len(shapes))(*[int(g) for _, g in shapes])
+    best = C.c_int()
+    times = (C.c_double * len(shapes))()
+    _check(load_library().sscg_autotune_batch(hs, nsys, nr, _f64(b), tol, sm, BASES.get(basis, basis), cr, gr,
+                                              len(shapes), trial_outer, C.byref(best), times, _stream_ptr(stream)),
+           "sscg_autotune_batch")
+    return best.value, list(times)
 
 
 def sscg_autotune(h: int, b, tol: float, candidates, trial_outer: int = 12, basis="newton"):

@@ -95,3 +95,37 @@ def test_autotune_picks_a_candidate(pkg):
     assert best in (4, 8, 16)
     assert all(t > 0 for t in times)
     assert times[[4, 8, 16].index(best)] == min(times)
+
+
+def test_batch_tile_shapes_and_their_autotuner(pkg):
+    """The batch's rows per work chunk and per Gram block are runtime choices:
+    every shape converges every pair to tol (independent residual) with the
+    same solutions to within 1e-8 (only summation orders change), the shape
+    autotuner returns one of its candidates with the least time, and
+    out-of-range shapes are rejected."""
+    systems, solvers, nrhs, b = build(pkg, 6, 2024, 300, 20000, 2)
+    bt = torch.tensor(b, device="cuda")
+    hs = [s.h for s in solvers]
+    s_max = [8] * len(systems)
+    xs = []
+    for chunk, gram in ((2048, 2048), (256, 512), (8192, 128)):
+        o = pkg.sscg.sscg_opts_default(batch_chunk_rows=chunk, batch_gram_rows=gram)
+        xt = torch.zeros_like(bt)
+        rc, stats = pkg.sscg.sscg_solve_batch(hs, nrhs, bt, xt, 1e-10, s_max, "newton", o)
+        assert rc == 0 and stats["converged"] == stats["npairs"]
+        assert stats["device_ms"] > 0.0
+        x = xt.cpu().numpy()
+        for st, bj, xj in split(systems, x):
+            A = as_matrix(st)
+            assert np.linalg.norm(bj - A @ xj) <= 1e-10 * np.linalg.norm(bj)
+        xs.append(x)
+    for x in xs[1:]:
+        for (_, _, x0j), (_, _, xj) in zip(split(systems, xs[0]), split(systems, x)):
+            assert np.linalg.norm(xj - x0j) <= 1e-8 * np.linalg.norm(x0j)
+    shapes = [(1024, 1024), (2048, 2048), (4096, 8192)]
+    best, times = pkg.sscg.sscg_autotune_batch(hs, nrhs, bt, 1e-10, s_max, shapes, trial_outer=8)
+    assert 0 <= best < len(shapes)
+    assert all(t > 0 for t in times) and times[best] == min(times)
+    with pytest.raises(pkg.sscg.SscgError):
+        pkg.sscg.sscg_solve_batch(hs, nrhs, bt, torch.zeros_like(bt), 1e-10, s_max, "newton",
+                                  pkg.sscg.sscg_opts_default(batch_chunk_rows=64))
