@@ -63,9 +63,9 @@ struct sscg_ctx {
   cudaStream_t stream = nullptr;  // private stream (stream capture needs a non-legacy stream)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // operator storage
-  DevBuf<int64_t> rowptr;
-  DevBuf<int32_t> col;
-  DevBuf<double> val, kx, ky, kz, diag;
+  DevBuf<int64_t> rowptr, s_off;
+  DevBuf<int32_t> col, s_row, s_len, s_col;
+  DevBuf<double> val, s_val, kx, ky, kz, diag;
   // solve storage
   int64_t ld = 0;
   DevBuf<double> Y, G, partials, rt, b, x, r, p, q, leja;
@@ -381,11 +381,79 @@ int sscg_create_csr(sscg_t* out, int64_t n, int64_t nnz, const int64_t* rowptr, 
       return fail(e, "copy val");
   }
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return fail(e, "create_csr sync");
+  // sliced ELL copy for the row kernels: every lane of a warp walks a row of
+  // nearly the same length, and the loads of a slice are coalesced
+  std::vector<int64_t> hrp(n + 1);
+  std::vector<int32_t> hcol(std::max<int64_t>(nnz, 1));
+  std::vector<double> hval(std::max<int64_t>(nnz, 1));
+  if ((e = cudaMemcpy(hrp.data(), h->rowptr.p, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return fail(e, "read rowptr");
+  if (nnz > 0) {
+    if ((e = cudaMemcpy(hcol.data(), h->col.p, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return fail(e, "read col");
+    if ((e = cudaMemcpy(hval.data(), h->val.p, nnz * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return fail(e, "read val");
+  }
+  // the kernels index with these: reject a malformed matrix here
+  if (hrp[0] != 0 || hrp[n] != nnz) return fail(cudaErrorInvalidValue, "rowptr bounds");
+  for (int64_t i = 0; i < n; ++i)
+    if (hrp[i + 1] < hrp[i]) return fail(cudaErrorInvalidValue, "rowptr order");
+  for (int64_t k = 0; k < nnz; ++k)
+    if (hcol[k] < 0 || hcol[k] >= n) return fail(cudaErrorInvalidValue, "column index");
+  const int64_t nslices = (n + kSliceRows - 1) / kSliceRows;
+  std::vector<int32_t> srow(nslices * kSliceRows, -1), slen(nslices);
+  std::vector<int64_t> soff(nslices + 1, 0);
+  for (int64_t w = 0; w < n; w += kSliceWindow) {
+    const int64_t cnt = std::min<int64_t>(kSliceWindow, n - w);
+    for (int64_t i = 0; i < cnt; ++i) srow[w + i] = (int32_t)(w + i);
+    std::stable_sort(srow.begin() + w, srow.begin() + w + cnt, [&](int32_t a, int32_t b) {
+      return hrp[a + 1] - hrp[a] > hrp[b + 1] - hrp[b];
+    });
+  }
+  for (int64_t sl = 0; sl < nslices; ++sl) {
+    int64_t mx = 0;
+    for (int t = 0; t < kSliceRows; ++t) {
+      const int32_t r = srow[sl * kSliceRows + t];
+      if (r >= 0) mx = std::max<int64_t>(mx, hrp[r + 1] - hrp[r]);
+    }
+    if (mx > INT32_MAX) return fail(cudaErrorInvalidValue, "row length");
+    slen[sl] = (int32_t)mx;
+    soff[sl + 1] = soff[sl] + mx * kSliceRows;
+  }
+  const int64_t scount = std::max<int64_t>(soff[nslices], 1);
+  std::vector<int32_t> scol(scount, 0);
+  std::vector<double> sval(scount, 0.0);
+  for (int64_t sl = 0; sl < nslices; ++sl)
+    for (int t = 0; t < kSliceRows; ++t) {
+      const int32_t r = srow[sl * kSliceRows + t];
+      if (r < 0) continue;
+      for (int64_t k = hrp[r], j = 0; k < hrp[r + 1]; ++k, ++j) {
+        scol[soff[sl] + j * kSliceRows + t] = hcol[k];
+        sval[soff[sl] + j * kSliceRows + t] = hval[k];
+      }
+    }
+  if ((e = h->s_row.ensure(srow.size())) != cudaSuccess) return fail(e, "alloc s_row");
+  if ((e = h->s_len.ensure(std::max<int64_t>(nslices, 1))) != cudaSuccess) return fail(e, "alloc s_len");
+  if ((e = h->s_off.ensure(nslices + 1)) != cudaSuccess) return fail(e, "alloc s_off");
+  if ((e = h->s_col.ensure(scount)) != cudaSuccess) return fail(e, "alloc s_col");
+  if ((e = h->s_val.ensure(scount)) != cudaSuccess) return fail(e, "alloc s_val");
+  if ((e = cudaMemcpy(h->s_row.p, srow.data(), srow.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->s_len.p, slen.data(), nslices * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->s_off.p, soff.data(), (nslices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->s_col.p, scol.data(), scount * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->s_val.p, sval.data(), scount * sizeof(double), cudaMemcpyHostToDevice)))
+    return fail(e, "copy sliced ELL");
   h->op.kind = 0;
   h->op.n = n;
   h->op.rowptr = h->rowptr.p;
   h->op.col = h->col.p;
   h->op.val = h->val.p;
+  h->op.nslices = nslices;
+  h->op.s_row = h->s_row.p;
+  h->op.s_off = h->s_off.p;
+  h->op.s_len = h->s_len.p;
+  h->op.s_col = h->s_col.p;
+  h->op.s_val = h->s_val.p;
   *out = h;
   return SSCG_OK;
 }
@@ -445,6 +513,11 @@ void sscg_destroy(sscg_t h) {
   h->rowptr.release();
   h->col.release();
   h->val.release();
+  h->s_off.release();
+  h->s_row.release();
+  h->s_len.release();
+  h->s_col.release();
+  h->s_val.release();
   h->kx.release();
   h->ky.release();
   h->kz.release();

@@ -63,7 +63,7 @@ gram_partial_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const SolveS
       const int c = e / kGramTileRows;
       const int r = e - c * kGramTileRows;
       const int64_t row = r0 + r;
-      tile[r][c] = row < r_end ? (double)__ldg(Y + (int64_t)c * ld + row) : 0.0;
+      tile[r][c] = row < r_end ? widen(__ldg(Y + (int64_t)c * ld + row)) : 0.0;
     }
     __syncthreads();
     if (active) {
@@ -217,7 +217,7 @@ gram_partial_ff_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
       const int e = t + k * kFFThreads;
       const int c = e / kFFRows;
       const int64_t row = r0 + (e - c * kFFRows);
-      pre[k] = (c < ncols && row < r_end) ? (double)__ldg(Y + (int64_t)c * ld + row) : 0.0;
+      pre[k] = (c < ncols && row < r_end) ? widen(__ldg(Y + (int64_t)c * ld + row)) : 0.0;
     }
   };
   if (r_begin < r_end) prefetch(r_begin);

@@ -28,7 +28,7 @@ __host__ __device__ inline int grid_for(int64_t n, int per_thread) {
 }
 
 template <typename T>
-__device__ __forceinline__ double ld_val(const T* p) { return (double)__ldg(p); }
+__device__ __forceinline__ double ld_val(const T* p) { return widen(__ldg(p)); }
 
 // (A - shift I) v at cell i of a stencil, v read through `vp` (stride-1 vector).
 // Coordinates (x, y, z) of cell i; boundary neighbours contribute 0.
@@ -145,6 +145,91 @@ __global__ void __launch_bounds__(kOpThreads) stencil_mpk_kernel(Operator A, T* 
   }
 }
 
+// ---------------------------------------------------- CSR as sliced ELL
+// One warp per slice of 32 rows whose lengths differ little (sorted within
+// windows of 256 rows): on GB300 a binary64 instruction costs its warp the
+// same 64 cycles whether 1 or 32 lanes are active, so thread-per-row CSR pays
+// every warp's longest row on all lanes; here each lane loops to its own row
+// length (lanes of shorter rows idle for the few steps up to the slice's
+// longest row) and the loads of column indices and values are coalesced.
+// Each row is summed in its CSR order, so results are the bits of the
+// thread-per-row kernels.
+template <int MODE>  // 0: y = A v; 1: y = b - A v
+__global__ void __launch_bounds__(kOpThreads) sell_apply_kernel(Operator A, const double* __restrict__ v,
+                                                                const double* __restrict__ b,
+                                                                double* __restrict__ y, const SolveState* gate,
+                                                                int gmode) {
+  if (gate_closed(gate, gmode)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t s = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); s < A.nslices; s += warps) {
+    const int r = __ldg(A.s_row + s * kSliceRows + lane);
+    if (r < 0) continue;
+    const int len = (int)(__ldg(A.rowptr + r + 1) - __ldg(A.rowptr + r));
+    const int64_t base = __ldg(A.s_off + s) + lane;
+    double acc = 0.0;
+    for (int j = 0; j < len; ++j) {
+      const int64_t k = base + (int64_t)j * kSliceRows;
+      acc = fma(__ldg(A.s_val + k), __ldg(v + __ldg(A.s_col + k)), acc);
+    }
+    y[r] = MODE == 0 ? acc : b[r] - acc;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kOpThreads) sell_mpk_kernel(Operator A, T* __restrict__ Y, int64_t ld, int level,
+                                                              const SolveState* __restrict__ st, int sbar_fixed,
+                                                              LevelCoef coef) {
+  int sbar = sbar_fixed;
+  if (sbar <= 0) {
+    if (st->done) return;
+    sbar = st->sbar;
+  }
+  const bool doP = level < sbar;
+  const bool doR = level + 1 < sbar;
+  if (!doP) return;
+  const double theta = coef.theta[level];
+  const double ig = coef.inv_gamma[level];
+  const double mu = level >= 1 ? coef.mu[level - 1] : 0.0;
+  const T* Pl = Y + (int64_t)(2 * level) * ld;
+  const T* Rl = Y + (int64_t)(2 * level + 1) * ld;
+  const T* Pm = level >= 1 ? Y + (int64_t)(2 * level - 2) * ld : nullptr;
+  const T* Rm = level >= 1 ? Y + (int64_t)(2 * level - 1) * ld : nullptr;
+  T* Pn = Y + (int64_t)(2 * level + 2) * ld;
+  T* Rn = Y + (int64_t)(2 * level + 3) * ld;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t s = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); s < A.nslices; s += warps) {
+    const int r = __ldg(A.s_row + s * kSliceRows + lane);
+    if (r < 0) continue;
+    const int len = (int)(__ldg(A.rowptr + r + 1) - __ldg(A.rowptr + r));
+    const int64_t base = __ldg(A.s_off + s) + lane;
+    double ap = 0.0, ar = 0.0;
+    if (doR) {
+      for (int j = 0; j < len; ++j) {
+        const int64_t k = base + (int64_t)j * kSliceRows;
+        const double a = __ldg(A.s_val + k);
+        const int c = __ldg(A.s_col + k);
+        ap = fma(a, ld_val(Pl + c), ap);
+        ar = fma(a, ld_val(Rl + c), ar);
+      }
+    } else {
+      for (int j = 0; j < len; ++j) {
+        const int64_t k = base + (int64_t)j * kSliceRows;
+        ap = fma(__ldg(A.s_val + k), ld_val(Pl + __ldg(A.s_col + k)), ap);
+      }
+    }
+    double wp = fma(-theta, ld_val(Pl + r), ap);
+    if (mu != 0.0) wp = fma(-mu, ld_val(Pm + r), wp);
+    Pn[r] = (T)(wp * ig);
+    if (doR) {
+      double wr = fma(-theta, ld_val(Rl + r), ar);
+      if (mu != 0.0) wr = fma(-mu, ld_val(Rm + r), wr);
+      Rn[r] = (T)(wr * ig);
+    }
+  }
+}
+
 // ------------------------------------------------- 3D stencil, z-marching
 // The 3D SpMV and residual (the HSCG comparator's operator and the true
 // residual) march along z: a block covers a 32 x 8 tile of (x, y) columns and
@@ -157,6 +242,13 @@ __global__ void __launch_bounds__(kOpThreads) stencil_mpk_kernel(Operator A, T* 
 // scheme needs ~60 registers per thread and measured slower than the
 // cell-parallel kernel, which it therefore keeps.)
 constexpr int kZTx = 32, kZTy = 8, kZChunk = 4;
+
+__host__ inline int sell_grid(const Operator& A) {
+  const int64_t warps_per_block = kOpThreads / 32;
+  int64_t g = (A.nslices + warps_per_block - 1) / warps_per_block;
+  if (g > 152 * 16) g = 152 * 16;
+  return g < 1 ? 1 : (int)g;
+}
 
 __host__ inline dim3 zmarch_grid(const Operator& A) {
   return dim3((unsigned)((A.nx + kZTx - 1) / kZTx), (unsigned)((A.ny + kZTy - 1) / kZTy),
@@ -228,82 +320,7 @@ __global__ void __launch_bounds__(kZTx * kZTy, 6) stencil3d_apply_kernel(Operato
   }
 }
 
-// ------------------------------------------------------------------- CSR
-__global__ void __launch_bounds__(kOpThreads) csr_spmv_kernel(Operator A, const double* __restrict__ v,
-                                                              double* __restrict__ y, const SolveState* gate,
-                                                              int gmode) {
-  if (gate_closed(gate, gmode)) return;
-  const int64_t n = A.n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = __ldg(A.rowptr + i), e = __ldg(A.rowptr + i + 1);
-    double acc = 0.0;
-    for (int64_t k = b; k < e; ++k) acc = fma(__ldg(A.val + k), __ldg(v + __ldg(A.col + k)), acc);
-    y[i] = acc;
-  }
-}
 
-__global__ void __launch_bounds__(kOpThreads) csr_residual_kernel(Operator A, const double* __restrict__ bvec,
-                                                                  const double* __restrict__ xv,
-                                                                  double* __restrict__ r, const SolveState* gate,
-                                                                  int gmode) {
-  if (gate_closed(gate, gmode)) return;
-  const int64_t n = A.n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = __ldg(A.rowptr + i), e = __ldg(A.rowptr + i + 1);
-    double acc = 0.0;
-    for (int64_t k = b; k < e; ++k) acc = fma(__ldg(A.val + k), __ldg(xv + __ldg(A.col + k)), acc);
-    r[i] = bvec[i] - acc;
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kOpThreads) csr_mpk_kernel(Operator A, T* __restrict__ Y, int64_t ld,
-                                                             int level, const SolveState* __restrict__ st,
-                                                             int sbar_fixed, LevelCoef coef) {
-  int sbar = sbar_fixed;
-  if (sbar <= 0) {
-    if (st->done) return;
-    sbar = st->sbar;
-  }
-  const bool doP = level < sbar;
-  const bool doR = level + 1 < sbar;
-  if (!doP) return;
-  const double theta = coef.theta[level];
-  const double ig = coef.inv_gamma[level];
-  const double mu = level >= 1 ? coef.mu[level - 1] : 0.0;
-  const T* Pl = Y + (int64_t)(2 * level) * ld;
-  const T* Rl = Y + (int64_t)(2 * level + 1) * ld;
-  const T* Pm = level >= 1 ? Y + (int64_t)(2 * level - 2) * ld : nullptr;
-  const T* Rm = level >= 1 ? Y + (int64_t)(2 * level - 1) * ld : nullptr;
-  T* Pn = Y + (int64_t)(2 * level + 2) * ld;
-  T* Rn = Y + (int64_t)(2 * level + 3) * ld;
-  const int64_t n = A.n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = __ldg(A.rowptr + i), e = __ldg(A.rowptr + i + 1);
-    double ap = 0.0, ar = 0.0;
-    if (doR) {
-      for (int64_t k = b; k < e; ++k) {
-        const double a = __ldg(A.val + k);
-        const int c = __ldg(A.col + k);
-        ap = fma(a, ld_val(Pl + c), ap);
-        ar = fma(a, ld_val(Rl + c), ar);
-      }
-    } else {
-      for (int64_t k = b; k < e; ++k) ap = fma(__ldg(A.val + k), ld_val(Pl + __ldg(A.col + k)), ap);
-    }
-    double wp = fma(-theta, ld_val(Pl + i), ap);
-    if (mu != 0.0) wp = fma(-mu, ld_val(Pm + i), wp);
-    Pn[i] = (T)(wp * ig);
-    if (doR) {
-      double wr = fma(-theta, ld_val(Rl + i), ar);
-      if (mu != 0.0) wr = fma(-mu, ld_val(Rm + i), wr);
-      Rn[i] = (T)(wr * ig);
-    }
-  }
-}
 
 __global__ void __launch_bounds__(kOpThreads) stencil_diag_kernel(Operator A, double* __restrict__ diag) {
   const int64_t n = A.n;
@@ -402,7 +419,7 @@ cudaError_t launch_stencil_diag(const Operator& A, double* diag, cudaStream_t st
 cudaError_t launch_spmv(const Operator& A, const double* v, double* y, cudaStream_t st, const SolveState* gate,
                         int gmode) {
   int g = grid_for(A.n, 4);
-  if (A.kind == 0) csr_spmv_kernel<<<g, kOpThreads, 0, st>>>(A, v, y, gate, gmode);
+  if (A.kind == 0) sell_apply_kernel<0><<<sell_grid(A), kOpThreads, 0, st>>>(A, v, nullptr, y, gate, gmode);
   else if (A.dim == 3)
     stencil3d_apply_kernel<0><<<zmarch_grid(A), dim3(kZTx, kZTy), 0, st>>>(A, v, nullptr, y, gate, gmode);
   else stencil_spmv_kernel<false><<<g, kOpThreads, 0, st>>>(A, v, y, gate, gmode);
@@ -412,7 +429,7 @@ cudaError_t launch_spmv(const Operator& A, const double* v, double* y, cudaStrea
 cudaError_t launch_residual(const Operator& A, const double* b, const double* x, double* r, cudaStream_t st,
                             const SolveState* gate, int gmode) {
   int g = grid_for(A.n, 4);
-  if (A.kind == 0) csr_residual_kernel<<<g, kOpThreads, 0, st>>>(A, b, x, r, gate, gmode);
+  if (A.kind == 0) sell_apply_kernel<1><<<sell_grid(A), kOpThreads, 0, st>>>(A, x, b, r, gate, gmode);
   else if (A.dim == 3)
     stencil3d_apply_kernel<1><<<zmarch_grid(A), dim3(kZTx, kZTy), 0, st>>>(A, x, b, r, gate, gmode);
   else stencil_residual_kernel<false><<<g, kOpThreads, 0, st>>>(A, b, x, r, gate, gmode);
@@ -424,13 +441,15 @@ cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level, 
   int g = grid_for(A.n, 4);
   if (y32) {
     float* Yf = static_cast<float*>(Y);
-    if (A.kind == 0) csr_mpk_kernel<float><<<g, kOpThreads, 0, st>>>(A, Yf, ld, level, state, sbar_fixed, coef);
+    if (A.kind == 0)
+      sell_mpk_kernel<float><<<sell_grid(A), kOpThreads, 0, st>>>(A, Yf, ld, level, state, sbar_fixed, coef);
     else if (A.dim == 3)
       stencil_mpk_kernel<true, float><<<g, kOpThreads, 0, st>>>(A, Yf, ld, level, state, sbar_fixed, coef);
     else stencil_mpk_kernel<false, float><<<g, kOpThreads, 0, st>>>(A, Yf, ld, level, state, sbar_fixed, coef);
   } else {
     double* Yd = static_cast<double*>(Y);
-    if (A.kind == 0) csr_mpk_kernel<double><<<g, kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);
+    if (A.kind == 0)
+      sell_mpk_kernel<double><<<sell_grid(A), kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);
     else if (A.dim == 3)
       stencil_mpk_kernel<true, double><<<g, kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);
     else stencil_mpk_kernel<false, double><<<g, kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);

@@ -30,6 +30,16 @@ struct Operator {
   const int64_t* rowptr;
   const int32_t* col;
   const double* val;
+  // the same CSR matrix in sliced ELL (slices of kSliceRows rows, rows sorted
+  // by length within windows of kSliceWindow rows): lane t of slice s owns
+  // row s_row[32 s + t] (-1: padding), whose j-th entry sits at
+  // s_off[s] + 32 j + t of s_col / s_val; s_len[s] = the slice's longest row
+  int64_t nslices;
+  const int32_t* s_row;
+  const int64_t* s_off;
+  const int32_t* s_len;
+  const int32_t* s_col;
+  const double* s_val;
   // stencil: cells x fastest; kx [nz][ny][nx+1], ky [nz][ny+1][nx], kz [nz+1][ny][nx]
   int dim, nx, ny, nz;
   const double* kx;
@@ -37,6 +47,23 @@ struct Operator {
   const double* kz;
   const double* diag;  // sum of the faces of each cell (the diagonal of A)
 };
+
+constexpr int kSliceRows = 32;     // one warp per slice
+constexpr int kSliceWindow = 256;  // rows sorted by length within each window
+
+// binary32 -> binary64, exact, by integer operations on the bits (the FP64
+// unit's own conversion costs a 64-cycle binary64 slot per warp on GB300);
+// subnormal inputs take the rare hardware path
+__device__ __forceinline__ double widen(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xffu;
+  if (e == 0u && (u & 0x7fffffu) != 0u) return (double)f;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long e64 = e == 0u ? 0ull : (e == 255u ? 2047ull : (unsigned long long)(e + 896u));
+  const unsigned long long m64 = (unsigned long long)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(sign | (e64 << 52) | m64));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
 
 // ------------------------------------------------------------ solver state
 // Device-resident state of one s-step solve (Algorithm 5).  Only kernels read

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kVecThreads) recombine_kernel(const SolveState
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double sx = 0.0, sr = 0.0, sp = 0.0;
     for (int c = 0; c < nc; ++c) {
-      const double y = (double)Y[(int64_t)c * ld + i];
+      const double y = widen(Y[(int64_t)c * ld + i]);
       sx = fma(y, cx[c], sx);
       sr = fma(y, cr[c], sr);
       sp = fma(y, cp[c], sp);
