@@ -42,6 +42,10 @@ WORKLOADS = {
     "adjoint2d_512": dict(desc="differentiable solve: 2D 5-pt var-coef Poisson 512^2 (N=262,144), theta=exp(g) per "
                                "edge, loss ||x(theta)-x_t||^2; forward s-step solve + adjoint s-step solve + "
                                "face-gradient gather", smax=16, basis="newton", tol=1e-10),
+    # a smaller graph of the same family, used for kernel profiles
+    "rgg_400k": dict(desc="FP64 CSR: Laplacian of a 3D random geometric graph, N=400,000 (the 2M workload's "
+                          "recipe at a smaller size), for kernel profiles", smax=16, basis="newton", tol=1e-10,
+                     base="rgg_2m", scale=400_000),
     # a smaller grid of the same stencil family, used for kernel profiles
     "varcoef3d_96": dict(desc="FP64 3D 7-pt var-coef diffusion 96^3 (N=884,736), k=exp(N(0,1)) per face, "
                               "b~N(0,1), x0=0", smax=16, basis="newton", tol=1e-10, base="varcoef3d_160",
@@ -233,10 +237,14 @@ def run_rgg(args, cfg, pkg, torch, dev):
         el = e0.elapsed_time(e1) / 1e3
         st = sts[-1]
         h = pkg.sscg.history(st)
+        # one more solve, untimed, with direct launches and per-phase events
+        xp = torch.zeros(n, dtype=torch.float64, device=dev)
+        sp = solver.solve(b, xp, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], y_fp32=y32, profile=1)
+        phases = {k: getattr(sp, "t_" + k + "_ms") for k in ("mpk", "gram", "kappa", "control", "recombine", "other")}
         out[y32] = dict(value=args.steps / el, ms_per_step=el / args.steps * 1e3, outer=st.outer_iters,
                         inner=st.inner_iters, status=st.status, true_relres=st.true_relres,
                         mean_sk=float(np.mean([r["sk"] for r in h])) if h else None,
-                        fp32_replacements=st.fp32_replacements, x=x.clone())
+                        fp32_replacements=st.fp32_replacements, phase_ms_profiled_solve=phases, x=x.clone())
     err = float(torch.linalg.norm(out[1]["x"] - out[0]["x"]) / torch.linalg.norm(out[0]["x"]))
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
@@ -381,9 +389,10 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
-    if args.workload in ("rgg_2m", "batched_256", "adjoint2d_512"):
+    if args.workload in ("rgg_2m", "rgg_400k", "batched_256", "adjoint2d_512"):
         if rank == 0:
-            {"rgg_2m": run_rgg, "batched_256": run_batched, "adjoint2d_512": run_adjoint}[args.workload](
+            {"rgg_2m": run_rgg, "rgg_400k": run_rgg, "batched_256": run_batched,
+             "adjoint2d_512": run_adjoint}[args.workload](
                 args, cfg, pkg, torch, dev)
         if world > 1:
             dist.destroy_process_group()

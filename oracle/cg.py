@@ -33,6 +33,9 @@ Readings of the paper used here (the CUDA path takes the same ones):
   C22  the Meurant-Tichy state is fed every alpha; the estimates are used from
        global iteration 2 on (m + j + 1 > 1).
   C23  gamma_l := kappa(Y_{l+1}) for l = 1..s~-1; the break test at step j uses gamma_{j+1}.
+  C27  a Gram block with a non-finite entry (a basis column that overflowed,
+       possible with a binary32-stored basis) has kappa_l = +inf; the first
+       coordinate step then fails and the solve stops with BREAKDOWN (C17).
 """
 from __future__ import annotations
 
@@ -135,13 +138,18 @@ def kappa_estimates(G: np.ndarray, sbar: int, kappa_cut: float = KAPPA_CUT):
     """kappa_l ~ kappa(Y_l) = sqrt(kappa(G_l)), l = 1..sbar (Section 3).
 
     G_l is the leading (2l+1) x (2l+1) block of G; its extreme eigenvalues come
-    from a dense symmetric eigensolve.  Entry 0 is unused.
+    from a dense symmetric eigensolve.  Entry 0 is unused.  A block with a
+    non-finite entry (a basis column that overflowed) has no eigenvalues:
+    kappa_l = inf (reading C27), and the coordinate step then fails.
     """
     kap = np.full(sbar + 1, np.nan)
     lmins = np.full(sbar + 1, np.nan)
     lmaxs = np.full(sbar + 1, np.nan)
     for l in range(1, sbar + 1):
         n = 2 * l + 1
+        if not np.all(np.isfinite(G[:n, :n])):
+            kap[l] = math.inf
+            continue
         w = np.linalg.eigvalsh(G[:n, :n])
         lmins[l], lmaxs[l] = w[0], w[-1]
         if not (w[-1] > 0.0) or w[0] <= kappa_cut * w[-1]:

@@ -401,7 +401,7 @@ def test_full_size_rgg_2m(pkg):
     path = os.path.join(os.path.dirname(__file__), "golden", "oracle_counts.json")
     ref = json.load(open(path)) if os.path.exists(path) else {}
     for key, st in (("rgg_2m", sts[0]), ("rgg_2m_fp32", sts[1])):
-        if key in ref:
+        if key in ref and ref[key]["sstep_status"] == 0:
             assert abs(st.outer_iters - ref[key]["sstep_outer"]) <= 0.1 * ref[key]["sstep_outer"], key
             assert abs(st.inner_iters - ref[key]["sstep_inner"]) <= 0.1 * ref[key]["sstep_inner"], key
 
