@@ -51,17 +51,23 @@ struct Operator {
 constexpr int kSliceRows = 32;     // one warp per slice
 constexpr int kSliceWindow = 256;  // rows sorted by length within each window
 
-// binary32 -> binary64, exact, by integer operations on the bits (the FP64
-// unit's own conversion costs a 64-cycle binary64 slot per warp on GB300);
-// subnormal inputs take the rare hardware path
+// binary32 -> binary64, exact, by integer operations on the bits only (the
+// FP64 unit's own conversion costs a 64-cycle binary64 slot per warp on
+// GB300): normal numbers rebias the exponent; a subnormal m 2^-149 is
+// renormalised at its leading bit p (value 2^(p-149) (1 + ...)); zero, Inf and
+// NaN keep their class (NaN payloads are kept as they are)
 __device__ __forceinline__ double widen(float f) {
   const unsigned int u = __float_as_uint(f);
   const unsigned int e = (u >> 23) & 0xffu;
-  if (e == 0u && (u & 0x7fffffu) != 0u) return (double)f;
-  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-  const unsigned long long e64 = e == 0u ? 0ull : (e == 255u ? 2047ull : (unsigned long long)(e + 896u));
-  const unsigned long long m64 = (unsigned long long)(u & 0x7fffffu) << 29;
-  return __longlong_as_double((long long)(sign | (e64 << 52) | m64));
+  const unsigned int m = u & 0x7fffffu;
+  const int p = 31 - __clz(m | 1u);  // leading bit of a subnormal's mantissa
+  const unsigned long long m_norm = (unsigned long long)m << 29;
+  const unsigned long long m_sub = (unsigned long long)(m ^ (1u << p)) << (52 - p);
+  const unsigned long long e_norm = e == 255u ? 2047ull : (unsigned long long)(e + 896u);
+  const unsigned long long e_sub = m == 0u ? 0ull : (unsigned long long)(p + 874);
+  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                  ((e == 0u ? e_sub : e_norm) << 52) | (e == 0u ? (m == 0u ? 0ull : m_sub) : m_norm);
+  return __longlong_as_double((long long)bits);
 }
 __device__ __forceinline__ double widen(double d) { return d; }
 
