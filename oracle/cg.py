@@ -33,9 +33,11 @@ Readings of the paper used here (the CUDA path takes the same ones):
   C22  the Meurant-Tichy state is fed every alpha; the estimates are used from
        global iteration 2 on (m + j + 1 > 1).
   C23  gamma_l := kappa(Y_{l+1}) for l = 1..s~-1; the break test at step j uses gamma_{j+1}.
-  C27  a Gram block with a non-finite entry (a basis column that overflowed,
-       possible with a binary32-stored basis) has kappa_l = +inf; the first
-       coordinate step then fails and the solve stops with BREAKDOWN (C17).
+  C27  a Gram block G_l with a non-finite entry (a basis column that
+       overflowed, possible with a binary32-stored basis) has kappa_l = +inf,
+       so s~ stays below the first such column and the solve goes on; only a
+       non-finite leading block makes the first coordinate step fail
+       (BREAKDOWN, C17).
 """
 from __future__ import annotations
 
@@ -140,7 +142,7 @@ def kappa_estimates(G: np.ndarray, sbar: int, kappa_cut: float = KAPPA_CUT):
     G_l is the leading (2l+1) x (2l+1) block of G; its extreme eigenvalues come
     from a dense symmetric eigensolve.  Entry 0 is unused.  A block with a
     non-finite entry (a basis column that overflowed) has no eigenvalues:
-    kappa_l = inf (reading C27), and the coordinate step then fails.
+    kappa_l = inf (reading C27).
     """
     kap = np.full(sbar + 1, np.nan)
     lmins = np.full(sbar + 1, np.nan)

@@ -136,9 +136,22 @@ __device__ void kappa_body(const double* __restrict__ G, int ldg, int l, double 
   constexpr int kTri = 32 * 33 / 2;  // lower triangle of the largest trailing block
   __shared__ unsigned char tri_i[kTri], tri_j[kTri];
 
+  int nonfinite = 0;
   for (int e = t; e < n * n; e += kKappaThreads) {
     const int i = e / n, j = e - (e / n) * n;
-    A[i][j] = G[i * ldg + j];
+    const double g = G[i * ldg + j];
+    nonfinite |= ((__double_as_longlong(g) >> 52) & 0x7ff) == 0x7ff;
+    A[i][j] = g;
+  }
+  // a block with a non-finite entry (a basis column that overflowed) has no
+  // eigenvalues: kappa_l = inf, so s-tilde stays below that column
+  if (__syncthreads_or(nonfinite)) {
+    if (t == 0) {
+      lmin_out[l] = NAN;
+      lmax_out[l] = NAN;
+      kap[l] = INFINITY;
+    }
+    return;
   }
   if (t < 32) {  // entry e = i (i + 1) / 2 + j of the lower triangle, j <= i; thread t fills row t
     const int base = t * (t + 1) / 2;

@@ -180,6 +180,32 @@ def test_kappa_degenerate_gram(pkg, sbar, case):
             assert abs(kap[l] - kap_o[l]) <= 1e-8 * kap_o[l], (l, kap[l], kap_o[l])
 
 
+@pytest.mark.parametrize("bad", ["inf", "nan"])
+def test_kappa_nonfinite_trailing_column(pkg, bad):
+    """Reading C27: a basis column that overflowed (binary32 storage) puts
+    Inf/NaN into the trailing rows and columns of G; the blocks G_l that
+    contain it get kappa_l = inf, the leading blocks keep their values, as in
+    the oracle, so s-tilde stays below the overflowed column."""
+    sbar, col = 16, 24
+    ncols = 2 * sbar + 1
+    rng = np.random.default_rng(5)
+    Y = rng.standard_normal((500, ncols)) * np.logspace(0, 3, ncols)[None, :]
+    G = Y.T @ Y
+    G[col, :] = G[:, col] = np.inf if bad == "inf" else np.nan
+    kap_o, lmin_o, lmax_o = cg.kappa_estimates(G, sbar)
+    kap = torch.zeros(sbar + 1, dtype=torch.float64, device="cuda")
+    lmn = torch.zeros_like(kap)
+    lmx = torch.zeros_like(kap)
+    pkg.sscg.sscg_kappa(dev(G.ravel()), ncols, sbar, 2.0 ** -44, kap, lmn, lmx)
+    kap, lmn, lmx = kap.cpu().numpy(), lmn.cpu().numpy(), lmx.cpu().numpy()
+    for l in range(1, sbar + 1):
+        if 2 * l + 1 > col:
+            assert math.isinf(kap_o[l]) and math.isinf(kap[l]), (l, kap[l])
+        else:
+            assert abs(lmx[l] - lmax_o[l]) <= 1e-13 * lmax_o[l]
+            assert abs(kap[l] - kap_o[l]) <= 1e-8 * kap_o[l] or (math.isinf(kap_o[l]) and math.isinf(kap[l]))
+
+
 # ---------------------------------------------------------------- solves
 
 def agreeing_prefix(hist_g, hist_o, rel=1e-8):
