@@ -217,8 +217,10 @@ typedef struct {
  * offset sum_{s' < s} nrhs[s'] n_{s'} + k n_s; x holds the initial guesses on
  * entry and the solutions on exit.  s_max: per-system sigma in
  * [1, SSCG_MAX_S] (e.g. from sscg_autotune).  opts: as for sscg_solve
- * (y_fp32 unsupported here; use_graph = 0 replaces the WHILE node by host
- * polling every check_every outer loops).  Returns SSCG_OK if every pair
+ * (y_fp32 and gram_mode = 1 are unsupported here: SSCG_ERR_UNSUPPORTED;
+ * batch_chunk_rows / batch_gram_rows set the tile shapes; use_graph = 0
+ * replaces the WHILE node by host polling every check_every outer loops).
+ * Returns SSCG_OK if every pair
  * converged, SSCG_NOT_CONVERGED / SSCG_BREAKDOWN if some did not, or a
  * negative error.  Device memory for the batch is allocated for the call. */
 int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double* x,

@@ -36,6 +36,10 @@ template <typename T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }  // frees on every return path of the entry points
   cudaError_t ensure(size_t count) {
     if (count <= n) return cudaSuccess;
     if (p) cudaFree(p);
@@ -815,7 +819,7 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
   if (opts) o = *opts;
   int rc = validate_opts(o);
   if (rc) return rc;
-  if (o.y_fp32) return SSCG_ERR_UNSUPPORTED;
+  if (o.y_fp32 || o.gram_mode != 0) return SSCG_ERR_UNSUPPORTED;
   // ---- pairs, chunks and Gram blocks (host)
   const int chunk_rows = o.batch_chunk_rows > 0 ? o.batch_chunk_rows : kBatchChunk;
   const int gram_rows = o.batch_gram_rows > 0 ? o.batch_gram_rows : kBatchGramRows;
