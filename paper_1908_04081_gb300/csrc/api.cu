@@ -399,11 +399,16 @@ int sscg_create_csr(sscg_t* out, int64_t n, int64_t nnz, const int64_t* rowptr, 
       return fail(e, "read val");
   }
   // the kernels index with these: reject a malformed matrix here
-  if (hrp[0] != 0 || hrp[n] != nnz) return fail(cudaErrorInvalidValue, "rowptr bounds");
+  auto bad = [&](const char* what) {
+    g_last_cuda_error = std::string("create_csr: ") + what;
+    sscg_destroy(h);
+    return SSCG_ERR_INVALID_ARG;
+  };
+  if (hrp[0] != 0 || hrp[n] != nnz) return bad("rowptr[0] must be 0 and rowptr[n] = nnz");
   for (int64_t i = 0; i < n; ++i)
-    if (hrp[i + 1] < hrp[i]) return fail(cudaErrorInvalidValue, "rowptr order");
+    if (hrp[i + 1] < hrp[i]) return bad("rowptr must not decrease");
   for (int64_t k = 0; k < nnz; ++k)
-    if (hcol[k] < 0 || hcol[k] >= n) return fail(cudaErrorInvalidValue, "column index");
+    if (hcol[k] < 0 || hcol[k] >= n) return bad("column index out of range");
   const int64_t nslices = (n + kSliceRows - 1) / kSliceRows;
   std::vector<int32_t> srow(nslices * kSliceRows, -1), slen(nslices);
   std::vector<int64_t> soff(nslices + 1, 0);

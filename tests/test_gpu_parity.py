@@ -70,6 +70,59 @@ def test_csr_spmv(pkg):
     assert np.linalg.norm(y.cpu().numpy() - ref) <= 1e-14 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("case", ["empty_rows", "one_dense_row", "tiny", "ragged_slices"])
+def test_csr_sliced_layout_edge_cases(pkg, case):
+    """The CSR kernels run on a sliced-ELL copy (32-row slices, rows sorted by
+    length within 256-row windows): empty rows, a dense row next to short
+    ones, fewer rows than a slice and a ragged last slice give A v to within
+    rounding of a row-by-row sum."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(11)
+    if case == "empty_rows":
+        n = 300
+        M = sp.random(n, n, density=0.02, random_state=3, format="lil")
+        for i in range(0, n, 7):
+            M[i, :] = 0
+    elif case == "one_dense_row":
+        n = 257
+        M = sp.random(n, n, density=0.01, random_state=4, format="lil")
+        M[100, :] = rng.standard_normal(n)
+    elif case == "tiny":
+        n = 5
+        M = sp.random(n, n, density=0.5, random_state=5, format="lil")
+    else:
+        n = 32 * 9 + 13
+        M = sp.random(n, n, density=0.05, random_state=6, format="lil")
+    A = sp.csr_matrix(M)
+    A.sort_indices()
+    rowptr = A.indptr.astype(np.int64)
+    col = A.indices.astype(np.int32)
+    val = A.data.astype(np.float64)
+    s = pkg.Solver.csr(rowptr, col, val)
+    v = rng.standard_normal(n)
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s.spmv(dev(v), y)
+    ref = np.array([sum((val[k] * v[col[k]] for k in range(rowptr[i], rowptr[i + 1])), 0.0) for i in range(n)])
+    mag = np.array([sum((abs(val[k] * v[col[k]]) for k in range(rowptr[i], rowptr[i + 1])), 0.0) for i in range(n)])
+    got = y.cpu().numpy()
+    # per row: rounding of a sum of len_i products, relative to sum |a_ik v_k|
+    assert np.all(np.abs(got - ref) <= 1e-14 * mag), np.max(np.abs(got - ref) / np.maximum(mag, 1e-300))
+    assert np.all(got[mag == 0] == 0.0)
+
+
+def test_csr_malformed_input_is_rejected(pkg):
+    """Creation checks the row pointers and column indices the kernels index with."""
+    rowptr = np.array([0, 2, 1, 3], dtype=np.int64)          # not monotone
+    col = np.array([0, 1, 2], dtype=np.int32)
+    val = np.ones(3)
+    with pytest.raises(pkg.sscg.SscgError):
+        pkg.Solver.csr(rowptr, col, val)
+    rowptr = np.array([0, 1, 2, 3], dtype=np.int64)
+    col = np.array([0, 5, 2], dtype=np.int32)                 # column out of range
+    with pytest.raises(pkg.sscg.SscgError):
+        pkg.Solver.csr(rowptr, col, val)
+
+
 @pytest.mark.parametrize("kind", ["monomial", "newton", "chebyshev"])
 @pytest.mark.parametrize("s", [1, 3, 8, 16])
 def test_basis_columns(pkg, kind, s):
