@@ -348,6 +348,20 @@ def run_batched(args, cfg, pkg, torch, dev):
             hc_iters = sum(ex.map(run_systems, [list(range(t, len(systems), 16)) for t in range(16)]))
         torch.cuda.synchronize()
         hc_el = time.perf_counter() - t0
+        # batched HSCG: all pairs in lock-step in one graph launch, like the s-step batch
+        xh.zero_()
+        pkg.sscg.sscg_solve_batch_hscg([s.h for s in solvers], nrhs, b, xh, cfg["tol"])  # warm-up
+        xh.zero_()
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record()
+        hrc, hst = pkg.sscg.sscg_solve_batch_hscg([s.h for s in solvers], nrhs, b, xh, cfg["tol"])
+        h1.record()
+        torch.cuda.synchronize()
+        hb_el = h0.elapsed_time(h1) / 1e3
+        hb = {"value": pairs / hb_el, "unit": "system-rhs solves/s", "seconds": hb_el, "status": hrc,
+              "converged": hst["converged"], "iters_total": hst["inner_iters"], "max_iters": hst["max_iters"],
+              "note": "sscg_solve_batch_hscg: plain CG for every pair in lock-step, one graph launch"}
     line = {"metric": METRIC, "value": pairs * args.steps / el, "unit": "system-rhs solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -365,6 +379,7 @@ def run_batched(args, cfg, pkg, torch, dev):
                                  "iters_total": hs_iters, "converged": hs_conv,
                                  "note": "each pair by sscg_solve_hscg (one graph launch and one host wait per pair), "
                                          "host-timed"}
+        line["hscg_batched"] = hb
         line["hscg_concurrent"] = {"value": pairs / hc_el, "unit": "system-rhs solves/s", "seconds": hc_el,
                                    "iters_total": hc_iters,
                                    "note": "the same per-pair HSCG solves from 16 host threads (systems dealt "

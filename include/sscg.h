@@ -240,7 +240,19 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
 int sscg_autotune(sscg_t h, const double* b, double tol, const int* candidates, int ncand, int trial_outer,
                   sscg_basis basis, int* best, double* times);
 
-/* Autotuner for the batched solve's tile shapes (rows per work chunk and per
+/* Plain CG (Algorithm 1, as sscg_solve_hscg) for the same batch layout as
+ * sscg_solve_batch, every pair in lock-step inside one CUDA graph launch
+ * (WHILE over bodies of 8 iterations and a true-residual confirmation per
+ * pair): the comparator of the batched s-step solve.  systems, nsys, nrhs, b,
+ * x, tol, stats: as for sscg_solve_batch (stats->outer_loops = the largest
+ * iteration count; pair_outer = pair_inner = each pair's iterations).
+ * max_iters caps each pair's iterations (<= 0: 100000); chunk_rows: rows per
+ * work chunk (0 = 2048, else 128..1048576).  Returns SSCG_OK if every pair
+ * converged, else the first non-OK pair status, or a negative error. */
+int sscg_solve_batch_hscg(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double* x, double tol,
+                          int max_iters, int chunk_rows, sscg_batch_stats* stats, void* cuda_stream);
+
+/* Autotuner for the batched solve's tile shapes/* Autotuner for the batched solve's tile shapes (rows per work chunk and per
  * Gram block, sscg_opts.batch_chunk_rows / batch_gram_rows): for each of the
  * ncand candidates (chunk_rows[i], gram_rows[i]) run sscg_solve_batch on the
  * given batch (same arguments as there; x0 = 0 in a scratch array, b

@@ -1041,6 +1041,181 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
   return worst;
 }
 
+int sscg_solve_batch_hscg(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double* x, double tol,
+                          int max_iters, int chunk_rows_opt, sscg_batch_stats* stats, void* cuda_stream) {
+  if (!systems || nsys <= 0 || !nrhs || !b || !x || !(tol > 0.0)) return SSCG_ERR_INVALID_ARG;
+  if (chunk_rows_opt != 0 && (chunk_rows_opt < 128 || chunk_rows_opt > (1 << 20))) return SSCG_ERR_INVALID_ARG;
+  const int chunk_rows = chunk_rows_opt > 0 ? chunk_rows_opt : kBatchChunk;
+  const int iters_cap = max_iters > 0 ? max_iters : 100000;
+  constexpr int kItersPerBody = 8;
+  std::vector<BatchPair> pairs;
+  std::vector<int> chunk_pair;
+  int64_t off = 0;
+  for (int s = 0; s < nsys; ++s) {
+    if (!systems[s] || nrhs[s] < 0) return SSCG_ERR_INVALID_ARG;
+    const int64_t n = systems[s]->n;
+    for (int k = 0; k < nrhs[s]; ++k) {
+      BatchPair bp;
+      bp.op = systems[s]->op;
+      bp.off = off;
+      bp.n = n;
+      bp.chunk0 = (int)chunk_pair.size();
+      bp.nchunk = (int)((n + chunk_rows - 1) / chunk_rows);
+      bp.gblk0 = 0;
+      bp.ngblk = 0;
+      const int j = (int)pairs.size();
+      for (int c = 0; c < bp.nchunk; ++c) chunk_pair.push_back(j);
+      pairs.push_back(bp);
+      off += n;
+    }
+  }
+  const int P = (int)pairs.size();
+  if (P == 0) return SSCG_OK;
+  const int64_t total = off;
+  DevBuf<BatchPair> d_pairs;
+  DevBuf<int> d_cp;
+  DevBuf<SolveState> d_st;
+  DevBuf<double> d_r, d_p, d_q, d_rt, d_part;
+  DevBuf<unsigned int> d_cnt;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int result = SSCG_OK;
+  float device_ms = 0.f;
+  std::vector<SolveState> hs(P);
+  int launches = 0;
+  unsigned int bodies_run = 0;
+  do {
+    cudaError_t e;
+#define BK(call)                                  \
+  if ((e = (call)) != cudaSuccess) {              \
+    result = cuda_fail(e, #call);                 \
+    break;                                        \
+  }
+    BK(d_pairs.ensure(P));
+    BK(d_cp.ensure(chunk_pair.size()));
+    BK(d_st.ensure(P));
+    BK(d_r.ensure(total));
+    BK(d_p.ensure(total));
+    BK(d_q.ensure(total));
+    BK(d_rt.ensure(total));
+    BK(d_part.ensure(chunk_pair.size()));
+    BK(d_cnt.ensure(2));
+    BK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    BK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    BK(cudaEventCreate(&t0));
+    BK(cudaEventCreate(&t1));
+    BK(cudaEventRecord(ev, (cudaStream_t)cuda_stream));
+    BK(cudaStreamWaitEvent(st, ev, 0));
+    for (int j = 0; j < P; ++j) {
+      std::memset(&hs[j], 0, sizeof(SolveState));
+      hs[j].tol = tol;
+      hs[j].status = SSCG_NOT_CONVERGED;
+      hs[j].h_max_iters = iters_cap;
+    }
+    BK(cudaMemcpyAsync(d_pairs.p, pairs.data(), P * sizeof(BatchPair), cudaMemcpyHostToDevice, st));
+    BK(cudaMemcpyAsync(d_cp.p, chunk_pair.data(), chunk_pair.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    BK(cudaMemcpyAsync(d_st.p, hs.data(), P * sizeof(SolveState), cudaMemcpyHostToDevice, st));
+    BK(cudaMemsetAsync(d_cnt.p, 0, 2 * sizeof(unsigned int), st));
+    BatchView v;
+    std::memset(&v, 0, sizeof(v));
+    v.pairs = d_pairs.p;
+    v.npairs = P;
+    v.chunk_pair = d_cp.p;
+    v.nchunks = (int)chunk_pair.size();
+    v.states = d_st.p;
+    v.active = d_cnt.p;
+    v.bodies = d_cnt.p + 1;
+    v.max_bodies = (iters_cap + kItersPerBody - 1) / kItersPerBody + 2;
+    v.chunk_rows = chunk_rows;
+    v.gram_rows = kBatchGramRows;
+    BK(launch_batch_hscg_init(v, b, x, d_r.p, d_p.p, d_part.p, st));
+    launches += 3;
+    // one graph: arm the condition, then WHILE (a pair is running) { 8 iterations, confirmation }
+    BK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    BK(cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault));
+    BK(cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ea = launch_batch_arm(cond, st);
+    cudaGraph_t tmp;
+    cudaError_t ee = cudaStreamEndCapture(st, &tmp);
+    BK(ea);
+    BK(ee);
+    size_t nn = 1;
+    cudaGraphNode_t arm_node;
+    BK(cudaGraphGetNodes(graph, &arm_node, &nn));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    BK(cudaGraphAddNode(&wnode, graph, &arm_node, nullptr, 1, &cp));
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    BK(cudaStreamBeginCaptureToGraph(st, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaError_t eb = launch_batch_begin(v, st);
+    for (int i = 0; i < kItersPerBody && eb == cudaSuccess; ++i)
+      eb = launch_batch_hscg_iteration(v, x, d_r.p, d_p.p, d_q.p, d_part.p, st);
+    if (eb == cudaSuccess) eb = launch_batch_hscg_check(v, b, x, d_rt.p, d_r.p, d_p.p, d_part.p, cond, 1, st);
+    ee = cudaStreamEndCapture(st, &tmp);
+    BK(eb);
+    BK(ee);
+    BK(cudaGraphInstantiate(&gexec, graph, 0));
+    BK(cudaEventRecord(t0, st));
+    BK(cudaGraphLaunch(gexec, st));
+    BK(cudaEventRecord(t1, st));
+    BK(cudaMemcpyAsync(hs.data(), d_st.p, P * sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    BK(cudaMemcpyAsync(&bodies_run, d_cnt.p + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    BK(cudaStreamSynchronize(st));
+    BK(cudaEventElapsedTime(&device_ms, t0, t1));
+    launches += 1 + (int)bodies_run * (1 + 3 * kItersPerBody + 4);
+    BK(cudaEventRecord(ev, st));
+    BK(cudaStreamWaitEvent((cudaStream_t)cuda_stream, ev, 0));
+#undef BK
+  } while (0);
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  if (st) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  if (ev) cudaEventDestroy(ev);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (result) return result;
+  int conv = 0, worst = SSCG_OK, max_it = 0;
+  int64_t inner = 0;
+  double max_rel = 0.0;
+  for (int j = 0; j < P; ++j) {
+    const SolveState& q = hs[j];
+    const int status = q.done ? q.status : SSCG_NOT_CONVERGED;
+    if (status == SSCG_OK) ++conv;
+    else if (worst == SSCG_OK) worst = status;
+    max_it = std::max(max_it, q.h_iters);
+    inner += q.h_iters;
+    const double rel = q.normb > 0.0 ? std::sqrt(q.rt2) / q.normb : 0.0;
+    max_rel = std::max(max_rel, rel);
+    if (stats) {
+      if (stats->pair_status) stats->pair_status[j] = status;
+      if (stats->pair_outer) stats->pair_outer[j] = q.h_iters;
+      if (stats->pair_inner) stats->pair_inner[j] = q.h_iters;
+    }
+  }
+  if (stats) {
+    stats->npairs = P;
+    stats->converged = conv;
+    stats->outer_loops = max_it;
+    stats->host_syncs = 1;
+    stats->kernel_launches = launches;
+    stats->graph_launches = 1;
+    stats->inner_iters = inner;
+    stats->max_true_relres = max_rel;
+    stats->device_ms = device_ms;
+  }
+  return worst;
+}
+
 int sscg_autotune_batch(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double tol,
                         const int* s_max, sscg_basis basis, const int* chunk_rows, const int* gram_rows, int ncand,
                         int trial_outer, int* best, double* times, void* cuda_stream) {

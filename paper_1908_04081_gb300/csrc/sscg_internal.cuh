@@ -236,6 +236,14 @@ cudaError_t launch_batch_check(const BatchView& v, const double* b, const double
 cudaError_t launch_batch_init(const BatchView& v, const double* b, double* x, double* Y, int64_t LD,
                               double* partials, cudaStream_t st);
 cudaError_t launch_batch_begin(const BatchView& v, cudaStream_t st);
+// batched HSCG (the comparator of the batched s-step solve)
+cudaError_t launch_batch_hscg_init(const BatchView& v, const double* b, double* x, double* r, double* p,
+                                   double* partials, cudaStream_t st);
+cudaError_t launch_batch_hscg_iteration(const BatchView& v, double* x, double* r, double* p, double* q,
+                                        double* partials, cudaStream_t st);
+cudaError_t launch_batch_hscg_check(const BatchView& v, const double* b, const double* x, double* rt, double* r,
+                                    double* p, double* partials, cudaGraphConditionalHandle cond, int use_cond,
+                                    cudaStream_t st);
 cudaError_t launch_batch_end(const BatchView& v, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
 cudaError_t launch_batch_arm(cudaGraphConditionalHandle cond, cudaStream_t st);
 cudaError_t launch_solve_cond(const SolveState* state, cudaGraphConditionalHandle cond, cudaStream_t st);

@@ -635,6 +635,198 @@ __global__ void batch_arm_kernel(cudaGraphConditionalHandle cond) {
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, 1u);
 }
 
+// ------------------------------------------------------------ batched HSCG
+// Algorithm 1 for every pair in lock-step, the comparator of the batched
+// s-step solve: per iteration q = A p with (p, q), then x, r and (r, r), then
+// p; every pair keeps its own alpha, beta and test (reading C16 confirmation
+// with the true residual at the end of each graph body).
+__global__ void __launch_bounds__(kVecThreads) batch_hscg_init_kernel(BatchView v, const double* __restrict__ b,
+                                                                      const double* __restrict__ x,
+                                                                      double* __restrict__ r, double* __restrict__ p,
+                                                                      double* __restrict__ partials) {
+  // pass 1 of 2: r = p = b - A x and ||b||^2
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    SolveState* st = v.states + j;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
+    if (r1 > bp.n) r1 = bp.n;
+    const double* xb = x + bp.off;
+    double s = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double bi = b[bp.off + i];
+      const double ri = bi - batch_apply(bp.op, xb, i);
+      r[bp.off + i] = ri;
+      p[bp.off + i] = ri;
+      s = fma(bi, bi, s);
+    }
+    double tot;
+    if (pair_last_sum(s, bp, st, partials, c, &tot) && threadIdx.x == 0) {
+      st->normb = sqrt(tot);
+      if (tot == 0.0) {
+        st->zero_rhs = 1;
+        st->done = 1;
+        st->status = SSCG_OK;
+      } else if (!isfinite(tot)) {
+        st->done = 1;
+        st->status = SSCG_NONFINITE;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) batch_hscg_rr_kernel(BatchView v, const double* __restrict__ r,
+                                                                    double* __restrict__ partials) {
+  // pass 2 of 2: ||r0||^2 and the initial test
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    SolveState* st = v.states + j;
+    if (st->done) continue;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
+    if (r1 > bp.n) r1 = bp.n;
+    double s = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) s = fma(r[bp.off + i], r[bp.off + i], s);
+    double tot;
+    if (pair_last_sum(s, bp, st, partials, c, &tot) && threadIdx.x == 0) {
+      st->h_rr = tot;
+      if (!isfinite(tot)) {
+        st->done = 1;
+        st->status = SSCG_NONFINITE;
+      } else if (sqrt(tot) / st->normb <= st->tol) {
+        st->converged_est = 1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ bool hscg_running(const SolveState* st) { return !st->done && !st->converged_est; }
+
+__global__ void __launch_bounds__(kVecThreads) batch_hscg_q_kernel(BatchView v, const double* __restrict__ p,
+                                                                   double* __restrict__ q,
+                                                                   double* __restrict__ partials) {
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    SolveState* st = v.states + j;
+    if (!hscg_running(st)) continue;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
+    if (r1 > bp.n) r1 = bp.n;
+    const double* pb = p + bp.off;
+    double s = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double qi = batch_apply(bp.op, pb, i);
+      q[bp.off + i] = qi;
+      s = fma(pb[i], qi, s);
+    }
+    double tot;
+    if (pair_last_sum(s, bp, st, partials, c, &tot) && threadIdx.x == 0) {
+      st->h_pq = tot;
+      st->h_alpha = st->h_rr / tot;
+      if (!(tot > 0.0) || !isfinite(st->h_alpha)) {
+        st->done = 1;
+        st->status = SSCG_BREAKDOWN;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) batch_hscg_update_kernel(BatchView v, double* __restrict__ x,
+                                                                        double* __restrict__ r,
+                                                                        const double* __restrict__ p,
+                                                                        const double* __restrict__ q,
+                                                                        double* __restrict__ partials) {
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    SolveState* st = v.states + j;
+    if (!hscg_running(st)) continue;
+    const double alpha = st->h_alpha;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
+    if (r1 > bp.n) r1 = bp.n;
+    double s = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const int64_t k = bp.off + i;
+      x[k] = fma(alpha, p[k], x[k]);
+      const double ri = fma(-alpha, q[k], r[k]);
+      r[k] = ri;
+      s = fma(ri, ri, s);
+    }
+    double tot;
+    if (pair_last_sum(s, bp, st, partials, c, &tot) && threadIdx.x == 0) {
+      st->h_beta = tot / st->h_rr;
+      st->h_rr = tot;
+      st->h_iters += 1;
+      st->m = st->h_iters;
+      if (sqrt(tot) / st->normb <= st->tol) st->converged_est = 1;
+      if (st->h_iters >= st->h_max_iters && !st->converged_est) {
+        st->status = SSCG_NOT_CONVERGED;
+        st->done = 1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) batch_hscg_p_kernel(BatchView v, const double* __restrict__ r,
+                                                                   double* __restrict__ p) {
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    const SolveState* st = v.states + j;
+    if (!hscg_running(st)) continue;
+    const double beta = st->h_beta;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
+    if (r1 > bp.n) r1 = bp.n;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const int64_t k = bp.off + i;
+      p[k] = fma(beta, p[k], r[k]);
+    }
+  }
+}
+
+// r := p := b - A x for the pairs whose confirmation failed (C16)
+__global__ void __launch_bounds__(kVecThreads) batch_hscg_replace_kernel(BatchView v, const double* __restrict__ rt,
+                                                                         double* __restrict__ r,
+                                                                         double* __restrict__ p) {
+  for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
+    const int j = v.chunk_pair[c];
+    const BatchPair& bp = v.pairs[j];
+    const SolveState* st = v.states + j;
+    if (st->done || !st->replace_pending) continue;
+    const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
+    int64_t r1 = r0 + v.chunk_rows;
+    if (r1 > bp.n) r1 = bp.n;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const int64_t k = bp.off + i;
+      r[k] = rt[k];
+      p[k] = rt[k];
+    }
+  }
+}
+
+__global__ void batch_hscg_end_kernel(BatchView v) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.npairs; j += gridDim.x * blockDim.x) {
+    SolveState* st = v.states + j;
+    if (st->done) continue;
+    if (st->replace_pending) {
+      st->replace_pending = 0;
+      st->converged_est = 0;
+      st->h_rr = st->rt2;
+      st->replacements += 1;
+    }
+    atomicAdd(v.active, 1u);
+  }
+}
+
 int chunk_grid(const BatchView& v) {
   int g = v.nchunks < 152 * 8 ? v.nchunks : 152 * 8;
   return g < 1 ? 1 : g;
@@ -660,6 +852,33 @@ cudaError_t launch_batch_check(const BatchView& v, const double* b, const double
                                int64_t LD, double* partials, cudaStream_t st) {
   batch_true_residual_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, b, x, rt, partials);
   batch_replacement_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, rt, Y, LD);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_hscg_init(const BatchView& v, const double* b, double* x, double* r, double* p,
+                                   double* partials, cudaStream_t st) {
+  batch_hscg_init_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, b, x, r, p, partials);
+  batch_hscg_rr_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, r, partials);
+  batch_zero_x_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_hscg_iteration(const BatchView& v, double* x, double* r, double* p, double* q,
+                                        double* partials, cudaStream_t st) {
+  batch_hscg_q_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, p, q, partials);
+  batch_hscg_update_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, x, r, p, q, partials);
+  batch_hscg_p_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, r, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_hscg_check(const BatchView& v, const double* b, const double* x, double* rt, double* r,
+                                    double* p, double* partials, cudaGraphConditionalHandle cond, int use_cond,
+                                    cudaStream_t st) {
+  batch_true_residual_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, b, x, rt, partials);
+  batch_hscg_replace_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, rt, r, p);
+  const int g = (v.npairs + 255) / 256;
+  batch_hscg_end_kernel<<<g < 1 ? 1 : g, 256, 0, st>>>(v);
+  if (use_cond) batch_cond_kernel<<<1, 32, 0, st>>>(v, cond);
   return cudaGetLastError();
 }
 

@@ -104,6 +104,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                        C.POINTER(C.c_int), C.c_int, C.POINTER(Opts), C.POINTER(BatchStats), _P]),
         "sscg_autotune": (C.c_int, [_P, _P, C.c_double, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int,
                                     C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "sscg_solve_batch_hscg": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(C.c_int), _P, _P, C.c_double,
+                                            C.c_int, C.c_int, C.POINTER(BatchStats), _P]),
         "sscg_autotune_batch": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(C.c_int), _P, C.c_double,
                                           C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                           C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
@@ -337,6 +339,27 @@ def sscg_solve_batch(handles, nrhs, b, x, tol: float, s_max, basis="newton", opt
                     kernel_launches=st.kernel_launches, graph_launches=st.graph_launches,
                     inner_iters=st.inner_iters, max_true_relres=st.max_true_relres, device_ms=st.device_ms,
                     pair_status=list(ps)[:npairs], pair_outer=list(po)[:npairs], pair_inner=list(pi)[:npairs])
+
+
+def sscg_solve_batch_hscg(handles, nrhs, b, x, tol: float, max_iters: int = 0, chunk_rows: int = 0, stream=None):
+    """Batched plain CG (Algorithm 1) over the same pairs as sscg_solve_batch,
+    in one graph launch.  Returns (status, stats dict with per-pair arrays)."""
+    nsys = len(handles)
+    hs = (_P * nsys)(*handles)
+    nr = (C.c_int * nsys)(*[int(k) for k in nrhs])
+    npairs = int(sum(int(k) for k in nrhs))
+    st = BatchStats()
+    ps, po, pi = (C.c_int * max(npairs, 1))(), (C.c_int * max(npairs, 1))(), (C.c_int * max(npairs, 1))()
+    st.pair_status = C.cast(ps, C.POINTER(C.c_int))
+    st.pair_outer = C.cast(po, C.POINTER(C.c_int))
+    st.pair_inner = C.cast(pi, C.POINTER(C.c_int))
+    rc = load_library().sscg_solve_batch_hscg(hs, nsys, nr, _f64(b), _f64(x), tol, int(max_iters), int(chunk_rows),
+                                              C.byref(st), _stream_ptr(stream))
+    _check(rc, "sscg_solve_batch_hscg", allow_status=True)
+    return rc, dict(npairs=st.npairs, converged=st.converged, max_iters=st.outer_loops,
+                    kernel_launches=st.kernel_launches, graph_launches=st.graph_launches,
+                    inner_iters=st.inner_iters, max_true_relres=st.max_true_relres, device_ms=st.device_ms,
+                    pair_status=list(ps)[:npairs], pair_iters=list(pi)[:npairs])
 
 
 def sscg_autotune_batch(handles, nrhs, b, tol: float, s_max, shapes, trial_outer: int = 20, basis="newton",

@@ -132,3 +132,31 @@ def test_batch_tile_shapes_and_their_autotuner(pkg):
     with pytest.raises(pkg.sscg.SscgError):  # the batch has no binary32-pair Gram
         pkg.sscg.sscg_solve_batch(hs, nrhs, bt, torch.zeros_like(bt), 1e-10, s_max, "newton",
                                   pkg.sscg.sscg_opts_default(gram_mode=1))
+
+
+def test_batched_hscg_matches_per_pair_hscg(pkg):
+    """The batched HSCG comparator (one graph launch over all pairs) takes each
+    pair through the iterations of the single-system HSCG (its kernels sum in
+    another order: counts within 2, solutions within 1e-8), every pair to tol
+    (independent residual), and the oracle's HSCG count within 2 per pair."""
+    systems, solvers, nrhs, b = build(pkg, 6, 77, 300, 9000, 3)
+    bt = torch.tensor(b, device="cuda")
+    xb = torch.zeros_like(bt)
+    rc, stats = pkg.sscg.sscg_solve_batch_hscg([s.h for s in solvers], nrhs, bt, xb, 1e-10)
+    assert rc == 0 and stats["converged"] == stats["npairs"] == sum(nrhs)
+    assert stats["graph_launches"] == 1 and stats["device_ms"] > 0.0
+    x = xb.cpu().numpy()
+    off, j = 0, 0
+    for solver, (st, B) in zip(solvers, systems):
+        A = as_matrix(st)
+        for k in range(B.shape[0]):
+            xs = torch.zeros(st.n, dtype=torch.float64, device="cuda")
+            r = solver.hscg(torch.tensor(B[k], device="cuda"), xs, tol=1e-10)
+            xj = x[off:off + st.n]
+            assert r.status == 0 and abs(stats["pair_iters"][j] - r.inner_iters) <= 2
+            assert np.linalg.norm(xj - xs.cpu().numpy()) <= 1e-8 * np.linalg.norm(xj)
+            assert np.linalg.norm(B[k] - A @ xj) <= 1e-10 * np.linalg.norm(B[k])
+            _, h = cg.hscg(A, B[k], np.zeros(st.n), 1e-10)
+            assert abs(h["iters"] - stats["pair_iters"][j]) <= 2
+            off += st.n
+            j += 1
