@@ -354,6 +354,25 @@ def test_option_readings(pkg, opts):
     compare_solves(xt.cpu().numpy(), st, pkg.sscg.history(st), x_o, info, 1e-10)
 
 
+def test_adjoint_type_rhs_solve(pkg):
+    """The adjoint system of the differentiable workload, A lambda = 2 (x - x_t),
+    on a 96^2 grid: the method takes far fewer inner steps per outer loop than
+    for the forward right-hand side (oracle: 222 outer / 1185 inner against 137
+    / 1275); the GPU follows the oracle's run (agreeing prefix, counts within
+    10 %, solution within 1e-8)."""
+    import scipy.sparse.linalg as spla
+    op, b, x0, extra = gen.config_problem("adjoint2d_512", scale=96)
+    A = as_matrix(op)
+    x = spla.spsolve(A.tocsc(), b)
+    g = 2.0 * (x - extra["x_target"])
+    x_o, info = cg.sstep_cg(A, g, np.zeros_like(g), 1e-10, cg.Options(smax=16, basis="newton"))
+    s = stencil_solver(pkg, op)
+    lam = dev(np.zeros_like(g))
+    st = s.solve(dev(g), lam, tol=1e-10, s_max=16, basis="newton", hist_cap=4000)
+    compare_solves(lam.cpu().numpy(), st, pkg.sscg.history(st), x_o, info, 1e-10)
+    assert info["inner"] / info["outer"] < 6.0
+
+
 def test_nonzero_x0_and_host_path(pkg):
     A, b, _, _ = gen.config_problem("poisson2d_64", scale=20)
     x0 = gen.uniform_vector(A.n, 9)
