@@ -145,6 +145,45 @@ __global__ void __launch_bounds__(kOpThreads) stencil_mpk_kernel(Operator A, T* 
   }
 }
 
+// One matrix-powers level for a stencil, one cell per thread on a 3D grid
+// (x in 32-lane rows, y in 8-row tiles, z per grid plane): the coordinates
+// come from the launch indices, with no division, and the sum is formed in
+// stencil_apply's order (same bits as the grid-stride kernel).
+template <bool DIM3, typename T>
+__global__ void __launch_bounds__(256) stencil_mpk_grid_kernel(Operator A, T* __restrict__ Y, int64_t ld,
+                                                                 int level, const SolveState* __restrict__ st,
+                                                                 int sbar_fixed, LevelCoef coef) {
+  int sbar = sbar_fixed;
+  if (sbar <= 0) {
+    if (st->done) return;
+    sbar = st->sbar;
+  }
+  const bool doP = level < sbar;
+  const bool doR = level + 1 < sbar;
+  if (!doP) return;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int yy = blockIdx.y * 8 + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= A.nx || yy >= A.ny) return;
+  const int64_t i = ((int64_t)z * A.ny + yy) * A.nx + x;
+  const double theta = coef.theta[level];
+  const double ig = coef.inv_gamma[level];
+  const double mu = level >= 1 ? coef.mu[level - 1] : 0.0;
+  const T* Pl = Y + (int64_t)(2 * level) * ld;
+  const T* Rl = Y + (int64_t)(2 * level + 1) * ld;
+  T* Pn = Y + (int64_t)(2 * level + 2) * ld;
+  T* Rn = Y + (int64_t)(2 * level + 3) * ld;
+  const double ds = __ldg(A.diag + i) - theta;
+  double wp = stencil_apply<DIM3>(A, Pl, i, x, yy, z, ds);
+  if (mu != 0.0) wp = fma(-mu, ld_val(Y + (int64_t)(2 * level - 2) * ld + i), wp);
+  Pn[i] = (T)(wp * ig);
+  if (doR) {
+    double wr = stencil_apply<DIM3>(A, Rl, i, x, yy, z, ds);
+    if (mu != 0.0) wr = fma(-mu, ld_val(Y + (int64_t)(2 * level - 1) * ld + i), wr);
+    Rn[i] = (T)(wr * ig);
+  }
+}
+
 // ---------------------------------------------------- CSR as sliced ELL
 // One warp per slice of 32 rows whose lengths differ little (sorted within
 // windows of 256 rows): on GB300 a binary64 instruction costs its warp the
@@ -242,6 +281,10 @@ __global__ void __launch_bounds__(kOpThreads) sell_mpk_kernel(Operator A, T* __r
 // scheme needs ~60 registers per thread and measured slower than the
 // cell-parallel kernel, which it therefore keeps.)
 constexpr int kZTx = 32, kZTy = 8, kZChunk = 4;
+
+__host__ inline dim3 cell_grid3(const Operator& A) {
+  return dim3((unsigned)((A.nx + 31) / 32), (unsigned)((A.ny + 7) / 8), (unsigned)A.nz);
+}
 
 __host__ inline int sell_grid(const Operator& A) {
   const int64_t warps_per_block = kOpThreads / 32;
@@ -443,16 +486,26 @@ cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level, 
     float* Yf = static_cast<float*>(Y);
     if (A.kind == 0)
       sell_mpk_kernel<float><<<sell_grid(A), kOpThreads, 0, st>>>(A, Yf, ld, level, state, sbar_fixed, coef);
-    else if (A.dim == 3)
+    else if (A.nz > 65535)  // beyond the grid's z extent: grid-stride kernel
       stencil_mpk_kernel<true, float><<<g, kOpThreads, 0, st>>>(A, Yf, ld, level, state, sbar_fixed, coef);
-    else stencil_mpk_kernel<false, float><<<g, kOpThreads, 0, st>>>(A, Yf, ld, level, state, sbar_fixed, coef);
+    else if (A.dim == 3)
+      stencil_mpk_grid_kernel<true, float><<<cell_grid3(A), dim3(32, 8), 0, st>>>(A, Yf, ld, level, state,
+                                                                                 sbar_fixed, coef);
+    else
+      stencil_mpk_grid_kernel<false, float><<<cell_grid3(A), dim3(32, 8), 0, st>>>(A, Yf, ld, level, state,
+                                                                                  sbar_fixed, coef);
   } else {
     double* Yd = static_cast<double*>(Y);
     if (A.kind == 0)
       sell_mpk_kernel<double><<<sell_grid(A), kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);
-    else if (A.dim == 3)
+    else if (A.nz > 65535)  // beyond the grid's z extent: grid-stride kernel
       stencil_mpk_kernel<true, double><<<g, kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);
-    else stencil_mpk_kernel<false, double><<<g, kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);
+    else if (A.dim == 3)
+      stencil_mpk_grid_kernel<true, double><<<cell_grid3(A), dim3(32, 8), 0, st>>>(A, Yd, ld, level, state,
+                                                                                  sbar_fixed, coef);
+    else
+      stencil_mpk_grid_kernel<false, double><<<cell_grid3(A), dim3(32, 8), 0, st>>>(A, Yd, ld, level, state,
+                                                                                   sbar_fixed, coef);
   }
   return cudaGetLastError();
 }
