@@ -64,6 +64,28 @@ L2_BYTES = 129 * 2 ** 20
 L2_FLUSH_BYTES = 256 * 2 ** 20
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
 FP32_PEAK_TINST = 152 * 128 * 2.070e9 / 1e12  # 152 SMs x 128 binary32 lanes/clk x 2070 MHz
+
+
+def _bf16_peak_tflops():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback"
+
+
+BF16_PEAK_TFLOPS, BF16_PEAK_SRC = _bf16_peak_tflops()   # f16 has the same nominal dense rate
+
+
+def dg_tiles(ncols):
+    """m16n8 tiles the gram_mode 2 kernel runs for ncols columns (the
+    diagonal-only last tile row of ncols = 16 m + 1 is summed in binary64)."""
+    mt_n, nt_n = (ncols + 15) // 16, (ncols + 7) // 8
+    rows = mt_n - 1 if ncols % 16 == 1 else mt_n
+    return sum(nt_n - 2 * a for a in range(rows))
+
+
+DG_MMA_FLOP_PER_ROW_TILE = 78 * 16 * 8 * 16 * 2 // 16   # 78 f16 m16n8k16 MMAs per 16 rows and tile
 FF_OPS_PER_PRODUCT = 13                       # binary32 instructions per pair and row (gram_mode 1)
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -85,7 +107,8 @@ def parse_args():
     ap.add_argument("--s-max", type=int, default=0,
                     help="override the workload's s_max (sigma) for studies; 0 keeps the configuration's")
     ap.add_argument("--gram-mode", type=int, default=0,
-                    help="0: binary64 Gram (the method as written); 1: binary32-pair products on the FP32 pipes")
+                    help="0: binary64 Gram (the method as written); 1: binary32-pair products on the FP32 pipes; "
+                         "2: exact 5-bit digit products on the f16 tensor cores")
     return ap.parse_args()
 
 
@@ -551,6 +574,20 @@ def main():
                     "traffic": gram_traffic, "launches": n_gram,
                     "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 is not in "
                                  "MEASURED_PEAKS.json)"}
+    elif args.gram_mode == 2:
+        # digit Gram: executed f16 MMA flops (tiles x 78 MMAs per 16 rows) per
+        # second of the Gram phase (which includes the chunk-exponent pass)
+        dg_flop = sum(n * dg_tiles(2 * h["sbar"] + 1) * DG_MMA_FLOP_PER_ROW_TILE for h in hist)
+        t_solve_gram = t_gram / max(1, len(stats))
+        dg_tf = dg_flop / t_solve_gram / 1e12 if t_solve_gram > 0 else None
+        roofline = {"bound": "tensor", "kernel": "gram_chunk_exp+gram_partial_dg+gram_reduce (G = Y^T Y, "
+                                                  "exact 5-bit digit products on f16 tensor cores)",
+                    "achieved": dg_tf, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": (dg_tf / BF16_PEAK_TFLOPS) if dg_tf else None,
+                    "traffic": gram_traffic, "launches": n_gram,
+                    "gram_fp64_equiv_tflops": gram_tflops,
+                    "peak_note": f"{BF16_PEAK_SRC} bf16 burst {BF16_PEAK_TFLOPS:.0f} TFLOP/s (same nominal dense rate "
+                                 "as f16); mma.sync f16 measured 604 TFLOP/s on this part"}
     else:
         # binary32-pair Gram: 13 binary32 instructions per unique (i <= j) pair and row
         # (one binary64 FMA is 2 flop, so gram_flops / 2 is pairs x rows)
@@ -619,7 +656,9 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "l2": l2_note,
                        "timing": "CUDA events around K solves; per-phase CUDA events inside each solve",
-                       "gram": "binary64 FMA" if args.gram_mode == 0 else "binary32-pair products, binary64 accumulation"},
+                       "gram": {0: "binary64 FMA", 1: "binary32-pair products, binary64 accumulation",
+                                2: "exact 5-bit digit products on f16 tensor cores, exact binary32 sums over "
+                                   "1024 rows, binary64 accumulation"}[args.gram_mode]},
             "converged": ok, "true_relres": max(s.true_relres for s in stats),
             "outer_loops": st0.outer_iters, "inner_iters": st0.inner_iters, "host_syncs": st0.host_syncs,
             "ms_per_outer_loop": ms_per_step / st0.outer_iters,

@@ -80,7 +80,10 @@ typedef struct {
   double kappa_cut;      /* kappa_l = inf when lambda_min(G_l) <= kappa_cut * lambda_max(G_l); default 2^-44 */
   int gram_mode;         /* 0: G by binary64 FMAs (the method as written); 1: binary32-pair products on the
                             FP32 pipes (each within ~2^-46 of Y_i Y_j), compensated binary32 sums over
-                            256-row tiles, binary64 across tiles; default 0 */
+                            256-row tiles, binary64 across tiles; 2: every value written as 12 signed
+                            5-bit digits after a per-4096-row-chunk power-of-two column scale, all digit
+                            products on the f16 tensor cores with exact binary32 sums over 1024 rows,
+                            binary64 across them (error below binary64 FMAs'); default 0 */
   int batch_chunk_rows;  /* sscg_solve_batch only: rows per work chunk of the row kernels (matrix powers,
                             recombination, residual checks); 0 = 2048, else 128..1048576 */
   int batch_gram_rows;   /* sscg_solve_batch only: rows per Gram block; 0 = 2048, else 128..1048576 */
@@ -220,7 +223,7 @@ typedef struct {
  * offset sum_{s' < s} nrhs[s'] n_{s'} + k n_s; x holds the initial guesses on
  * entry and the solutions on exit.  s_max: per-system sigma in
  * [1, SSCG_MAX_S] (e.g. from sscg_autotune).  opts: as for sscg_solve
- * (y_fp32 and gram_mode = 1 are unsupported here: SSCG_ERR_UNSUPPORTED;
+ * (y_fp32 and gram_mode != 0 are unsupported here: SSCG_ERR_UNSUPPORTED;
  * batch_chunk_rows / batch_gram_rows set the tile shapes; use_graph = 0
  * replaces the WHILE node by host polling every check_every outer loops).
  * Returns SSCG_OK if every pair
@@ -294,8 +297,14 @@ int sscg_gram(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, voi
  * forms every product from binary32 pairs on the FP32 pipes (each value split
  * exactly into two 24-bit parts after a per-tile power-of-two column scale,
  * compensated binary32 sums over 256-row tiles, binary64 across tiles), which
- * GB300 executes far faster than binary64 FMAs.  Same arguments and
- * allocation behaviour as sscg_gram otherwise. */
+ * GB300 executes far faster than binary64 FMAs; mode 2 writes every value as
+ * the integer F = round(|y| 2^(1082 - e_c)) (e_c the biased exponent of
+ * column c's largest value in its 4096-row chunk) split into 12 signed 5-bit
+ * digits, forms all digit products (pairs s + t <= 11) on the f16 tensor
+ * cores with exact binary32 sums over 1024 rows, and adds those in binary64;
+ * a column with an Inf or NaN in a chunk gives NaN entries.  Mode 2 also
+ * allocates an integer scratch of 33 entries per 4096 rows.  Same arguments and allocation
+ * behaviour as sscg_gram otherwise; mode outside 0..2: SSCG_ERR_INVALID_ARG. */
 int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, int mode, void* cuda_stream);
 
 /* Same result as sscg_gram, for callers that cannot allocate device memory

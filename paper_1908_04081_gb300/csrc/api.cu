@@ -73,6 +73,7 @@ struct sscg_ctx {
   // solve storage
   int64_t ld = 0;
   DevBuf<double> Y, G, partials, rt, b, x, r, p, q, leja;
+  DevBuf<int> chunk_exp;  // gram_mode 2 scratch
   DevBuf<SolveState> state;
   DevBuf<sscg_outer_record> hist;
   SolveState* host_state = nullptr;  // pinned mirror
@@ -134,6 +135,7 @@ int ensure_solve_buffers(sscg_ctx* h, int sigma, int hist_cap, bool y32 = false)
   const int rb = reduce_blocks(n);
   CK(gram_prepare());
   CK(h->partials.ensure(std::max((size_t)gb * kMaxPairs, (size_t)4 * rb)));
+  CK(h->chunk_exp.ensure((size_t)gram_exp_ints(n)));
   CK(h->rt.ensure(n));
   CK(h->b.ensure(n));
   CK(h->x.ensure(n));
@@ -176,8 +178,8 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
   }
   if ((rc = mark(1))) return rc;
   CK(launch_gram(h->Y.p, h->n, h->ld, nullptr, 0, ds, h->partials.p, gram_blocks(h->n), h->G.p, kMaxCols, y32,
-                 st, h->host_state->gram_mode));
-  count += 2;
+                 st, h->host_state->gram_mode, h->chunk_exp.p));
+  count += h->host_state->gram_mode == 2 ? 3 : 2;
   if ((rc = mark(2))) return rc;
   CK(launch_kappa(h->G.p, kMaxCols, ds, 0, 0.0 /* taken from the state */, ds->kappa, ds->glmin,
                   ds->glmax, sigma, st));
@@ -298,7 +300,7 @@ void fill_state_config(SolveState& s, int sigma, double tol, int basis, const ss
 
 int validate_opts(const sscg_opts& o) {
   if (o.c_mode < 0 || o.c_mode > SSCG_C_CONST) return SSCG_ERR_INVALID_ARG;
-  if (o.gram_mode < 0 || o.gram_mode > 1) return SSCG_ERR_INVALID_ARG;
+  if (o.gram_mode < 0 || o.gram_mode > 2) return SSCG_ERR_INVALID_ARG;
   if (o.batch_chunk_rows != 0 && (o.batch_chunk_rows < 128 || o.batch_chunk_rows > (1 << 20)))
     return SSCG_ERR_INVALID_ARG;
   if (o.batch_gram_rows != 0 && (o.batch_gram_rows < 128 || o.batch_gram_rows > (1 << 20)))
@@ -534,6 +536,7 @@ void sscg_destroy(sscg_t h) {
   h->Y.release();
   h->G.release();
   h->partials.release();
+  h->chunk_exp.release();
   h->rt.release();
   h->b.release();
   h->x.release();
@@ -1379,14 +1382,16 @@ int sscg_gram(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, voi
 }
 
 int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, int mode, void* cuda_stream) {
-  if (!Y || !G || n <= 0 || ldy < n || ncols < 1 || ncols > kMaxCols || mode < 0 || mode > 1)
+  if (!Y || !G || n <= 0 || ldy < n || ncols < 1 || ncols > kMaxCols || mode < 0 || mode > 2)
     return SSCG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int nb = gram_blocks(n);
   CK(gram_prepare());
   DevBuf<double> part;
+  DevBuf<int> cexp;
   CK(part.ensure((size_t)nb * kMaxPairs));
-  CK(launch_gram(Y, n, ldy, nullptr, ncols, nullptr, part.p, nb, G, ncols, false, st, mode));
+  if (mode == 2) CK(cexp.ensure((size_t)gram_exp_ints(n)));
+  CK(launch_gram(Y, n, ldy, nullptr, ncols, nullptr, part.p, nb, G, ncols, false, st, mode, cexp.p));
   CK(cudaStreamSynchronize(st));
   part.release();
   return SSCG_OK;

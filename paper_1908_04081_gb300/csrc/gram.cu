@@ -294,6 +294,374 @@ gram_partial_ff_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
   }
 }
 
+// ------------------------------------------------------------------------
+// Gram on the tensor cores by exact digit products (gram_mode = 2).
+//
+// GB300 runs `mma.sync` f16 with binary32 accumulation at about 600 TFLOP/s
+// against 1.2 TFLOP/s of binary64 FMA, so this variant writes every value of
+// Y as 12 signed 5-bit digits and lets the tensor cores form all digit
+// products, exactly.  Rows are grouped in scale chunks of kDgChunkRows;
+// within a chunk column c has the power-of-two scale of its largest value
+// (biased exponent ce_c, from a pre-pass over Y), and each value becomes the
+// 60-bit integer
+//   F = round(|y| 2^(1082 - ce_c)),  |y| ~ F 2^(ce_c - 1082)
+// (exact when y is within 2^7 of the column's largest value, else rounded at
+// bit 60), F = sum_t d_t 32^(11 - t), d_t in [0, 31], each digit carrying
+// y's sign.  The f16 bit pattern k (0 <= k <= 1023) is the subnormal k 2^-24,
+// so a digit is its own encoding.  For u = s + t <= 11 the tensor cores
+// accumulate H_u = 2^-48 sum_rows sum_{s+t=u} d_s(y_i) d_t(y_j) in binary32;
+// every partial sum is an integer times 2^-48 below 2^24 2^-48 (at most
+// 1024 rows x 12 products x 961), so it is exact.  Every kDgFlushRows rows
+// the block adds
+//   G_ij += 2^(ce_i + ce_j - 2006) sum_{u <= 11} H_u 2^(-5u)
+// in binary64.  The terms dropped (s + t > 11) and the rounding of F are
+// below 2^-53 |y_i y_j| for values near the column's largest, so the result
+// is at least as accurate as binary64 FMAs; a column with an Inf or NaN in a
+// chunk makes its entries NaN.
+//
+// Work layout (warp specialised): eight MMA warps own one 16 x 8 tile
+// (m16n8k16) of the upper triangle of G each, with all 12 accumulators
+// H_0..H_11 of the tile (48 registers).  Per 16-row k-step a warp loads the
+// B fragments of all 12 digit planes once, then for each plane s one A
+// fragment feeding 12 - s MMAs (78 per k-step).  Eight conversion warps fetch
+// the raw values of the stages ahead by cp.async and write their digits; the
+// digits of a 64-row stage sit in shared memory as [plane][8-row block]
+// [column][16 bytes] (one 16-byte ldmatrix row per column and block), double
+// buffered, handed over with named barriers (full: conversion warps arrive,
+// MMA warps wait; empty: the reverse), so conversion overlaps the MMAs.  When ncols = 16 m + 1 (ncols = 17, 33) the last tile row holds
+// only the diagonal entry of the last column; it is summed with binary64
+// FMAs by the threads that convert that column instead, which leaves 2
+// MMA warps per sub-partition at ncols = 33.
+constexpr int kDgPlanes = 12;
+constexpr int kDgStageRows = 64;
+constexpr int kDgKBlocks = kDgStageRows / 8;    // 8-row blocks per stage
+constexpr int kDgChunkRows = 4096;              // scale granularity
+constexpr int kDgChunkShift = 12;
+constexpr int kDgFlushShift = 10;               // exact binary32 sums over 1024 rows
+constexpr int kDgColPad = 48;                   // 3 m-tiles of 16 columns
+constexpr int kDgTileWarps = 8;                 // MMA warps: one per tile (8 tiles at ncols = 33)
+constexpr int kDgConvWarps = 8;                 // conversion warps
+constexpr int kDgWarps = kDgTileWarps + kDgConvWarps;
+constexpr int kDgThreads = kDgWarps * 32;
+constexpr int kDgConvThreads = kDgConvWarps * 32;
+constexpr int kDgTasks = 5;                     // conversion tasks per warp and stage (8 x 5 <= 5 x 8)
+// named barriers (0 is __syncthreads): stage buffer b full / empty, and the
+// conversion warps among themselves
+constexpr int kBarFull = 1, kBarEmpty = 3, kBarConv = 5;
+constexpr int kDgPlaneBytes = kDgKBlocks * kDgColPad * 16;             // 6,144
+constexpr size_t kDgStageBytes = (size_t)kDgPlanes * kDgPlaneBytes;    // 73,728
+constexpr int kDgRawLd = kDgStageRows + 8;      // raw stage row stride (elements): conflict-free pair reads
+template <typename T>
+constexpr size_t dg_raw_bytes() { return (size_t)kMaxCols * kDgRawLd * sizeof(T); }
+template <typename T>
+constexpr size_t dg_smem_bytes() { return 2 * kDgStageBytes + 2 * dg_raw_bytes<T>(); }  // 185,472 for binary64
+static_assert(kDgChunkRows == (1 << kDgChunkShift) && kDgChunkShift >= kDgFlushShift &&
+              (1 << kDgFlushShift) % kDgStageRows == 0, "chunk");
+static_assert(kDgKBlocks * ((kMaxCols + 7) / 8) <= kDgTasks * kDgConvWarps, "conversion tasks cover a stage");
+static_assert(kMaxCols <= 33, "tile layout assumes at most kDgTileWarps tiles");
+
+// biased binary64 exponent of the value, at least 1 (zero and subnormals
+// count as exponent 1: |y| = M 2^(max(E,1) - 1075)); 2047 for Inf/NaN
+__device__ __forceinline__ int dg_exp(double y) {
+  const int E = (int)(((unsigned long long)__double_as_longlong(y) >> 52) & 0x7ff);
+  return E > 1 ? E : 1;
+}
+
+// 60-bit digit integer F of |y| at column exponent ce (see above)
+__device__ __forceinline__ unsigned long long dg_fixed(double y, int ce) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(y);
+  const int E = (int)((bits >> 52) & 0x7ff);
+  if (E == 0x7ff) return 0ull;
+  const unsigned long long M = (bits & ((1ull << 52) - 1)) | (E ? (1ull << 52) : 0ull);
+  const int sh = (E > 1 ? E : 1) - ce + 7;  // <= 7
+  if (sh >= 0) return M << sh;
+  const int r = -sh;
+  if (r > 54) return 0ull;
+  return (M + (1ull << (r - 1))) >> r;
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], unsigned addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(unsigned (&r)[2], unsigned addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(addr));
+}
+__device__ __forceinline__ void mma_f16(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// largest biased exponent (dg_exp) of every column within every chunk of
+// kDgChunkRows rows: cexp[chunk * kMaxCols + column]
+template <typename T>
+__global__ void __launch_bounds__(256)
+gram_chunk_exp_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const SolveState* __restrict__ st,
+                      int ncols_fixed, int* __restrict__ cexp) {
+  int ncols = ncols_fixed;
+  if (ncols <= 0) {
+    if (st->done) return;
+    ncols = 2 * st->sbar + 1;
+  }
+  const int c = blockIdx.y;
+  if (c >= ncols) return;
+  const int64_t r0 = (int64_t)blockIdx.x * kDgChunkRows;
+  const T* col = Y + (int64_t)c * ld;
+  int m = 1;
+#pragma unroll 4
+  for (int k = threadIdx.x; k < kDgChunkRows; k += 256) {
+    const int64_t r = r0 + k;
+    if (r < n) m = max(m, dg_exp(widen(__ldg(col + r))));
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  __shared__ int wm[8];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int v = wm[0];
+    for (int w = 1; w < 8; ++w) v = max(v, wm[w]);
+    cexp[(int64_t)blockIdx.x * kMaxCols + c] = v;
+  }
+}
+
+// Raw stage: the stage's rows of every column copied from global memory by
+// cp.async into [column][kDgRawLd] (zero filled past the block's last row).
+template <typename T>
+__device__ __forceinline__ void dg_issue_raw(T* raw, const T* __restrict__ Y, int64_t ld, int64_t r0, int64_t r_end,
+                                             int ncols, int ct) {
+  const unsigned rbase = (unsigned)__cvta_generic_to_shared(raw);
+  for (int e = ct; e < ncols * kDgStageRows; e += kDgConvThreads) {
+    const int c = e / kDgStageRows, r = e - c * kDgStageRows;
+    const int64_t row = r0 + r;
+    const bool ok = row < r_end;
+    const T* src = Y + (int64_t)c * ld + (ok ? row : 0);
+    const unsigned dst = rbase + (unsigned)((c * kDgRawLd + r) * sizeof(T));
+    if (sizeof(T) == 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Conversion tasks of a stage: (8-row block kb, group of 8 columns cg), task
+// tau = 8 cg + kb; lane -> (column 8 cg + lane / 4, rows 8 kb + 2 (lane % 4)
+// and the next).  Conversion warp cw takes tasks cw + i kDgConvWarps.  Word
+// t of a lane holds digit t of its two rows as two f16 bit patterns.
+template <typename T>
+__device__ __forceinline__ void dg_convert(const T* raw, unsigned char* stage, const int* __restrict__ ce_g,
+                                           int ncols, int cw, bool diag_fp64, double& dg) {
+  constexpr int kPlaneWords = kDgPlaneBytes / 4;
+  const int lane = threadIdx.x & 31;
+  const int c8 = lane >> 2, w4 = lane & 3;
+  const int ntasks = kDgKBlocks * ((ncols + 7) >> 3);
+#pragma unroll 1
+  for (int i = 0; i < kDgTasks; ++i) {
+    const int tau = cw + i * kDgConvWarps;
+    const int kb = tau & 7, c = 8 * (tau >> 3) + c8;
+    if (tau < ntasks && c < ncols) {
+      const T* src = raw + c * kDgRawLd + 8 * kb + 2 * w4;
+      const double v0 = widen(src[0]), v1 = widen(src[1]);
+      if (diag_fp64 && c == ncols - 1) dg = fma(v1, v1, fma(v0, v0, dg));
+      const int ce = __ldg(ce_g + c);
+      const unsigned long long F0 = dg_fixed(v0, ce), F1 = dg_fixed(v1, ce);
+      const unsigned h0 = (unsigned)(F0 >> 32), l0 = (unsigned)F0;
+      const unsigned h1 = (unsigned)(F1 >> 32), l1 = (unsigned)F1;
+      const unsigned sgn = (((unsigned)((unsigned long long)__double_as_longlong(v0) >> 63)) << 15) |
+                           (((unsigned)((unsigned long long)__double_as_longlong(v1) >> 63)) << 31);
+      unsigned* wbase = reinterpret_cast<unsigned*>(stage) + ((kb * kDgColPad + c) * 4 + w4);
+      // digit t sits at bits 55 - 5t .. 59 - 5t of F
+#pragma unroll
+      for (int t = 0; t < 5; ++t)
+        wbase[t * kPlaneWords] = ((h0 >> (23 - 5 * t)) & 31u) | (((h1 >> (23 - 5 * t)) & 31u) << 16) | sgn;
+      wbase[5 * kPlaneWords] =
+          (__funnelshift_r(l0, h0, 30) & 31u) | ((__funnelshift_r(l1, h1, 30) & 31u) << 16) | sgn;
+#pragma unroll
+      for (int t = 6; t < kDgPlanes; ++t)
+        wbase[t * kPlaneWords] = ((l0 >> (55 - 5 * t)) & 31u) | (((l1 >> (55 - 5 * t)) & 31u) << 16) | sgn;
+    }
+  }
+}
+
+// add the digit sums of this lane's four tile entries into gacc (binary64)
+// and clear them
+__device__ __forceinline__ void dg_flush(float (&acc)[kDgPlanes][4], double (&gacc)[4], const int* ce_s, int ncols,
+                                         int m0, int n0, int g, int tig) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int i = m0 + g + (e >> 1) * 8, j = n0 + 2 * tig + (e & 1);
+    if (i < ncols && j < ncols && i <= j) {
+      const int ci = ce_s[i], cj = ce_s[j];
+      double h = 0.0;
+#pragma unroll
+      for (int u = kDgPlanes - 1; u >= 0; --u)
+        h = fma(widen(acc[u][e]), __longlong_as_double((long long)(1023 - 5 * u) << 52), h);
+      const int k = ci + cj - 2006;
+      double& ge = gacc[e];
+      if (ci == 2047 || cj == 2047)
+        ge = __longlong_as_double(0x7ff8000000000000ll);
+      else if (((unsigned long long)__double_as_longlong(h) << 1) == 0ull)
+        ;  // nothing to add (and no 0 x Inf below)
+      else if (k >= -1022 && k <= 1023)
+        ge = fma(h, pow2(k), ge);
+      else if (k > 1023)
+        ge = fma(h * pow2(k - 1023), 0x1p1023, ge);
+      else
+        ge = fma(h * pow2(k + 1022), 0x1p-1022, ge);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kDgPlanes; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
+}
+
+// all digit products of one 64-row stage for this warp's tile
+__device__ __forceinline__ void dg_mma_stage(float (&acc)[kDgPlanes][4], unsigned sbase, unsigned a_off,
+                                             unsigned b_off) {
+#pragma unroll 1
+  for (int ks = 0; ks < kDgKBlocks / 2; ++ks) {
+    const unsigned kofs = (unsigned)(ks * 2 * kDgColPad * 16);
+    unsigned bf[kDgPlanes][2];
+#pragma unroll
+    for (int s = 0; s < kDgPlanes; ++s) ldsm_x2(bf[s], sbase + s * kDgPlaneBytes + kofs + b_off);
+#pragma unroll
+    for (int s = 0; s < kDgPlanes; ++s) {
+      unsigned af[4];
+      ldsm_x4(af, sbase + s * kDgPlaneBytes + kofs + a_off);
+#pragma unroll
+      for (int q = 0; q < kDgPlanes - s; ++q) mma_f16(acc[s + q], af, bf[q]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDgThreads, 1)
+gram_partial_dg_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const SolveState* __restrict__ st,
+                       int ncols_fixed, const int* __restrict__ cexp, double* __restrict__ partials) {
+  int ncols = ncols_fixed;
+  if (ncols <= 0) {
+    if (st->done) return;
+    ncols = 2 * st->sbar + 1;
+  }
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int g = lane >> 2, tig = lane & 3;
+  const bool conv = warp >= kDgTileWarps;
+
+  // tiles (mt, nt) with nt >= 2 mt, in order; the diagonal-only last tile row
+  // (ncols = 16 m + 1) is left to binary64
+  const int MT = (ncols + 15) >> 4, NT = (ncols + 7) >> 3;
+  const bool diag_fp64 = (ncols & 15) == 1;
+  int ntiles = 0, mt = 0, nt = 0;
+  for (int a = 0; a < MT; ++a) {
+    if (diag_fp64 && a == MT - 1) break;
+    for (int b = 2 * a; b < NT; ++b) {
+      if (ntiles == warp) {
+        mt = a;
+        nt = b;
+      }
+      ++ntiles;
+    }
+  }
+  const bool mma_warp = !conv && warp < ntiles;
+  const int m0 = 16 * mt, n0 = 8 * nt;
+
+  extern __shared__ __align__(16) unsigned char dg_smem[];
+  T* raw[2] = {reinterpret_cast<T*>(dg_smem + 2 * kDgStageBytes),
+               reinterpret_cast<T*>(dg_smem + 2 * kDgStageBytes + dg_raw_bytes<T>())};
+  __shared__ int ce_buf[2][kMaxCols];  // exponents of the stage in digit buffer b
+  __shared__ double dred[kDgThreads];
+
+  const int64_t nst_all = (n + kDgStageRows - 1) / kDgStageRows;
+  const int64_t spb = (nst_all + gridDim.x - 1) / gridDim.x;
+  const int64_t r_begin = (int64_t)blockIdx.x * spb * kDgStageRows;
+  int64_t r_end = r_begin + spb * kDgStageRows;
+  if (r_end > n) r_end = n;
+  const int64_t nst = r_begin < r_end ? (r_end - r_begin + kDgStageRows - 1) / kDgStageRows : 0;
+
+  // both digit buffers zero: columns >= ncols are never written again
+  for (int e = t; e < (int)(2 * kDgStageBytes / 16); e += kDgThreads)
+    reinterpret_cast<uint4*>(dg_smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+
+  double dg = 0.0;  // binary64 diagonal entry of the last column (diag_fp64)
+  double gacc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (conv) {
+    // ---- conversion warps: stage k into digit buffer k & 1.  Every stage
+    // commits one cp.async group (possibly empty), so "wait_group 1" means
+    // that raw stage k has landed.
+    const int ct = t - kDgTileWarps * 32, cw = warp - kDgTileWarps;
+    dg_issue_raw(raw[0], Y, ld, r_begin, r_end, ncols, ct);
+    dg_issue_raw(raw[1], Y, ld, r_begin + kDgStageRows, r_end, ncols, ct);
+    for (int64_t k = 0; k < nst; ++k) {
+      const int b = (int)(k & 1);
+      const int64_t r0 = r_begin + k * kDgStageRows;
+      const int* ce_g = cexp + (r0 >> kDgChunkShift) * kMaxCols;
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      bar_sync(kBarConv, kDgConvThreads);                   // raw stage k visible to all conversion warps
+      if (k >= 2) bar_sync(kBarEmpty + b, kDgThreads);      // the MMA warps are done with stage k - 2
+      if (ct < ncols) ce_buf[b][ct] = __ldg(ce_g + ct);
+      dg_convert(raw[b], dg_smem + (size_t)b * kDgStageBytes, ce_g, ncols, cw, diag_fp64, dg);
+      bar_sync(kBarConv, kDgConvThreads);                   // raw stage k fully read
+      dg_issue_raw(raw[b], Y, ld, r0 + 2 * kDgStageRows, r_end, ncols, ct);
+      bar_arrive(kBarFull + b, kDgThreads);                 // digit buffer b holds stage k
+    }
+    // the empty signals of the last two stages
+    for (int64_t k = nst > 2 ? nst - 2 : 0; k < nst; ++k) bar_sync(kBarEmpty + (int)(k & 1), kDgThreads);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else {
+    // ---- MMA warps
+    const unsigned smem0 = (unsigned)__cvta_generic_to_shared(dg_smem);
+    // per-lane ldmatrix row offsets within a plane (k-step 0): x4 matrices
+    // (m0..+7, kb0), (m0+8..+15, kb0), (m0..+7, kb0+1), (m0+8..+15, kb0+1);
+    // x2 matrices (n0..+7, kb0), (n0..+7, kb0+1)
+    const unsigned a_off = (unsigned)(((lane >> 4) * kDgColPad + m0 + ((lane >> 3) & 1) * 8 + (lane & 7)) * 16);
+    const unsigned b_off = (unsigned)((((lane >> 3) & 1) * kDgColPad + n0 + (lane & 7)) * 16);
+    float acc[kDgPlanes][4];
+#pragma unroll
+    for (int u = 0; u < kDgPlanes; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
+    for (int64_t k = 0; k < nst; ++k) {
+      const int b = (int)(k & 1);
+      const int64_t r0 = r_begin + k * kDgStageRows, r1 = r0 + kDgStageRows;
+      bar_sync(kBarFull + b, kDgThreads);
+      if (mma_warp) {
+        dg_mma_stage(acc, smem0 + (unsigned)(b * kDgStageBytes), a_off, b_off);
+        // exact binary32 sums end at every 1024-row boundary and at the end
+        if (k + 1 == nst || (r1 >> kDgFlushShift) != (r0 >> kDgFlushShift))
+          dg_flush(acc, gacc, ce_buf[b], ncols, m0, n0, g, tig);
+      }
+      bar_arrive(kBarEmpty + b, kDgThreads);
+    }
+  }
+  __syncthreads();
+
+  // binary64 diagonal entry of the last column: fixed-order sum over threads
+  if (diag_fp64) {
+    dred[t] = dg;
+    __syncthreads();
+    if (t == 0) {
+      double s = 0.0;
+      for (int k = 0; k < kDgThreads; ++k) s += dred[k];
+      const int i = ncols - 1;
+      partials[(int64_t)blockIdx.x * kMaxPairs + i * ncols - i * (i - 1) / 2] = s;
+    }
+  }
+  if (mma_warp) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int i = m0 + g + (e >> 1) * 8, j = n0 + 2 * tig + (e & 1);
+      if (i < ncols && j < ncols && i <= j)
+        partials[(int64_t)blockIdx.x * kMaxPairs + i * ncols - i * (i - 1) / 2 + (j - i)] = gacc[e];
+    }
+  }
+}
+
 // One warp per pair: fixed-order sum of the per-block partials.
 __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restrict__ partials, int nblocks,
                                                           const SolveState* __restrict__ st, int ncols_fixed,
@@ -422,14 +790,44 @@ cudaError_t gram_prepare() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(gram_partial_ff_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFFSmem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gram_partial_dg_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)dg_smem_bytes<double>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gram_partial_dg_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)dg_smem_bytes<float>());
+  if (e != cudaSuccess) return e;
   done[dev] = true;
   return cudaSuccess;
 }
 
+int64_t gram_exp_ints(int64_t n) { return ((n + kDgChunkRows - 1) / kDgChunkRows) * kMaxCols; }
+
 cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* /*ncols_dev*/, int ncols_fixed,
                         const SolveState* state, double* partials, int nblocks, double* G, int ldg, bool y32,
-                        cudaStream_t st, int gram_mode) {
-  if (gram_mode == 1) {
+                        cudaStream_t st, int gram_mode, int* chunk_exp) {
+  if (gram_mode == 2) {
+    if (!chunk_exp) return cudaErrorInvalidValue;
+    const int64_t nchunks = (n + kDgChunkRows - 1) / kDgChunkRows;
+    if (nchunks > 0x7fffffff) return cudaErrorInvalidValue;
+    const dim3 egrid((unsigned)nchunks, ncols_fixed > 0 ? ncols_fixed : kMaxCols);
+    // one block per SM, at most one block per 64-row stage
+    const int64_t nstages = (n + kDgStageRows - 1) / kDgStageRows;
+    int nb = nblocks < 152 ? nblocks : 152;
+    if (nstages < nb) nb = (int)nstages;
+    if (nb < 1) nb = 1;
+    nblocks = nb;
+    if (y32) {
+      gram_chunk_exp_kernel<float><<<egrid, 256, 0, st>>>(static_cast<const float*>(Y), n, ld, state, ncols_fixed,
+                                                          chunk_exp);
+      gram_partial_dg_kernel<float><<<nblocks, kDgThreads, dg_smem_bytes<float>(), st>>>(
+          static_cast<const float*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials);
+    } else {
+      gram_chunk_exp_kernel<double><<<egrid, 256, 0, st>>>(static_cast<const double*>(Y), n, ld, state,
+                                                           ncols_fixed, chunk_exp);
+      gram_partial_dg_kernel<double><<<nblocks, kDgThreads, dg_smem_bytes<double>(), st>>>(
+          static_cast<const double*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials);
+    }
+  } else if (gram_mode == 1) {
     // one block per SM, at most one block per 256-row tile
     const int64_t ntiles = (n + kFFRows - 1) / kFFRows;
     int nb = nblocks < 152 ? nblocks : 152;

@@ -93,7 +93,7 @@ struct SolveState {
   // FP32-stored basis: periodic residual replacement (r := b - A x, p kept)
   double fp32_drop, rho_last;
   double prev_fail;   // relative true residual at the last failed convergence check
-  int gram_mode;      // 0: binary64 Gram; 1: binary32-pair products
+  int gram_mode;      // 0: binary64 Gram; 1: binary32-pair products; 2: f16 digit products
   int fp32_replace_pending, fp32_replacements;
   double c, psi, normb, upd_relres;
   // Meurant-Tichy state (Algs. 3-4)
@@ -142,10 +142,14 @@ int gram_blocks(int64_t n);
 // above the 48 KB default); call outside stream capture, before launch_gram
 cudaError_t gram_prepare();
 // gram_mode 0: binary64 products and sums; 1: binary32-pair products on the
-// FP32 pipes, compensated binary32 sums per tile, binary64 across tiles.
+// FP32 pipes, compensated binary32 sums per tile, binary64 across tiles;
+// 2: exact products of 5-bit digits on the f16 tensor cores, exact binary32
+// sums over 1024 rows, binary64 across them (needs `chunk_exp`, an int
+// scratch of gram_exp_ints(n) entries).
+int64_t gram_exp_ints(int64_t n);
 cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* ncols_dev, int ncols_fixed,
                         const SolveState* state, double* partials, int nblocks, double* G, int ldg,
-                        bool y32, cudaStream_t st, int gram_mode = 0);
+                        bool y32, cudaStream_t st, int gram_mode = 0, int* chunk_exp = nullptr);
 
 // control.cu
 cudaError_t launch_kappa(const double* G, int ldg, const SolveState* state, int sbar_fixed,

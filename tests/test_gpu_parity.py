@@ -556,12 +556,16 @@ def test_failure_detection_injected_on_the_host(pkg):
     assert st4.status == 0 and st4.true_relres <= 1e-10
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("n,ncols", [(1, 1), (2, 2), (777, 5), (513, 4), (10007, 33), (70001, 17),
-                                     (300000, 33), (1000003, 9)])
-def test_gram_binary32_pair_mode(pkg, n, ncols):
-    """gram_mode 1 against binary64: each term carries at most ~2^-46 relative
-    error, so G agrees to 1e-13 relative to sqrt(G_ii G_jj), including columns
-    whose scales differ by 10^8 and a column of exact zeros."""
+                                     (300000, 33), (1000003, 9), (8193, 3), (4095, 32), (12289, 31)])
+def test_gram_fast_modes(pkg, n, ncols, mode):
+    """gram_mode 1 and 2 against binary64: mode 1 carries at most ~2^-46
+    relative error per term, mode 2 at most ~2^-53 of the product of the
+    chunk's largest values, so G agrees to 1e-13 relative to sqrt(G_ii G_jj),
+    including columns whose scales differ by 10^8, a column of exact zeros,
+    row counts that end inside a 64-row stage, a 1024-row exact-sum block and
+    a 4096-row scale chunk, and every tile shape (1 to 33 columns)."""
     rng = np.random.default_rng(n + 7 * ncols)
     Y = rng.standard_normal((n, ncols)) * np.logspace(-4, 4, ncols)[None, :]
     if ncols > 2:
@@ -570,7 +574,7 @@ def test_gram_binary32_pair_mode(pkg, n, ncols):
     Yd = torch.zeros(ld * ncols, dtype=torch.float64, device="cuda")
     Yd.reshape(ncols, ld)[:, :n] = dev(Y.T)
     G1 = torch.zeros(ncols * ncols, dtype=torch.float64, device="cuda")
-    pkg.sscg.sscg_gram_ex(Yd, n, ld, ncols, G1, 1)
+    pkg.sscg.sscg_gram_ex(Yd, n, ld, ncols, G1, mode)
     Gg = G1.reshape(ncols, ncols).cpu().numpy()
     Go = Y.T @ Y
     d = np.sqrt(np.outer(np.diag(Go), np.diag(Go)))
@@ -579,10 +583,46 @@ def test_gram_binary32_pair_mode(pkg, n, ncols):
     assert np.array_equal(Gg, Gg.T)
 
 
-def test_gram_binary32_pair_nonfinite(pkg):
+@pytest.mark.parametrize("n,ncols", [(10007, 33), (70001, 17), (5000, 6)])
+def test_gram_fp8_digits_exact_on_integers(pkg, n, ncols):
+    """gram_mode 2 is exact where the products and sums are: integer entries
+    below 2^16 have every digit exact, every 1024-row sum below 2^24 x 2^-48
+    is exact in binary32 and the binary64 combination stays below 2^53, so G
+    equals the integer Gram bit for bit (columns of very different sizes, so
+    that the digits fall in different planes)."""
+    rng = np.random.default_rng(n)
+    bits = rng.integers(1, 17, ncols)
+    Yi = np.stack([rng.integers(-(2 ** int(k)) + 1, 2 ** int(k), n) for k in bits], axis=1).astype(np.int64)
+    Gi = Yi.T @ Yi  # exact in int64
+    Yd = dev(np.ascontiguousarray(Yi.T.astype(np.float64)).ravel())
+    G1 = torch.zeros(ncols * ncols, dtype=torch.float64, device="cuda")
+    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G1, 2)
+    Gg = G1.reshape(ncols, ncols).cpu().numpy()
+    assert np.array_equal(Gg, Gi.astype(np.float64))
+
+
+def test_gram_fp8_digits_wide_exponents(pkg):
+    """gram_mode 2 with values spread over 2^-60 .. 2^60 inside one column and
+    chunk: entries far below the chunk's largest value lose their low bits,
+    which the normwise bound absorbs (each row's error is below 2^-60 times
+    the product of the two column maxima)."""
+    n, ncols = 20000, 9
+    rng = np.random.default_rng(11)
+    Y = rng.standard_normal((n, ncols)) * np.exp2(rng.integers(-60, 61, (n, ncols)))
+    Yd = dev(np.ascontiguousarray(Y.T).ravel())
+    G1 = torch.zeros(ncols * ncols, dtype=torch.float64, device="cuda")
+    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G1, 2)
+    Gg = G1.reshape(ncols, ncols).cpu().numpy()
+    Go = Y.T @ Y
+    d = np.sqrt(np.outer(np.diag(Go), np.diag(Go)))
+    assert np.max(np.abs(Gg - Go) / d) <= 1e-13
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_gram_fast_modes_nonfinite(pkg, mode):
     """A NaN or Inf in Y reaches the entries of G that it touches in
-    gram_mode 1, as it does in binary64 (the solver's non-finite check relies
-    on it)."""
+    gram_mode 1 and 2, as it does in binary64 (the solver's non-finite check
+    relies on it)."""
     n, ncols = 5000, 7
     rng = np.random.default_rng(3)
     Y = rng.standard_normal((n, ncols))
@@ -590,7 +630,7 @@ def test_gram_binary32_pair_nonfinite(pkg):
     Y[4321, 5] = np.nan
     Yd = dev(np.ascontiguousarray(Y.T).ravel())
     G1 = torch.zeros(ncols * ncols, dtype=torch.float64, device="cuda")
-    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G1, 1)
+    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G1, mode)
     Gg = G1.reshape(ncols, ncols).cpu().numpy()
     for j in range(ncols):
         assert not np.isfinite(Gg[2, j]) and not np.isfinite(Gg[5, j])
@@ -598,8 +638,9 @@ def test_gram_binary32_pair_nonfinite(pkg):
     assert np.all(np.isfinite(Gg[np.ix_(keep, keep)]))
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("name", ["poisson", "varcoef3d", "varcoef3d_y32"])
-def test_solve_with_binary32_pair_gram(pkg, name):
+def test_solve_with_fast_gram(pkg, name, mode):
     if name == "poisson":
         A, b, x0, _ = gen.config_problem("poisson2d_64")
         M = as_matrix(A)
@@ -615,6 +656,6 @@ def test_solve_with_binary32_pair_gram(pkg, name):
     y32 = name.endswith("_y32")
     x_o, info = cg.sstep_cg(M, b, x0, 1e-10, cg.Options(smax=smax, basis=basis, y_fp32=y32))
     xt = dev(x0)
-    st = s.solve(dev(b), xt, tol=1e-10, s_max=smax, basis=basis, hist_cap=4000, gram_mode=1,
+    st = s.solve(dev(b), xt, tol=1e-10, s_max=smax, basis=basis, hist_cap=4000, gram_mode=mode,
                  y_fp32=int(y32))
     compare_solves(xt.cpu().numpy(), st, pkg.sscg.history(st), x_o, info, 1e-10, strict=(name == "poisson"))
