@@ -344,20 +344,23 @@ constexpr int kDgConvWarps = 8;                 // conversion warps
 constexpr int kDgWarps = kDgTileWarps + kDgConvWarps;
 constexpr int kDgThreads = kDgWarps * 32;
 constexpr int kDgConvThreads = kDgConvWarps * 32;
-constexpr int kDgTasks = 5;                     // conversion tasks per warp and stage (8 x 5 <= 5 x 8)
 // named barriers (0 is __syncthreads): stage buffer b full / empty, and the
 // conversion warps among themselves
 constexpr int kBarFull = 1, kBarEmpty = 3, kBarConv = 5;
 constexpr int kDgPlaneBytes = kDgKBlocks * kDgColPad * 16;             // 6,144
 constexpr size_t kDgStageBytes = (size_t)kDgPlanes * kDgPlaneBytes;    // 73,728
-constexpr int kDgRawLd = kDgStageRows + 8;      // raw stage row stride (elements): conflict-free pair reads
+// raw stage row stride (elements): odd, so that the reads of 8 consecutive
+// columns by one phase of lanes fall in distinct banks
 template <typename T>
-constexpr size_t dg_raw_bytes() { return (size_t)kMaxCols * kDgRawLd * sizeof(T); }
+constexpr int dg_raw_ld() { return kDgStageRows + 1; }
+template <typename T>
+constexpr size_t dg_raw_bytes() { return (size_t)kMaxCols * dg_raw_ld<T>() * sizeof(T); }
 template <typename T>
 constexpr size_t dg_smem_bytes() { return 2 * kDgStageBytes + 2 * dg_raw_bytes<T>(); }  // 185,472 for binary64
 static_assert(kDgChunkRows == (1 << kDgChunkShift) && kDgChunkShift >= kDgFlushShift &&
               (1 << kDgFlushShift) % kDgStageRows == 0, "chunk");
-static_assert(kDgKBlocks * ((kMaxCols + 7) / 8) <= kDgTasks * kDgConvWarps, "conversion tasks cover a stage");
+static_assert(kDgConvThreads == 32 * kDgKBlocks && kDgConvWarps == kDgKBlocks && kMaxCols <= 33,
+              "conversion: one thread per (column < 32, 8-row block), column 32 split over the warps");
 static_assert(kMaxCols <= 33, "tile layout assumes at most kDgTileWarps tiles");
 
 // biased binary64 exponent of the value, at least 1 (zero and subnormals
@@ -426,7 +429,7 @@ gram_chunk_exp_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Solv
 }
 
 // Raw stage: the stage's rows of every column copied from global memory by
-// cp.async into [column][kDgRawLd] (zero filled past the block's last row).
+// cp.async into [column][dg_raw_ld] (zero filled past the block's last row).
 template <typename T>
 __device__ __forceinline__ void dg_issue_raw(T* raw, const T* __restrict__ Y, int64_t ld, int64_t r0, int64_t r_end,
                                              int ncols, int ct) {
@@ -436,7 +439,7 @@ __device__ __forceinline__ void dg_issue_raw(T* raw, const T* __restrict__ Y, in
     const int64_t row = r0 + r;
     const bool ok = row < r_end;
     const T* src = Y + (int64_t)c * ld + (ok ? row : 0);
-    const unsigned dst = rbase + (unsigned)((c * kDgRawLd + r) * sizeof(T));
+    const unsigned dst = rbase + (unsigned)((c * dg_raw_ld<T>() + r) * sizeof(T));
     if (sizeof(T) == 8)
       asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
     else
@@ -452,42 +455,88 @@ __device__ __forceinline__ void bar_arrive(int id, int count) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// Conversion tasks of a stage: (8-row block kb, group of 8 columns cg), task
-// tau = 8 cg + kb; lane -> (column 8 cg + lane / 4, rows 8 kb + 2 (lane % 4)
-// and the next).  Conversion warp cw takes tasks cw + i kDgConvWarps.  Word
-// t of a lane holds digit t of its two rows as two f16 bit patterns.
+// digit t (0 = most significant) of the 60-bit F = (h << 32) | l: bits
+// 55 - 5t .. 59 - 5t
+template <int t>
+__device__ __forceinline__ unsigned dg_digit(unsigned h, unsigned l) {
+  if constexpr (t < 5)
+    return (h >> (23 - 5 * t)) & 31u;
+  else if constexpr (t == 5)
+    return __funnelshift_r(l, h, 30) & 31u;
+  else
+    return (l >> (55 - 5 * t)) & 31u;
+}
+
+// digits of 8 consecutive rows of one column (one 8-row block kb): plane t
+// gets the 16-byte ldmatrix row (two f16 bit patterns per word, row 2w in
+// the low half of word w)
+__device__ __forceinline__ void dg_store8(const double (&v)[8], int ce, unsigned char* stage, int kb, int c) {
+  unsigned h[8], l[8], sg[4];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const unsigned long long F = dg_fixed(v[k], ce);
+    h[k] = (unsigned)(F >> 32);
+    l[k] = (unsigned)F;
+  }
+#pragma unroll
+  for (int w = 0; w < 4; ++w)
+    sg[w] = (((unsigned)((unsigned long long)__double_as_longlong(v[2 * w]) >> 63)) << 15) |
+            (((unsigned)((unsigned long long)__double_as_longlong(v[2 * w + 1]) >> 63)) << 31);
+  unsigned char* row = stage + (kb * kDgColPad + c) * 16;
+#define DG_PLANE(t)                                                                                      \
+  *reinterpret_cast<uint4*>(row + (t) * kDgPlaneBytes) =                                                 \
+      make_uint4(dg_digit<t>(h[0], l[0]) | (dg_digit<t>(h[1], l[1]) << 16) | sg[0],                      \
+                 dg_digit<t>(h[2], l[2]) | (dg_digit<t>(h[3], l[3]) << 16) | sg[1],                      \
+                 dg_digit<t>(h[4], l[4]) | (dg_digit<t>(h[5], l[5]) << 16) | sg[2],                      \
+                 dg_digit<t>(h[6], l[6]) | (dg_digit<t>(h[7], l[7]) << 16) | sg[3]);
+  DG_PLANE(0) DG_PLANE(1) DG_PLANE(2) DG_PLANE(3) DG_PLANE(4) DG_PLANE(5)
+  DG_PLANE(6) DG_PLANE(7) DG_PLANE(8) DG_PLANE(9) DG_PLANE(10) DG_PLANE(11)
+#undef DG_PLANE
+}
+
+// digits of 2 consecutive rows (2 w4, 2 w4 + 1 of block kb) of one column:
+// word w4 of every plane's ldmatrix row
+__device__ __forceinline__ void dg_store2(double v0, double v1, int ce, unsigned char* stage, int kb, int c, int w4) {
+  const unsigned long long F0 = dg_fixed(v0, ce), F1 = dg_fixed(v1, ce);
+  const unsigned h0 = (unsigned)(F0 >> 32), l0 = (unsigned)F0;
+  const unsigned h1 = (unsigned)(F1 >> 32), l1 = (unsigned)F1;
+  const unsigned sgn = (((unsigned)((unsigned long long)__double_as_longlong(v0) >> 63)) << 15) |
+                       (((unsigned)((unsigned long long)__double_as_longlong(v1) >> 63)) << 31);
+  unsigned* wb = reinterpret_cast<unsigned*>(stage + (kb * kDgColPad + c) * 16) + w4;
+  constexpr int kPW = kDgPlaneBytes / 4;
+#define DG_WORD(t) wb[(t) * kPW] = dg_digit<t>(h0, l0) | (dg_digit<t>(h1, l1) << 16) | sgn;
+  DG_WORD(0) DG_WORD(1) DG_WORD(2) DG_WORD(3) DG_WORD(4) DG_WORD(5)
+  DG_WORD(6) DG_WORD(7) DG_WORD(8) DG_WORD(9) DG_WORD(10) DG_WORD(11)
+#undef DG_WORD
+}
+
+// Conversion of one stage by the conversion threads ct = 0..255: thread
+// (warp cw, lane) takes column 8 (cw % 4) + lane % 8 and 8-row block
+// 4 (cw / 4) + lane / 8 (8 consecutive columns per 8-lane phase: the 16-byte
+// shared stores do not conflict); column 32 (ncols = 33) is split over the
+// warps, warp cw taking its block cw with lanes 0..3 (two rows each).
 template <typename T>
 __device__ __forceinline__ void dg_convert(const T* raw, unsigned char* stage, const int* __restrict__ ce_g,
                                            int ncols, int cw, bool diag_fp64, double& dg) {
-  constexpr int kPlaneWords = kDgPlaneBytes / 4;
+  constexpr int LD = dg_raw_ld<T>();
   const int lane = threadIdx.x & 31;
-  const int c8 = lane >> 2, w4 = lane & 3;
-  const int ntasks = kDgKBlocks * ((ncols + 7) >> 3);
-#pragma unroll 1
-  for (int i = 0; i < kDgTasks; ++i) {
-    const int tau = cw + i * kDgConvWarps;
-    const int kb = tau & 7, c = 8 * (tau >> 3) + c8;
-    if (tau < ntasks && c < ncols) {
-      const T* src = raw + c * kDgRawLd + 8 * kb + 2 * w4;
-      const double v0 = widen(src[0]), v1 = widen(src[1]);
-      if (diag_fp64 && c == ncols - 1) dg = fma(v1, v1, fma(v0, v0, dg));
-      const int ce = __ldg(ce_g + c);
-      const unsigned long long F0 = dg_fixed(v0, ce), F1 = dg_fixed(v1, ce);
-      const unsigned h0 = (unsigned)(F0 >> 32), l0 = (unsigned)F0;
-      const unsigned h1 = (unsigned)(F1 >> 32), l1 = (unsigned)F1;
-      const unsigned sgn = (((unsigned)((unsigned long long)__double_as_longlong(v0) >> 63)) << 15) |
-                           (((unsigned)((unsigned long long)__double_as_longlong(v1) >> 63)) << 31);
-      unsigned* wbase = reinterpret_cast<unsigned*>(stage) + ((kb * kDgColPad + c) * 4 + w4);
-      // digit t sits at bits 55 - 5t .. 59 - 5t of F
+  const int c = 8 * (cw & 3) + (lane & 7), kb = 4 * (cw >> 2) + (lane >> 3);
+  if (c < ncols) {
+    const T* src = raw + c * LD + 8 * kb;
+    double v[8];
 #pragma unroll
-      for (int t = 0; t < 5; ++t)
-        wbase[t * kPlaneWords] = ((h0 >> (23 - 5 * t)) & 31u) | (((h1 >> (23 - 5 * t)) & 31u) << 16) | sgn;
-      wbase[5 * kPlaneWords] =
-          (__funnelshift_r(l0, h0, 30) & 31u) | ((__funnelshift_r(l1, h1, 30) & 31u) << 16) | sgn;
+    for (int k = 0; k < 8; ++k) v[k] = widen(src[k]);
+    if (diag_fp64 && c == ncols - 1) {
 #pragma unroll
-      for (int t = 6; t < kDgPlanes; ++t)
-        wbase[t * kPlaneWords] = ((l0 >> (55 - 5 * t)) & 31u) | (((l1 >> (55 - 5 * t)) & 31u) << 16) | sgn;
+      for (int k = 0; k < 8; ++k) dg = fma(v[k], v[k], dg);
     }
+    dg_store8(v, __ldg(ce_g + c), stage, kb, c);
+  }
+  if (ncols > 32 && lane < 4) {
+    const T* src = raw + 32 * LD + 8 * cw + 2 * lane;
+    const double v0 = widen(src[0]), v1 = widen(src[1]);
+    if (diag_fp64) dg = fma(v1, v1, fma(v0, v0, dg));
+    dg_store2(v0, v1, __ldg(ce_g + 32), stage, cw, 32, lane);
   }
 }
 
