@@ -558,14 +558,16 @@ def test_failure_detection_injected_on_the_host(pkg):
 
 @pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("n,ncols", [(1, 1), (2, 2), (777, 5), (513, 4), (10007, 33), (70001, 17),
-                                     (300000, 33), (1000003, 9), (8193, 3), (4095, 32), (12289, 31)])
+                                     (300000, 33), (1000003, 9), (8193, 3), (4095, 32), (12289, 31),
+                                     (155000, 33)])
 def test_gram_fast_modes(pkg, n, ncols, mode):
     """gram_mode 1 and 2 against binary64: mode 1 carries at most ~2^-46
     relative error per term, mode 2 at most ~2^-53 of the product of the
     chunk's largest values, so G agrees to 1e-13 relative to sqrt(G_ii G_jj),
     including columns whose scales differ by 10^8, a column of exact zeros,
     row counts that end inside a 64-row stage, a 1024-row exact-sum block and
-    a 4096-row scale chunk, and every tile shape (1 to 33 columns)."""
+    a 4096-row scale chunk, thread blocks whose row ranges start inside those,
+    and every tile shape (1 to 33 columns)."""
     rng = np.random.default_rng(n + 7 * ncols)
     Y = rng.standard_normal((n, ncols)) * np.logspace(-4, 4, ncols)[None, :]
     if ncols > 2:
