@@ -87,6 +87,14 @@ def dg_tiles(ncols):
 
 DG_MMA_FLOP_PER_ROW_TILE = 78 * 16 * 8 * 16 * 2 // 16   # 78 f16 m16n8k16 MMAs per 16 rows and tile
 FF_OPS_PER_PRODUCT = 13                       # binary32 instructions per pair and row (gram_mode 1)
+# binary64 lane operations per cell of one 3D matrix-powers level (both chains,
+# stencil_mpk_grid_kernel): 17 (Newton and monomial, mu = 0), 19 (Chebyshev)
+MPK_FP64_OPS_PER_CELL = {"newton": 17, "monomial": 17, "chebyshev": 19}
+FP64_PEAK_TOPS = 152 * 4 * 32 / 64 * 2.070e9 / 1e12   # binary64 lane ops/s: 4 sub-partitions x 32 lanes / 64 cycles
+# DRAM bytes per cell and level of stencil_mpk_grid_kernel (read + write),
+# from the one-pass ncu capture of two levels of the 160^3 case
+# (profiles/stencil_mpk_varcoef3d_160.md): 243.1 MB per launch / 4,096,000
+MPK_DRAM_BYTES_PER_CELL = 59.36
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -106,7 +114,7 @@ def parse_args():
     ap.add_argument("--max-outer", type=int, default=0, help="cap outer loops (profiling runs only)")
     ap.add_argument("--s-max", type=int, default=0,
                     help="override the workload's s_max (sigma) for studies; 0 keeps the configuration's")
-    ap.add_argument("--gram-mode", type=int, default=0,
+    ap.add_argument("--gram-mode", type=int, default=2,
                     help="0: binary64 Gram (the method as written); 1: binary32-pair products on the FP32 pipes; "
                          "2: exact 5-bit digit products on the f16 tensor cores")
     return ap.parse_args()
@@ -547,7 +555,9 @@ def main():
     ok = all(s.status == 0 and s.true_relres <= cfg["tol"] for s in stats)
     ms_per_step = elapsed / args.steps * 1e3
 
-    # roofline of the dominant kernel (the Gram contraction: FP64 ALU bound)
+    # rooflines of the Gram (tensor cores in gram_mode 2, else the FP64 or
+    # FP32 pipes) and of the matrix powers (FP64 issue); the slower phase's
+    # kernel is the one reported
     t_gram = sum(s.t_gram_ms for s in stats) / 1e3
     f_gram = sum(s.gram_flops for s in stats)
     n_gram = sum(s.n_gram_launches for s in stats)
@@ -567,6 +577,22 @@ def main():
     if hist and hasattr(op, "kx"):
         gram_traffic = sum(8.0 * n * (2 * h["sbar"] + 1) + 3.4e6 for h in hist) / len(hist)
     launches = sum(s.kernel_launches for s in stats)
+    # the matrix-powers phase: binary64 issue bound (stencil workloads)
+    mpk_roof = None
+    if hasattr(op, "kx") and op.kz is not None and phase_ms["mpk"] > 0:
+        ops = MPK_FP64_OPS_PER_CELL.get(cfg["basis"], 17)
+        # s-bar levels per outer loop; the last one advances the P chain only
+        lane_ops = sum(n * ops * (h["sbar"] - 0.5) for h in hist)
+        levels = sum(h["sbar"] for h in hist)
+        mpk_tops = lane_ops / (phase_ms["mpk"] / 1e3) / 1e12
+        mpk_roof = {"bound": "alu", "kernel": "stencil_mpk_grid_kernel (one matrix-powers level, both chains)",
+                    "achieved": mpk_tops, "peak": FP64_PEAK_TOPS, "unit": "T binary64 lane-ops/s",
+                    "frac": mpk_tops / FP64_PEAK_TOPS,
+                    "traffic": (MPK_DRAM_BYTES_PER_CELL * n) if MPK_DRAM_BYTES_PER_CELL else None,
+                    "launches": levels,
+                    "algorithmic": f"{ops} binary64 lane operations per cell and level",
+                    "peak_note": "derived: 152 SMs x 4 sub-partitions x 32 lanes per 64 cycles x 2070 MHz "
+                                 "(one binary64 instruction holds its sub-partition's unit 64 cycles)"}
     if args.gram_mode == 0:
         roofline = {"bound": "alu", "kernel": "gram_partial+gram_reduce (G = Y^T Y, FP64)",
                     "achieved": gram_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -598,6 +624,12 @@ def main():
                     "traffic": gram_traffic, "launches": n_gram,
                     "gram_fp64_equiv_tflops": gram_tflops,
                     "peak_note": "derived: 152 SMs x 128 binary32 lanes/clk x 2070 MHz"}
+    # report the dominant phase's kernel; the other one beside it
+    gram_roof = roofline
+    if mpk_roof is not None and phase_ms["mpk"] > phase_ms["gram"]:
+        roofline = dict(mpk_roof, secondary=gram_roof)
+    elif mpk_roof is not None:
+        roofline = dict(gram_roof, secondary=mpk_roof)
 
     # ---- HSCG on the same GPU
     hs = []

@@ -434,9 +434,11 @@ def test_not_converged_cap(pkg):
     assert st.status == 3 and st.outer_iters == 3
 
 
-def test_full_size_varcoef3d_160(pkg):
+@pytest.mark.parametrize("gram_mode", [2, 0])
+def test_full_size_varcoef3d_160(pkg, gram_mode):
     """The benchmark workload at full size (N = 4,096,000) in the benchmark's
-    launch configuration: converged to tol by an independent residual (the
+    launch configuration (the tensor-core digit Gram, gram_mode 2) and with
+    the binary64 Gram: converged to tol by an independent residual (the
     oracle's sparse matrix), counts within 10 % of the oracle's full solve, and
     the first outer loops identical to the oracle's."""
     import json
@@ -445,7 +447,7 @@ def test_full_size_varcoef3d_160(pkg):
     A = as_matrix(op)
     s = stencil_solver(pkg, op)
     xt = dev(x0)
-    st = s.solve(dev(b), xt, tol=1e-10, s_max=16, basis="newton", hist_cap=20000, profile=1)
+    st = s.solve(dev(b), xt, tol=1e-10, s_max=16, basis="newton", hist_cap=20000, profile=1, gram_mode=gram_mode)
     assert st.status == 0
     x = xt.cpu().numpy()
     relres = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
