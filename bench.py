@@ -254,7 +254,8 @@ def run_rgg(args, cfg, pkg, torch, dev):
         x = torch.zeros(n, dtype=torch.float64, device=dev)
         for _ in range(args.warmup):
             x.zero_()
-            solver.solve(b, x, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], y_fp32=y32)
+            solver.solve(b, x, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], y_fp32=y32,
+                         gram_mode=args.gram_mode)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
@@ -262,7 +263,7 @@ def run_rgg(args, cfg, pkg, torch, dev):
         for _ in range(args.steps):
             x.zero_()
             sts.append(solver.solve(b, x, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], y_fp32=y32,
-                                    hist_cap=20000))
+                                    hist_cap=20000, gram_mode=args.gram_mode))
         e1.record()
         torch.cuda.synchronize()
         el = e0.elapsed_time(e1) / 1e3
@@ -270,7 +271,8 @@ def run_rgg(args, cfg, pkg, torch, dev):
         h = pkg.sscg.history(st)
         # one more solve, untimed, with direct launches and per-phase events
         xp = torch.zeros(n, dtype=torch.float64, device=dev)
-        sp = solver.solve(b, xp, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], y_fp32=y32, profile=1)
+        sp = solver.solve(b, xp, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], y_fp32=y32, profile=1,
+                          gram_mode=args.gram_mode)
         phases = {k: getattr(sp, "t_" + k + "_ms") for k in ("mpk", "gram", "kappa", "control", "recombine", "other")}
         out[y32] = dict(value=args.steps / el, ms_per_step=el / args.steps * 1e3, outer=st.outer_iters,
                         inner=st.inner_iters, status=st.status, true_relres=st.true_relres,
@@ -289,7 +291,7 @@ def run_rgg(args, cfg, pkg, torch, dev):
             "warmup": args.warmup, "ms_per_step": out[0]["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["desc"], "s_max": cfg["smax"], "basis": cfg["basis"], "tol": cfg["tol"],
-                       "nnz": int(op.val.size)},
+                       "nnz": int(op.val.size), "gram_mode": args.gram_mode},
             "fp64_basis": out[0], "fp32_basis": out[1], "fp32_vs_fp64_solution_rel_diff": err,
             "hscg": {"value": 1.0 / th, "unit": "solves/s", "iters": hs.inner_iters, "status": hs.status,
                      "true_relres": hs.true_relres}}
@@ -430,7 +432,8 @@ def run_adjoint(args, cfg, pkg, torch, dev):
 
     def step():
         kxr, kyr = kx.clone().requires_grad_(), ky.clone().requires_grad_()
-        x = stencil_solve(kxr, kyr, None, b, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"])
+        x = stencil_solve(kxr, kyr, None, b, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"],
+                          gram_mode=args.gram_mode)
         loss = ((x - xt) ** 2).sum()
         loss.backward()
         return loss
@@ -454,7 +457,8 @@ def run_adjoint(args, cfg, pkg, torch, dev):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["desc"], "s_max": cfg["smax"], "basis": cfg["basis"], "tol": cfg["tol"],
-                       "l2": f"L2 flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)"},
+                       "l2": f"L2 flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                       "gram_mode": args.gram_mode},
             "loss": float(loss.item())}
     for k in ("forward", "adjoint"):
         st = ag.last_stats.get(k)

@@ -18,16 +18,16 @@ last_stats: dict = {}
 
 class StencilSolve(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, kx, ky, kz, b, tol=1e-10, s_max=16, basis="newton"):
+    def forward(ctx, kx, ky, kz, b, tol=1e-10, s_max=16, basis="newton", gram_mode=0):
         solver = sscg.Solver.stencil(kx.detach().contiguous(), ky.detach().contiguous(),
                                      kz.detach().contiguous() if kz is not None else None)
         x = torch.zeros_like(b)
-        st = solver.solve(b.detach().contiguous(), x, tol=tol, s_max=s_max, basis=basis)
+        st = solver.solve(b.detach().contiguous(), x, tol=tol, s_max=s_max, basis=basis, gram_mode=gram_mode)
         if st.status != sscg.OK:
             raise sscg.SscgError(f"forward solve status {st.status}")
         last_stats["forward"] = st
         ctx.solver = solver
-        ctx.cfg = (tol, s_max, basis)
+        ctx.cfg = (tol, s_max, basis, gram_mode)
         ctx.has_kz = kz is not None
         ctx.save_for_backward(x)
         ctx.shapes = (kx.shape, ky.shape, kz.shape if kz is not None else None)
@@ -36,10 +36,10 @@ class StencilSolve(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
-        tol, s_max, basis = ctx.cfg
+        tol, s_max, basis, gram_mode = ctx.cfg
         solver = ctx.solver
         lam = torch.zeros_like(x)
-        st = solver.solve(gx.contiguous(), lam, tol=tol, s_max=s_max, basis=basis)
+        st = solver.solve(gx.contiguous(), lam, tol=tol, s_max=s_max, basis=basis, gram_mode=gram_mode)
         if st.status != sscg.OK:
             raise sscg.SscgError(f"adjoint solve status {st.status}")
         last_stats["adjoint"] = st
@@ -49,9 +49,11 @@ class StencilSolve(torch.autograd.Function):
         gkz = torch.empty(sz, dtype=x.dtype, device=x.device) if ctx.has_kz else None
         sscg.sscg_stencil_face_grad(solver.h, lam, x, gkx, gky, gkz)
         solver.close()
-        return gkx, gky, gkz, lam, None, None, None
+        return gkx, gky, gkz, lam, None, None, None, None
 
 
-def stencil_solve(kx, ky, kz, b, tol=1e-10, s_max=16, basis="newton"):
-    """x = A(k)^{-1} b, differentiable in kx, ky, kz and b."""
-    return StencilSolve.apply(kx, ky, kz, b, tol, s_max, basis)
+def stencil_solve(kx, ky, kz, b, tol=1e-10, s_max=16, basis="newton", gram_mode=0):
+    """x = A(k)^{-1} b, differentiable in kx, ky, kz and b.  gram_mode selects
+    the Gram arithmetic of both solves (0: binary64 FMAs; 2: exact digit
+    products on the tensor cores; see sscg_opts)."""
+    return StencilSolve.apply(kx, ky, kz, b, tol, s_max, basis, gram_mode)
