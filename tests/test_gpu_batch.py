@@ -129,9 +129,10 @@ def test_batch_tile_shapes_and_their_autotuner(pkg):
     with pytest.raises(pkg.sscg.SscgError):
         pkg.sscg.sscg_solve_batch(hs, nrhs, bt, torch.zeros_like(bt), 1e-10, s_max, "newton",
                                   pkg.sscg.sscg_opts_default(batch_chunk_rows=64))
-    with pytest.raises(pkg.sscg.SscgError):  # the batch has no binary32-pair Gram
-        pkg.sscg.sscg_solve_batch(hs, nrhs, bt, torch.zeros_like(bt), 1e-10, s_max, "newton",
-                                  pkg.sscg.sscg_opts_default(gram_mode=1))
+    for mode in (1, 2):  # the batch has neither the binary32-pair nor the tensor-core Gram
+        with pytest.raises(pkg.sscg.SscgError):
+            pkg.sscg.sscg_solve_batch(hs, nrhs, bt, torch.zeros_like(bt), 1e-10, s_max, "newton",
+                                      pkg.sscg.sscg_opts_default(gram_mode=mode))
 
 
 def test_batched_hscg_matches_per_pair_hscg(pkg):

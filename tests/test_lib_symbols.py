@@ -60,3 +60,7 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert L.sscg_create_csr(ctypes.byref(h), 0, 0, None, None, None, 0, None) == -1
     assert L.sscg_solve(None, None, None, 1e-10, 8, 2, None, None) == -1
     assert L.sscg_leja(0, None) == -1
+    # Gram product arithmetic outside 0..2 is rejected before any pointer is used
+    fake = ctypes.c_void_p(16)
+    for mode in (-1, 3):
+        assert L.sscg_gram_ex(fake, ctypes.c_int64(10), ctypes.c_int64(10), 3, fake, mode, None) == -1
