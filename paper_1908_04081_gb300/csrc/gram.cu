@@ -311,10 +311,10 @@ gram_partial_ff_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
 // so a digit is its own encoding.  For u = s + t <= 11 the tensor cores
 // accumulate H_u = 2^-48 sum_rows sum_{s+t=u} d_s(y_i) d_t(y_j) in binary32;
 // every partial sum is an integer times 2^-48 below 2^24 2^-48 (at most
-// 1024 rows x 12 products x 961), so it is exact.  Every kDgFlushRows rows
-// the block adds
+// 1024 rows x 12 products x 961), so it is exact.  Every 1024 rows the
+// block adds
 //   G_ij += 2^(ce_i + ce_j - 2006) sum_{u <= 11} H_u 2^(-5u)
-// in binary64.  The terms dropped (s + t > 11) and the rounding of F are
+// (the sum formed exactly in two 64-bit integers, then two binary64 adds).  The terms dropped (s + t > 11) and the rounding of F are
 // below 2^-53 |y_i y_j| for values near the column's largest, so the result
 // is at least as accurate as binary64 FMAs; a column with an Inf or NaN in a
 // chunk makes its entries NaN.
@@ -540,31 +540,39 @@ __device__ __forceinline__ void dg_convert(const T* raw, unsigned char* stage, c
   }
 }
 
+// v 2^k for any k a sum of two exponents can give (two factors when 2^k
+// itself is out of the normal range)
+__device__ __forceinline__ double dg_scale(double v, int k) {
+  return (k >= -1022 && k <= 1023) ? v * pow2(k) : (v * pow2(k / 2)) * pow2(k - k / 2);
+}
+
 // add the digit sums of this lane's four tile entries into gacc (binary64)
-// and clear them
+// and clear them.  Each H_u is an integer times 2^-48 below 2^24 2^-48, so
+// 2^48 H_u converts to int32 exactly; Horner in base 32 over u = 0..5 and
+// u = 6..11 gives two integers below 2^49 (exact in int64 and in binary64),
+// and G_ij += 2^(ce_i + ce_j - 2006) (S_hi 2^-73 + S_lo 2^-103).
 __device__ __forceinline__ void dg_flush(float (&acc)[kDgPlanes][4], double (&gacc)[4], const int* ce_s, int ncols,
                                          int m0, int n0, int g, int tig) {
+  constexpr int kHalf = kDgPlanes / 2;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int i = m0 + g + (e >> 1) * 8, j = n0 + 2 * tig + (e & 1);
     if (i < ncols && j < ncols && i <= j) {
       const int ci = ce_s[i], cj = ce_s[j];
-      double h = 0.0;
+      long long shi = 0, slo = 0;
 #pragma unroll
-      for (int u = kDgPlanes - 1; u >= 0; --u)
-        h = fma(widen(acc[u][e]), __longlong_as_double((long long)(1023 - 5 * u) << 52), h);
+      for (int u = 0; u < kHalf; ++u) {
+        shi = shi * 32 + __float2int_rz(acc[u][e] * 0x1p48f);
+        slo = slo * 32 + __float2int_rz(acc[u + kHalf][e] * 0x1p48f);
+      }
       const int k = ci + cj - 2006;
       double& ge = gacc[e];
-      if (ci == 2047 || cj == 2047)
+      if (ci == 2047 || cj == 2047) {
         ge = __longlong_as_double(0x7ff8000000000000ll);
-      else if (((unsigned long long)__double_as_longlong(h) << 1) == 0ull)
-        ;  // nothing to add (and no 0 x Inf below)
-      else if (k >= -1022 && k <= 1023)
-        ge = fma(h, pow2(k), ge);
-      else if (k > 1023)
-        ge = fma(h * pow2(k - 1023), 0x1p1023, ge);
-      else
-        ge = fma(h * pow2(k + 1022), 0x1p-1022, ge);
+      } else {
+        if (shi != 0) ge += dg_scale((double)shi, k - 5 * (kHalf - 1) - 48);
+        if (slo != 0) ge += dg_scale((double)slo, k - 5 * (kDgPlanes - 1) - 48);
+      }
     }
   }
 #pragma unroll
