@@ -32,7 +32,7 @@ WORKLOADS = {
     "varcoef3d_160": dict(desc="FP64 3D 7-pt var-coef diffusion 160^3 (N=4,096,000), k=exp(N(0,1)) per face, "
                                "b~N(0,1), x0=0", smax=16, basis="newton", tol=1e-10),
     "poisson2d_64": dict(desc="FP64 2D 5-pt Poisson 64x64 CSR (N=4096), b=A x*, x*~U(-1,1), x0=0",
-                         smax=8, basis="chebyshev", tol=1e-10),
+                         smax=8, basis="chebyshev", tol=1e-10, gram_mode=0),
     "rgg_2m": dict(desc="FP64 CSR: Laplacian of a 3D random geometric graph, N=2,000,000, ~27 nnz/row, RCM order, "
                         "+1e-4*mean-degree*I, diagonal scaling 10^U(0,3); FP64 basis vs FP32-stored basis",
                    smax=16, basis="newton", tol=1e-10),
@@ -114,9 +114,11 @@ def parse_args():
     ap.add_argument("--max-outer", type=int, default=0, help="cap outer loops (profiling runs only)")
     ap.add_argument("--s-max", type=int, default=0,
                     help="override the workload's s_max (sigma) for studies; 0 keeps the configuration's")
-    ap.add_argument("--gram-mode", type=int, default=2,
+    ap.add_argument("--gram-mode", type=int, default=None,
                     help="0: binary64 Gram (the method as written); 1: binary32-pair products on the FP32 pipes; "
-                         "2: exact 5-bit digit products on the f16 tensor cores")
+                         "2: exact 5-bit digit products on the f16 tensor cores.  Default: the workload's "
+                         "(2, except 0 for the 64^2 Poisson case, where the tensor-core kernel's fixed cost "
+                         "per launch exceeds the binary64 kernel's time)")
     return ap.parse_args()
 
 
@@ -470,6 +472,8 @@ def run_adjoint(args, cfg, pkg, torch, dev):
 def main():
     args = parse_args()
     cfg = dict(WORKLOADS[args.workload])
+    if args.gram_mode is None:
+        args.gram_mode = cfg.get("gram_mode", 2)
     if args.s_max > 0:
         cfg["smax"] = args.s_max
     rank = int(os.environ.get("RANK", "0"))
