@@ -29,8 +29,9 @@ def dev(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
+@pytest.mark.parametrize("gram_mode", [0, 2])
 @pytest.mark.parametrize("shape", [(16, 16), (6, 5, 7)])
-def test_gradients_match_dense_adjoint(pkg, shape):
+def test_gradients_match_dense_adjoint(pkg, shape, gram_mode):
     from paper_1908_04081_gb300.autograd import stencil_solve
     st = gen.varcoef_stencil(shape, seed=5)
     b = gen.random_rhs(st.n, 1)
@@ -40,7 +41,7 @@ def test_gradients_match_dense_adjoint(pkg, shape):
     ky = dev(st.ky).requires_grad_()
     kz = dev(st.kz).requires_grad_() if st.kz is not None else None
     bt = dev(b).requires_grad_()
-    x = stencil_solve(kx, ky, kz, bt, tol=1e-12, s_max=8, basis="newton")
+    x = stencil_solve(kx, ky, kz, bt, tol=1e-12, s_max=8, basis="newton", gram_mode=gram_mode)
     loss = ((x - dev(xt)) ** 2).sum()
     loss.backward()
     assert abs(loss.item() - L) <= 1e-9 * L
@@ -60,7 +61,8 @@ def test_full_size_gradient_vs_finite_differences(pkg):
     ky = dev(op.ky).requires_grad_()
     bt = dev(b)
     xtt = dev(xt)
-    x = stencil_solve(kx, ky, None, bt, tol=1e-10, s_max=16, basis="newton")
+    # the benchmark's configuration: the tensor-core digit Gram
+    x = stencil_solve(kx, ky, None, bt, tol=1e-10, s_max=16, basis="newton", gram_mode=2)
     loss = ((x - xtt) ** 2).sum()
     loss.backward()
     x = x.detach()

@@ -468,9 +468,11 @@ def test_full_size_varcoef3d_160(pkg, gram_mode):
             assert abs(st.inner_iters - ref["sstep_inner"]) <= 0.1 * ref["sstep_inner"]
 
 
-def test_full_size_rgg_2m(pkg):
+@pytest.mark.parametrize("gram_mode", [2, 0])
+def test_full_size_rgg_2m(pkg, gram_mode):
     """The unstructured workload at full size (N = 2,000,000, ~53M nonzeros,
-    condition ~1e8) in the benchmark's launch configuration, with the binary64
+    condition ~1e8) in the benchmark's launch configuration (the tensor-core
+    digit Gram) and with the binary64 Gram, with the binary64
     and the binary32-stored basis: each converged to tol by an independent
     residual (the oracle's sparse matrix); the first outer loops of the
     binary64 run identical to the oracle's; the binary32-basis solution within
@@ -484,7 +486,8 @@ def test_full_size_rgg_2m(pkg):
     xs, sts = {}, {}
     for y32 in (0, 1):
         xt = dev(x0)
-        st = s.solve(dev(b), xt, tol=1e-10, s_max=16, basis="newton", hist_cap=20000, y_fp32=y32)
+        st = s.solve(dev(b), xt, tol=1e-10, s_max=16, basis="newton", hist_cap=20000, y_fp32=y32,
+                     gram_mode=gram_mode)
         assert st.status == 0, (y32, st.status)
         x = xt.cpu().numpy()
         relres = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
@@ -506,11 +509,13 @@ def test_full_size_rgg_2m(pkg):
             assert abs(st.inner_iters - ref[key]["sstep_inner"]) <= 0.1 * ref[key]["sstep_inner"], key
 
 
+@pytest.mark.parametrize("gram_mode", [0, 2])
 @pytest.mark.parametrize("name", ["poisson", "varcoef3d"])
-def test_fp32_stored_basis(pkg, name):
+def test_fp32_stored_basis(pkg, name, gram_mode):
     """Basis Y stored in binary32 (the recurrence, G, x, r, p in binary64) with
-    residual replacement; against the oracle's run of the same variant, and its
-    error against the binary64 solve reported through the assertions."""
+    residual replacement, with the binary64 and the tensor-core Gram; against
+    the oracle's run of the same variant, and its error against the binary64
+    solve reported through the assertions."""
     if name == "poisson":
         A, b, x0, _ = gen.config_problem("poisson2d_64")
         M = as_matrix(A)
@@ -526,7 +531,7 @@ def test_fp32_stored_basis(pkg, name):
     x_o, info = cg.sstep_cg(M, b, x0, 1e-10, cg.Options(smax=smax, basis=basis, y_fp32=True))
     x64, info64 = cg.sstep_cg(M, b, x0, 1e-10, cg.Options(smax=smax, basis=basis))
     xt = dev(x0)
-    st = s.solve(dev(b), xt, tol=1e-10, s_max=smax, basis=basis, hist_cap=4000, y_fp32=1)
+    st = s.solve(dev(b), xt, tol=1e-10, s_max=smax, basis=basis, hist_cap=4000, y_fp32=1, gram_mode=gram_mode)
     xg = xt.cpu().numpy()
     compare_solves(xg, st, pkg.sscg.history(st), x_o, info, 1e-10, strict=(name == "poisson"))
     assert abs(st.fp32_replacements - info["fp32_replacements"]) <= 1
