@@ -593,7 +593,7 @@ def test_gram_fast_modes(pkg, n, ncols, mode):
 
 
 @pytest.mark.parametrize("n,ncols", [(10007, 33), (70001, 17), (5000, 6)])
-def test_gram_fp8_digits_exact_on_integers(pkg, n, ncols):
+def test_gram_digits_exact_on_integers(pkg, n, ncols):
     """gram_mode 2 is exact where the products and sums are: integer entries
     below 2^16 have every digit exact, every 1024-row sum below 2^24 x 2^-48
     is exact in binary32 and the binary64 combination stays below 2^53, so G
@@ -610,7 +610,7 @@ def test_gram_fp8_digits_exact_on_integers(pkg, n, ncols):
     assert np.array_equal(Gg, Gi.astype(np.float64))
 
 
-def test_gram_fp8_digits_wide_exponents(pkg):
+def test_gram_digits_wide_exponents(pkg):
     """gram_mode 2 with values spread over 2^-60 .. 2^60 inside one column and
     chunk: entries far below the chunk's largest value lose their low bits,
     which the normwise bound absorbs (each row's error is below 2^-60 times
