@@ -627,6 +627,31 @@ def test_gram_digits_wide_exponents(pkg):
     assert np.max(np.abs(Gg - Go) / d) <= 1e-13
 
 
+def test_gram_digits_subnormal_columns(pkg):
+    """gram_mode 2 with binary64 subnormals: a column of subnormals only (its
+    scale exponent is the subnormal one, so its digits are exact) and a
+    column mixing subnormals with unit-size values (the subnormals fall below
+    the column's resolution, as they fall below binary64's resolution of the
+    products); G against binary64 to 1e-13 of sqrt(G_ii G_jj), and exactly zero
+    where binary64's products underflow."""
+    n, ncols = 5000, 5
+    rng = np.random.default_rng(17)
+    Y = rng.standard_normal((n, ncols))
+    Y[:, 0] = rng.standard_normal(n) * 2.0 ** -1060
+    mix = rng.random(n) < 0.5
+    Y[mix, 1] *= 2.0 ** -1060
+    Yd = dev(np.ascontiguousarray(Y.T).ravel())
+    G2 = torch.zeros(ncols * ncols, dtype=torch.float64, device="cuda")
+    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G2, 2)
+    Gg = G2.reshape(ncols, ncols).cpu().numpy()
+    Go = Y.T @ Y
+    assert np.all(np.isfinite(Gg))
+    d = np.sqrt(np.outer(np.diag(Go), np.diag(Go)))
+    d[d == 0] = 1.0
+    assert np.max(np.abs(Gg - Go) / d) <= 1e-13
+    assert Gg[0, 0] == 0.0 and Go[0, 0] == 0.0
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_gram_fast_modes_nonfinite(pkg, mode):
     """A NaN or Inf in Y reaches the entries of G that it touches in
