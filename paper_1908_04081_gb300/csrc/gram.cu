@@ -156,7 +156,6 @@ __device__ __forceinline__ double pow2(int k) {
 constexpr int kFFThreads = 640;
 constexpr int kFFRows = 256;
 constexpr int kFFCols = kMaxCols + 1;                           // 34: padded to whole groups
-constexpr int kFFGroups = kFFCols / 2;                          // 17
 constexpr int kFFLoads = (kFFRows * kMaxCols + kFFThreads - 1) / kFFThreads;  // 14 per thread
 constexpr size_t kFFSmem = 2 * (size_t)kFFRows * kFFCols * sizeof(float2);  // 139,264 B
 
@@ -346,13 +345,14 @@ constexpr int kDgThreads = kDgWarps * 32;
 constexpr int kDgConvThreads = kDgConvWarps * 32;
 // named barriers (0 is __syncthreads): stage buffer b full / empty, and the
 // conversion warps among themselves
-constexpr int kBarFull = 1, kBarEmpty = 3, kBarConv = 5;
+constexpr int kBarFull = 1, kBarEmpty = 3;
 constexpr int kDgPlaneBytes = kDgKBlocks * kDgColPad * 16;             // 6,144
 constexpr size_t kDgStageBytes = (size_t)kDgPlanes * kDgPlaneBytes;    // 73,728
-// raw stage row stride (elements): odd, so that the reads of 8 consecutive
-// columns by one phase of lanes fall in distinct banks
+// raw stage row stride (elements): 16-byte rows (for 16-byte copies and
+// reads) whose 16-byte reads by 8 consecutive columns fall in distinct bank
+// groups (528 or 272 bytes per column: 16 mod 128)
 template <typename T>
-constexpr int dg_raw_ld() { return kDgStageRows + 1; }
+constexpr int dg_raw_ld() { return sizeof(T) == 8 ? kDgStageRows + 2 : kDgStageRows + 4; }
 template <typename T>
 constexpr size_t dg_raw_bytes() { return (size_t)kMaxCols * dg_raw_ld<T>() * sizeof(T); }
 template <typename T>
@@ -428,22 +428,62 @@ gram_chunk_exp_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Solv
   }
 }
 
-// Raw stage: the stage's rows of every column copied from global memory by
-// cp.async into [column][dg_raw_ld] (zero filled past the block's last row).
+// Raw stage: every conversion thread copies, by cp.async, the rows it will
+// convert (8 rows of column 8 (cw % 4) + lane % 8 from row 8 (4 (cw / 4) +
+// lane / 8), and for ncols = 33 lanes 0..3 two rows of column 32) into
+// [column][dg_raw_ld] of the stage buffer, zero filled past the thread
+// block's last row; it later waits for its own copies only, so the conversion
+// warps need no barrier among themselves.  vec16: Y 16-byte aligned and ld a
+// multiple of 16 bytes / sizeof(T), so 16-byte copies (else one element per
+// copy).
+template <typename T>
+__device__ __forceinline__ void cp_async_elems(unsigned dst, const T* src, int nvalid, int nelems, bool vec16) {
+  constexpr int E = 16 / sizeof(T);  // elements per 16-byte copy
+  if (vec16) {
+    for (int q = 0; q < nelems; q += E) {
+      int v = nvalid - q;
+      v = v < 0 ? 0 : (v > E ? E : v);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst + (unsigned)(q * sizeof(T))),
+                   "l"(v > 0 ? src + q : src), "r"(v * (int)sizeof(T))
+                   : "memory");
+    }
+  } else {
+    for (int q = 0; q < nelems; ++q) {
+      const int v = q < nvalid ? (int)sizeof(T) : 0;
+      if (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst + (unsigned)(q * 8)),
+                     "l"(v ? src + q : src), "r"(v)
+                     : "memory");
+      else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + (unsigned)(q * 4)),
+                     "l"(v ? src + q : src), "r"(v)
+                     : "memory");
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void dg_issue_raw(T* raw, const T* __restrict__ Y, int64_t ld, int64_t r0, int64_t r_end,
-                                             int ncols, int ct) {
+                                             int ncols, int cw, bool vec16) {
+  constexpr int LD = dg_raw_ld<T>();
+  const int lane = threadIdx.x & 31;
   const unsigned rbase = (unsigned)__cvta_generic_to_shared(raw);
-  for (int e = ct; e < ncols * kDgStageRows; e += kDgConvThreads) {
-    const int c = e / kDgStageRows, r = e - c * kDgStageRows;
-    const int64_t row = r0 + r;
-    const bool ok = row < r_end;
-    const T* src = Y + (int64_t)c * ld + (ok ? row : 0);
-    const unsigned dst = rbase + (unsigned)((c * dg_raw_ld<T>() + r) * sizeof(T));
-    if (sizeof(T) == 8)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
-    else
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
+  const int c = 8 * (cw & 3) + (lane & 7), kb = 4 * (cw >> 2) + (lane >> 3);
+  if (c < ncols) {
+    const int64_t row = r0 + 8 * kb;
+    const int64_t nv = r_end - row;
+    // rows past the end are zero filled; their source address is never read
+    // but stays inside Y (row 0 of the column)
+    cp_async_elems<T>(rbase + (unsigned)((c * LD + 8 * kb) * sizeof(T)), Y + (int64_t)c * ld + (nv > 0 ? row : 0),
+                      nv < 0 ? 0 : (nv > 8 ? 8 : (int)nv), 8, vec16);
+  }
+  if (ncols > 32 && lane < 4) {
+    const int64_t row = r0 + 8 * cw + 2 * lane;
+    const int64_t nv = r_end - row;
+    const int nvalid = nv < 0 ? 0 : (nv > 2 ? 2 : (int)nv);
+    const unsigned dst = rbase + (unsigned)((32 * LD + 8 * cw + 2 * lane) * sizeof(T));
+    // two elements: one 16-byte copy for binary64, element copies otherwise
+    cp_async_elems<T>(dst, Y + 32 * ld + (nvalid > 0 ? row : 0), nvalid, 2, vec16 && sizeof(T) == 8);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -522,10 +562,25 @@ __device__ __forceinline__ void dg_convert(const T* raw, unsigned char* stage, c
   const int lane = threadIdx.x & 31;
   const int c = 8 * (cw & 3) + (lane & 7), kb = 4 * (cw >> 2) + (lane >> 3);
   if (c < ncols) {
-    const T* src = raw + c * LD + 8 * kb;
+    const T* src = raw + c * LD + 8 * kb;  // 16-byte aligned
     double v[8];
+    if (sizeof(T) == 8) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = widen(src[k]);
+      for (int k = 0; k < 4; ++k) {
+        const double2 p = reinterpret_cast<const double2*>(src)[k];
+        v[2 * k] = p.x;
+        v[2 * k + 1] = p.y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float4 p = reinterpret_cast<const float4*>(src)[k];
+        v[4 * k] = widen(p.x);
+        v[4 * k + 1] = widen(p.y);
+        v[4 * k + 2] = widen(p.z);
+        v[4 * k + 3] = widen(p.w);
+      }
+    }
     if (diag_fp64 && c == ncols - 1) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) dg = fma(v[k], v[k], dg);
@@ -601,7 +656,7 @@ __device__ __forceinline__ void dg_mma_stage(float (&acc)[kDgPlanes][4], unsigne
 template <typename T>
 __global__ void __launch_bounds__(kDgThreads, 1)
 gram_partial_dg_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const SolveState* __restrict__ st,
-                       int ncols_fixed, const int* __restrict__ cexp, double* __restrict__ partials) {
+                       int ncols_fixed, const int* __restrict__ cexp, double* __restrict__ partials, bool vec16) {
   int ncols = ncols_fixed;
   if (ncols <= 0) {
     if (st->done) return;
@@ -654,19 +709,17 @@ gram_partial_dg_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
     // commits one cp.async group (possibly empty), so "wait_group 1" means
     // that raw stage k has landed.
     const int ct = t - kDgTileWarps * 32, cw = warp - kDgTileWarps;
-    dg_issue_raw(raw[0], Y, ld, r_begin, r_end, ncols, ct);
-    dg_issue_raw(raw[1], Y, ld, r_begin + kDgStageRows, r_end, ncols, ct);
+    dg_issue_raw(raw[0], Y, ld, r_begin, r_end, ncols, cw, vec16);
+    dg_issue_raw(raw[1], Y, ld, r_begin + kDgStageRows, r_end, ncols, cw, vec16);
     for (int64_t k = 0; k < nst; ++k) {
       const int b = (int)(k & 1);
       const int64_t r0 = r_begin + k * kDgStageRows;
       const int* ce_g = cexp + (r0 >> kDgChunkShift) * kMaxCols;
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-      bar_sync(kBarConv, kDgConvThreads);                   // raw stage k visible to all conversion warps
+      asm volatile("cp.async.wait_group 1;" ::: "memory");  // this thread's rows of stage k have landed
       if (k >= 2) bar_sync(kBarEmpty + b, kDgThreads);      // the MMA warps are done with stage k - 2
       if (ct < ncols) ce_buf[b][ct] = __ldg(ce_g + ct);
       dg_convert(raw[b], dg_smem + (size_t)b * kDgStageBytes, ce_g, ncols, cw, diag_fp64, dg);
-      bar_sync(kBarConv, kDgConvThreads);                   // raw stage k fully read
-      dg_issue_raw(raw[b], Y, ld, r0 + 2 * kDgStageRows, r_end, ncols, ct);
+      dg_issue_raw(raw[b], Y, ld, r0 + 2 * kDgStageRows, r_end, ncols, cw, vec16);  // own rows, read above
       bar_arrive(kBarFull + b, kDgThreads);                 // digit buffer b holds stage k
     }
     // the empty signals of the last two stages
@@ -873,16 +926,18 @@ cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* /*ncols
     if (nstages < nb) nb = (int)nstages;
     if (nb < 1) nb = 1;
     nblocks = nb;
+    const size_t esz = y32 ? 4 : 8;
+    const bool vec16 = ((uintptr_t)Y % 16 == 0) && ((size_t)ld * esz) % 16 == 0;
     if (y32) {
       gram_chunk_exp_kernel<float><<<egrid, 256, 0, st>>>(static_cast<const float*>(Y), n, ld, state, ncols_fixed,
                                                           chunk_exp);
       gram_partial_dg_kernel<float><<<nblocks, kDgThreads, dg_smem_bytes<float>(), st>>>(
-          static_cast<const float*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials);
+          static_cast<const float*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
     } else {
       gram_chunk_exp_kernel<double><<<egrid, 256, 0, st>>>(static_cast<const double*>(Y), n, ld, state,
                                                            ncols_fixed, chunk_exp);
       gram_partial_dg_kernel<double><<<nblocks, kDgThreads, dg_smem_bytes<double>(), st>>>(
-          static_cast<const double*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials);
+          static_cast<const double*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
     }
   } else if (gram_mode == 1) {
     // one block per SM, at most one block per 256-row tile

@@ -566,7 +566,7 @@ def test_failure_detection_injected_on_the_host(pkg):
 @pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("n,ncols", [(1, 1), (2, 2), (777, 5), (513, 4), (10007, 33), (70001, 17),
                                      (300000, 33), (1000003, 9), (8193, 3), (4095, 32), (12289, 31),
-                                     (155000, 33)])
+                                     (155000, 33), (4102, 33)])
 def test_gram_fast_modes(pkg, n, ncols, mode):
     """gram_mode 1 and 2 against binary64: mode 1 carries at most ~2^-46
     relative error per term, mode 2 at most ~2^-53 of the product of the
@@ -574,7 +574,8 @@ def test_gram_fast_modes(pkg, n, ncols, mode):
     including columns whose scales differ by 10^8, a column of exact zeros,
     row counts that end inside a 64-row stage, a 1024-row exact-sum block and
     a 4096-row scale chunk, thread blocks whose row ranges start inside those,
-    and every tile shape (1 to 33 columns)."""
+    every tile shape (1 to 33 columns), and odd leading dimensions (ld = n + 1:
+    element-wise instead of 16-byte copies)."""
     rng = np.random.default_rng(n + 7 * ncols)
     Y = rng.standard_normal((n, ncols)) * np.logspace(-4, 4, ncols)[None, :]
     if ncols > 2:
