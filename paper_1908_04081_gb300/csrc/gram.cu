@@ -313,24 +313,27 @@ gram_partial_ff_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
 // 1024 rows x 12 products x 961), so it is exact.  Every 1024 rows the
 // block adds
 //   G_ij += 2^(ce_i + ce_j - 2006) sum_{u <= 11} H_u 2^(-5u)
-// (the sum formed exactly in two 64-bit integers, then two binary64 adds).  The terms dropped (s + t > 11) and the rounding of F are
-// below 2^-53 |y_i y_j| for values near the column's largest, so the result
-// is at least as accurate as binary64 FMAs; a column with an Inf or NaN in a
-// chunk makes its entries NaN.
+// (the sum formed exactly in two 64-bit integers, then two binary64 adds).
+// The terms dropped (s + t > 11) and the rounding of F are below 2^-53
+// |y_i y_j| for values near the column's largest, so the result is at least
+// as accurate as binary64 FMAs; a column with an Inf or NaN in a chunk makes
+// its entries NaN.
 //
 // Work layout (warp specialised): eight MMA warps own one 16 x 8 tile
 // (m16n8k16) of the upper triangle of G each, with all 12 accumulators
 // H_0..H_11 of the tile (48 registers).  Per 16-row k-step a warp loads the
 // B fragments of all 12 digit planes once, then for each plane s one A
 // fragment feeding 12 - s MMAs (78 per k-step).  Eight conversion warps fetch
-// the raw values of the stages ahead by cp.async and write their digits; the
-// digits of a 64-row stage sit in shared memory as [plane][8-row block]
-// [column][16 bytes] (one 16-byte ldmatrix row per column and block), double
-// buffered, handed over with named barriers (full: conversion warps arrive,
-// MMA warps wait; empty: the reverse), so conversion overlaps the MMAs.  When ncols = 16 m + 1 (ncols = 17, 33) the last tile row holds
-// only the diagonal entry of the last column; it is summed with binary64
-// FMAs by the threads that convert that column instead, which leaves 2
-// MMA warps per sub-partition at ncols = 33.
+// the raw values of the stages ahead by cp.async (each thread the rows it
+// converts) and write their digits; the digits of a 64-row stage sit in
+// shared memory as [plane][8-row block][column][16 bytes] (one 16-byte
+// ldmatrix row per column and block), double buffered, handed over with
+// named barriers (full: conversion warps arrive, MMA warps wait; empty: the
+// reverse), so conversion overlaps the MMAs.  When ncols = 16 m + 1
+// (ncols = 17, 33) the last tile row holds only the diagonal entry of the
+// last column; it is summed with binary64 FMAs by the threads that convert
+// that column instead, which leaves 2 MMA warps per sub-partition at
+// ncols = 33.
 constexpr int kDgPlanes = 12;
 constexpr int kDgStageRows = 64;
 constexpr int kDgKBlocks = kDgStageRows / 8;    // 8-row blocks per stage
@@ -343,8 +346,8 @@ constexpr int kDgConvWarps = 8;                 // conversion warps
 constexpr int kDgWarps = kDgTileWarps + kDgConvWarps;
 constexpr int kDgThreads = kDgWarps * 32;
 constexpr int kDgConvThreads = kDgConvWarps * 32;
-// named barriers (0 is __syncthreads): stage buffer b full / empty, and the
-// conversion warps among themselves
+// named barriers (0 is __syncthreads): stage buffer b full (1 + b) and
+// empty (3 + b)
 constexpr int kBarFull = 1, kBarEmpty = 3;
 constexpr int kDgPlaneBytes = kDgKBlocks * kDgColPad * 16;             // 6,144
 constexpr size_t kDgStageBytes = (size_t)kDgPlanes * kDgPlaneBytes;    // 73,728
@@ -356,7 +359,7 @@ constexpr int dg_raw_ld() { return sizeof(T) == 8 ? kDgStageRows + 2 : kDgStageR
 template <typename T>
 constexpr size_t dg_raw_bytes() { return (size_t)kMaxCols * dg_raw_ld<T>() * sizeof(T); }
 template <typename T>
-constexpr size_t dg_smem_bytes() { return 2 * kDgStageBytes + 2 * dg_raw_bytes<T>(); }  // 185,472 for binary64
+constexpr size_t dg_smem_bytes() { return 2 * kDgStageBytes + 2 * dg_raw_bytes<T>(); }  // 182,304 for binary64
 static_assert(kDgChunkRows == (1 << kDgChunkShift) && kDgChunkShift >= kDgFlushShift &&
               (1 << kDgFlushShift) % kDgStageRows == 0, "chunk");
 static_assert(kDgConvThreads == 32 * kDgKBlocks && kDgConvWarps == kDgKBlocks && kMaxCols <= 33,
