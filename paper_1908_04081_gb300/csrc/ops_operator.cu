@@ -147,8 +147,12 @@ __global__ void __launch_bounds__(kOpThreads) stencil_mpk_kernel(Operator A, T* 
 
 // One matrix-powers level for a stencil, one cell per thread on a 3D grid
 // (x in 32-lane rows, y in 8-row tiles, z per grid plane): the coordinates
-// come from the launch indices, with no division, and the sum is formed in
-// stencil_apply's order (same bits as the grid-stride kernel).
+// come from the launch indices, with no division.  The block first stages
+// its 34 x 10 in-plane tile of P_l and R_l (halo included, zero outside the
+// domain) in shared memory, so the four in-plane neighbours come from shared
+// memory and only the centre tile and the two z neighbours from L1/L2; the
+// sum is formed in stencil_apply's order (same bits as the grid-stride
+// kernel).
 template <bool DIM3, typename T>
 __global__ void __launch_bounds__(256) stencil_mpk_grid_kernel(Operator A, T* __restrict__ Y, int64_t ld,
                                                                  int level, const SolveState* __restrict__ st,
@@ -161,26 +165,67 @@ __global__ void __launch_bounds__(256) stencil_mpk_grid_kernel(Operator A, T* __
   const bool doP = level < sbar;
   const bool doR = level + 1 < sbar;
   if (!doP) return;
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int yy = blockIdx.y * 8 + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= A.nx || yy >= A.ny) return;
-  const int64_t i = ((int64_t)z * A.ny + yy) * A.nx + x;
-  const double theta = coef.theta[level];
-  const double ig = coef.inv_gamma[level];
-  const double mu = level >= 1 ? coef.mu[level - 1] : 0.0;
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+  const int x = x0 + tx, yy = y0 + ty, z = blockIdx.z;
   const T* Pl = Y + (int64_t)(2 * level) * ld;
   const T* Rl = Y + (int64_t)(2 * level + 1) * ld;
   T* Pn = Y + (int64_t)(2 * level + 2) * ld;
   T* Rn = Y + (int64_t)(2 * level + 3) * ld;
+  __shared__ double sP[10][34], sR[10][34];
+  const int64_t zoff = (int64_t)z * ny * nx;
+  for (int e = ty * 32 + tx; e < 340; e += 256) {
+    const int ly = e / 34, lx = e - ly * 34;
+    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    const int64_t gi = zoff + (int64_t)gy * nx + gx;
+    sP[ly][lx] = in ? ld_val(Pl + gi) : 0.0;
+    sR[ly][lx] = (in && doR) ? ld_val(Rl + gi) : 0.0;
+  }
+  __syncthreads();
+  if (x >= nx || yy >= ny) return;
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t i = zoff + (int64_t)yy * nx + x;
+  const int64_t fx = ((int64_t)z * ny + yy) * (nx + 1) + x;
+  const int64_t fy = ((int64_t)z * (ny + 1) + yy) * nx + x;
+  const double kw = -__ldg(A.kx + fx), ke = -__ldg(A.kx + fx + 1);
+  const double ks = -__ldg(A.ky + fy), kn = -__ldg(A.ky + fy + nx);
+  double kd = 0.0, ku = 0.0;
+  if (DIM3) {
+    kd = -__ldg(A.kz + i);
+    ku = -__ldg(A.kz + i + plane);
+  }
+  const double theta = coef.theta[level];
+  const double ig = coef.inv_gamma[level];
+  const double mu = level >= 1 ? coef.mu[level - 1] : 0.0;
   const double ds = __ldg(A.diag + i) - theta;
-  double wp = stencil_apply<DIM3>(A, Pl, i, x, yy, z, ds);
-  if (mu != 0.0) wp = fma(-mu, ld_val(Y + (int64_t)(2 * level - 2) * ld + i), wp);
-  Pn[i] = (T)(wp * ig);
+  const int ly = ty + 1, lx = tx + 1;
+  {
+    double acc = ds * sP[ly][lx];
+    acc = fma(kw, sP[ly][lx - 1], acc);
+    acc = fma(ke, sP[ly][lx + 1], acc);
+    acc = fma(ks, sP[ly - 1][lx], acc);
+    acc = fma(kn, sP[ly + 1][lx], acc);
+    if (DIM3) {
+      acc = fma(kd, z > 0 ? ld_val(Pl + i - plane) : 0.0, acc);
+      acc = fma(ku, z < nz - 1 ? ld_val(Pl + i + plane) : 0.0, acc);
+    }
+    if (mu != 0.0) acc = fma(-mu, ld_val(Y + (int64_t)(2 * level - 2) * ld + i), acc);
+    Pn[i] = (T)(acc * ig);
+  }
   if (doR) {
-    double wr = stencil_apply<DIM3>(A, Rl, i, x, yy, z, ds);
-    if (mu != 0.0) wr = fma(-mu, ld_val(Y + (int64_t)(2 * level - 1) * ld + i), wr);
-    Rn[i] = (T)(wr * ig);
+    double acc = ds * sR[ly][lx];
+    acc = fma(kw, sR[ly][lx - 1], acc);
+    acc = fma(ke, sR[ly][lx + 1], acc);
+    acc = fma(ks, sR[ly - 1][lx], acc);
+    acc = fma(kn, sR[ly + 1][lx], acc);
+    if (DIM3) {
+      acc = fma(kd, z > 0 ? ld_val(Rl + i - plane) : 0.0, acc);
+      acc = fma(ku, z < nz - 1 ? ld_val(Rl + i + plane) : 0.0, acc);
+    }
+    if (mu != 0.0) acc = fma(-mu, ld_val(Y + (int64_t)(2 * level - 1) * ld + i), acc);
+    Rn[i] = (T)(acc * ig);
   }
 }
 
