@@ -93,8 +93,8 @@ MPK_FP64_OPS_PER_CELL = {"newton": 17, "monomial": 17, "chebyshev": 19}
 FP64_PEAK_TOPS = 152 * 4 * 32 / 64 * 2.070e9 / 1e12   # binary64 lane ops/s: 4 sub-partitions x 32 lanes / 64 cycles
 # DRAM bytes per cell and level of stencil_mpk_grid_kernel (read + write),
 # from the one-pass ncu capture of two levels of the 160^3 case
-# (profiles/stencil_mpk_varcoef3d_160.md): 243.1 MB per launch / 4,096,000
-MPK_DRAM_BYTES_PER_CELL = 59.36
+# (profiles/stencil_mpk_varcoef3d_160.md): 242.9 MB per launch / 4,096,000
+MPK_DRAM_BYTES_PER_CELL = 59.30
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
