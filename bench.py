@@ -697,10 +697,10 @@ def main():
                        "l2": l2_note,
                        "timing": "CUDA events around K solves; per-phase CUDA events inside each solve",
                        "gram": {0: "binary64 FMA", 1: "binary32-pair products, binary64 accumulation",
-                                2: "G at binary64 accuracy or better: every value written as 12 5-bit digits "
-                                   "(exact within 2^7 of its column's largest, else rounded at 2^-60 of it), "
-                                   "digit products exact on the f16 tensor cores, exact binary32 sums over 1024 "
-                                   "rows, binary64 across blocks (error below binary64 FMAs')"}
+                                2: "G at binary64 normwise accuracy or better: every value written as 12 5-bit "
+                                   "digits (exact within 2^7 of its column's largest, else rounded at 2^-60 of "
+                                   "it), digit products exact on the f16 tensor cores, exact binary32 sums over "
+                                   "1024 rows, binary64 across blocks (normwise error below binary64 FMAs')"}
                        [args.gram_mode]},
             "converged": ok, "true_relres": max(s.true_relres for s in stats),
             "outer_loops": st0.outer_iters, "inner_iters": st0.inner_iters, "host_syncs": st0.host_syncs,

@@ -83,7 +83,7 @@ typedef struct {
                             256-row tiles, binary64 across tiles; 2: every value written as 12 signed
                             5-bit digits after a per-4096-row-chunk power-of-two column scale, all digit
                             products on the f16 tensor cores with exact binary32 sums over 1024 rows,
-                            binary64 across them (error below binary64 FMAs'); default 0 */
+                            binary64 across them (normwise error below binary64 FMAs'); default 0 */
   int batch_chunk_rows;  /* sscg_solve_batch only: rows per work chunk of the row kernels (matrix powers,
                             recombination, residual checks); 0 = 2048, else 128..1048576 */
   int batch_gram_rows;   /* sscg_solve_batch only: rows per Gram block; 0 = 2048, else 128..1048576 */
@@ -301,10 +301,13 @@ int sscg_gram(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, voi
  * the integer F = round(|y| 2^(1082 - e_c)) (e_c the biased exponent of
  * column c's largest value in its 4096-row chunk) split into 12 signed 5-bit
  * digits, forms all digit products (pairs s + t <= 11) on the f16 tensor
- * cores with exact binary32 sums over 1024 rows, and adds those in binary64;
- * a column with an Inf or NaN in a chunk gives NaN entries.  Mode 2 also
- * allocates an integer scratch of 33 entries per 4096 rows.  Same arguments and allocation
- * behaviour as sscg_gram otherwise; mode outside 0..2: SSCG_ERR_INVALID_ARG. */
+ * cores with exact binary32 sums over 1024 rows, and adds those in binary64
+ * (normwise error below binary64 FMAs'; componentwise, an entry made only of
+ * products far below the two columns' largest values keeps just that
+ * absolute accuracy); a column with an Inf or NaN in a chunk gives NaN
+ * entries.  Mode 2 also allocates an integer scratch of 33 entries per 4096
+ * rows.  Same arguments and allocation behaviour as sscg_gram otherwise; mode
+ * outside 0..2: SSCG_ERR_INVALID_ARG. */
 int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, int mode, void* cuda_stream);
 
 /* Same result as sscg_gram, for callers that cannot allocate device memory

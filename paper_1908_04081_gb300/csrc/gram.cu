@@ -314,10 +314,14 @@ gram_partial_ff_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
 // block adds
 //   G_ij += 2^(ce_i + ce_j - 2006) sum_{u <= 11} H_u 2^(-5u)
 // (the sum formed exactly in two 64-bit integers, then two binary64 adds).
-// The terms dropped (s + t > 11) and the rounding of F are below 2^-53
-// |y_i y_j| for values near the column's largest, so the result is at least
-// as accurate as binary64 FMAs; a column with an Inf or NaN in a chunk makes
-// its entries NaN.
+// Per row, the rounding of F (2^-60 of the column's largest value) and the
+// terms dropped (s + t > 11: about 2^-56.5 of the product of the two columns'
+// largest values) bound the error, so normwise the result is at least as
+// accurate as binary64 FMAs (below 2^-53 ||y_i|| ||y_j|| in the tests, where
+// binary64 FMAs are only bounded by n 2^-53 ||y_i|| ||y_j||); componentwise it
+// is not: an entry whose products all lie far below the two columns' largest
+// values keeps only that absolute accuracy.  A column with an Inf or NaN in a
+// chunk makes its entries NaN.
 //
 // Work layout (warp specialised): eight MMA warps own one 16 x 8 tile
 // (m16n8k16) of the upper triangle of G each, with all 12 accumulators

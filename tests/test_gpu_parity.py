@@ -614,8 +614,8 @@ def test_gram_digits_exact_on_integers(pkg, n, ncols):
 def test_gram_digits_wide_exponents(pkg):
     """gram_mode 2 with values spread over 2^-60 .. 2^60 inside one column and
     chunk: entries far below the chunk's largest value lose their low bits,
-    which the normwise bound absorbs (each row's error is below 2^-60 times
-    the product of the two column maxima)."""
+    which the normwise bound absorbs (each row's error is below about 2^-56
+    times the product of the two column maxima)."""
     n, ncols = 20000, 9
     rng = np.random.default_rng(11)
     Y = rng.standard_normal((n, ncols)) * np.exp2(rng.integers(-60, 61, (n, ncols)))
