@@ -138,7 +138,7 @@ cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level,
 
 // gram.cu
 int gram_blocks(int64_t n);
-// per-device one-time setup of the gram_mode = 1 kernels (shared memory
+// per-device one-time setup of the gram_mode 1 and 2 kernels (shared memory
 // above the 48 KB default); call outside stream capture, before launch_gram
 cudaError_t gram_prepare();
 // gram_mode 0: binary64 products and sums; 1: binary32-pair products on the

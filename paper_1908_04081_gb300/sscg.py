@@ -169,6 +169,8 @@ def sscg_opts_default(**kw) -> Opts:
             v = {"standard": 0, "paper_printed": 1}[v]
         if k == "variant" and isinstance(v, str):
             v = {"improved": 0, "fixed": 1, "old": 2}[v]
+        if k == "gram_mode" and isinstance(v, str):
+            v = {"binary64": 0, "binary32_pair": 1, "digits": 2}[v]
         setattr(o, k, v)
     return o
 

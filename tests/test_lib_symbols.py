@@ -51,6 +51,9 @@ def test_binding_defaults(lib):
     assert o.inner_conv_check == 1 and o.eps == 2.0 ** -53 and o.kappa_cut == 2.0 ** -44
     o2 = sscg.sscg_opts_default(c_mode="one", variant="fixed")
     assert o2.c_mode == 2 and o2.variant == 1
+    assert o.gram_mode == 0  # the method as written
+    assert sscg.sscg_opts_default(gram_mode="digits").gram_mode == 2
+    assert sscg.sscg_opts_default(gram_mode="binary32_pair").gram_mode == 1
 
 
 def test_invalid_arguments_rejected_without_gpu(lib):
