@@ -134,6 +134,9 @@ class Options:
     # log-distance of the deciding quantity to its threshold ("margins"); the
     # solve ends after the last record.
     replay: list | None = None
+    # gram: a callable Y -> G used instead of Y^T Y (G = Y^T Y of Section 2
+    # computed another way, for studies of that arithmetic); None: Y.T @ Y
+    gram: object = None
 
 
 def kappa_estimates(G: np.ndarray, sbar: int, kappa_cut: float = KAPPA_CUT):
@@ -218,7 +221,7 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
     for k in range(o.max_outer):
         sbar = s0 if k == 0 else min(s_prev + f, sigma)
         Y = bs.krylov_basis(A, p, r, sbar, theta, gamma, mu, store32=o.y_fp32)
-        G = Y.T @ Y
+        G = Y.T @ Y if o.gram is None else o.gram(Y)
         kap, _, _ = kappa_estimates(G, sbar, o.kappa_cut)
         normr = math.sqrt(G[1, 1])
         margins = {}
