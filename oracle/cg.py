@@ -164,6 +164,35 @@ def kappa_estimates(G: np.ndarray, sbar: int, kappa_cut: float = KAPPA_CUT):
     return kap, lmins, lmaxs
 
 
+def choose_stilde(kap, sbar: int, tol: float, c: float, eps: float, normr: float, normb: float) -> int:
+    """s~_k of eq. (condy): the largest l <= s-bar with kappa(Y_l) <= eps*/(c eps ||r_m||/||b||)
+    (eq. (cond) with the relative residual, reading C10); 1 when no l qualifies (C12).
+
+    ``kap[l]`` is the estimate kappa_l of kappa(Y_{k,l}), l = 1..sbar (entry 0 unused).
+    """
+    thr = tol / (c * eps * normr / normb)
+    cands = [l for l in range(1, sbar + 1) if kap[l] <= thr]
+    return max(cands) if cands else 1
+
+
+def break_test(gam_next: float, tol: float, c: float, eps: float, phi: float, normb: float) -> bool:
+    """The improved break test of eq. (newcondy): stop the block when
+    gamma_{j+1} >= eps*/(c eps phi/||b||), phi the running maximum of the
+    residual estimates of the block (reading C10 for the relative form)."""
+    return gam_next >= tol / (c * eps * phi / normb)
+
+
+def psi_update(psi: float, beta: float) -> float:
+    """eq. (psiupd): psi_{n+1} = psi_n / (psi_n + beta_n), the ratio ||r_{n+1}||^2/||p_{n+1}||^2."""
+    return psi / (psi + beta)
+
+
+def uses_ritz_c(m: int, j: int) -> bool:
+    """Alg. 5 updates c from the Ritz estimates once the global iteration count
+    m + j + 1 exceeds 1 (two alphas known, reading C22)."""
+    return m + j + 1 > 1
+
+
 def c_value(mode: str, lmin: float, lmax: float, psi: float, c_const: float = 1.0) -> float:
     """c_{m+j+1} of Alg. 5 (eq. xiupd) and the alternatives of Section 5.1."""
     if mode == "xi":
@@ -230,9 +259,8 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
         if o.variant == "fixed":
             stilde = sbar
         else:
+            stilde = choose_stilde(kap, sbar, tol, c, eps, normr, normb)
             thr = tol / (c * eps * normr / normb)
-            cands = [l for l in range(1, sbar + 1) if kap[l] <= thr]
-            stilde = max(cands) if cands else 1
             if o.replay is not None:
                 own = stilde
                 stilde = o.replay[k]["stilde"]
@@ -252,6 +280,8 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
         rr = float(rc @ Gs @ rc)
         phi = math.sqrt(max(rr, 0.0))
         c_start = c
+        rr0 = rr
+        rr_steps, c_steps = [], []     # per inner step: r'^T G r' and c after the step
         sk = 0
         converged_est = False
         breakdown = False
@@ -274,18 +304,20 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
             beta = rr_new / rr
             pc = rc + beta * pc
             phi = max(phi, math.sqrt(rr_new))
-            psi = psi / (psi + beta)
+            psi = psi_update(psi, beta)
             ritz.push(alpha, betas[-1] if betas else None)
             betas.append(beta)
-            if m + j + 1 > 1 and o.variant != "old":
+            if uses_ritz_c(m, j) and o.variant != "old":
                 c = c_value(o.c_mode, ritz.lmin, ritz.lmax, psi, o.c_const)
             rr = rr_new
+            rr_steps.append(rr_new)
+            c_steps.append(c)
             own_conv = o.inner_conv_check and math.sqrt(rr_new) / normb <= tol
             if o.variant == "old":   # Alg. 2: kappa of the whole block, current residual
                 own_brk = (not own_conv) and kap[stilde] >= tol / (c * eps * math.sqrt(rr_new) / normb)
             else:
                 own_brk = (not own_conv) and o.variant != "fixed" and j < stilde - 1 and \
-                    gam[j + 1] >= tol / (c * eps * phi / normb)
+                    break_test(gam[j + 1], tol, c, eps, phi, normb)
             if forced_sk is None:
                 if own_conv:
                     converged_est = True
@@ -314,7 +346,9 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
         s_prev = sk
         hist.append(dict(sbar=sbar, stilde=stilde, sk=sk, kappa=kap.tolist(), c_start=c_start,
                          c=c, phi=phi, lmin=ritz.lmin, lmax=ritz.lmax,
-                         relres_est=math.sqrt(max(rr, 0.0)) / normb, m=m, margins=margins))
+                         relres_est=math.sqrt(max(rr, 0.0)) / normb, m=m, margins=margins,
+                         normr_start=normr, rr0=rr0, rr_steps=rr_steps, c_steps=c_steps,
+                         psi_end=psi, pGp_end=float(pc @ Gs @ pc)))
         if m > 1 and kind != bs.MONOMIAL and o.variant != "old":
             theta, gamma, mu = bs.basis_params(kind, sigma, ritz.lmin, ritz.lmax,
                                                o.newton_scale, o.cheb_params)

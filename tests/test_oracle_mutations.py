@@ -127,3 +127,92 @@ def test_swapped_newton_endpoints_fail_explicit_pin():
     th, _, _ = m.basis_params(1, 4, 0.5, 3.5)
     # eq. (newtbasis): theta_0 = lmax, theta_1 = lmin
     assert not (th[0] == 3.5 and th[1] == 0.5)
+
+
+# ------------------------------------------------- Alg. 5's adaptive decisions
+from tests import test_oracle_decisions as dec  # noqa: E402
+
+
+def _fails(pin, *args) -> bool:
+    try:
+        pin(*args)
+    except AssertionError:
+        return True
+    return False
+
+
+def test_condy_strict_inequality_fails_boundary_pin():
+    m = mutated("cg", "if kap[l] <= thr]", "if kap[l] < thr]")
+    assert _fails(dec.test_condy_largest_admissible_l_with_equality, m.choose_stilde)
+
+
+def test_condy_without_relative_residual_fails_pin():
+    m = mutated("cg", "thr = tol / (c * eps * normr / normb)\n    cands",
+                "thr = tol / (c * eps * normr)\n    cands")
+    assert _fails(dec.test_condy_uses_the_relative_residual, m.choose_stilde)
+
+
+def test_condy_first_failure_instead_of_largest_fails_pin():
+    m = mutated("cg", "return max(cands) if cands else 1",
+                "return next((l - 1 for l in range(1, sbar + 1) if l not in cands), sbar) or 1")
+    assert _fails(dec.test_condy_largest_admissible_l_with_equality, m.choose_stilde)
+
+
+def test_condy_empty_set_not_one_fails_pin():
+    m = mutated("cg", "return max(cands) if cands else 1", "return max(cands) if cands else sbar")
+    assert _fails(dec.test_condy_no_admissible_l_gives_one, m.choose_stilde)
+
+
+def test_condy_with_p_norm_fails_records_pin():
+    m = mutated("cg", "normr = math.sqrt(G[1, 1])", "normr = math.sqrt(G[0, 0])")
+    assert dec.check_condy_records(m) > 0
+
+
+def test_newcondy_strict_inequality_fails_boundary_pin():
+    m = mutated("cg", "return gam_next >= tol", "return gam_next > tol")
+    assert _fails(dec.test_newcondy_break_at_equality, m.break_test)
+
+
+def test_newcondy_without_relative_residual_fails_pin():
+    m = mutated("cg", "(c * eps * phi / normb)", "(c * eps * phi)")
+    assert _fails(dec.test_newcondy_break_at_equality, m.break_test)
+
+
+def test_newcondy_with_current_residual_fails_records_pin():
+    m = mutated("cg", "break_test(gam[j + 1], tol, c, eps, phi, normb)",
+                "break_test(gam[j + 1], tol, c, eps, math.sqrt(rr_new), normb)")
+    assert dec.check_break_records(m) > 0
+
+
+def test_newcondy_gamma_index_fails_records_pin():
+    m = mutated("cg", "gam = {l: kap[l + 1] for l in range(1, stilde)}",
+                "gam = {l: kap[l] for l in range(1, stilde)}")
+    assert dec.check_break_records(m) > 0
+
+
+def test_psi_wrong_recurrence_fails_worked_values():
+    m = mutated("cg", "return psi / (psi + beta)", "return psi / (1.0 + beta)")
+    assert _fails(dec.test_psi_recurrence_worked_values, m.psi_update)
+
+
+def test_psi_updated_with_previous_beta_fails_identity():
+    m = mutated("cg", "psi = psi_update(psi, beta)",
+                "psi = psi_update(psi, betas[-1] if betas else 0.0)")
+    assert dec.check_psi_records(m) > 1e-6
+
+
+def test_c_gate_from_first_iteration_fails_pins():
+    m = mutated("cg", "return m + j + 1 > 1", "return m + j + 1 > 0")
+    assert _fails(dec.test_ritz_c_gate, m.uses_ritz_c)
+    assert dec.check_first_ritz_c(m) > 1e-6
+
+
+def test_c_from_stale_psi_fails_first_ritz_pin():
+    m = mutated("cg", "c = c_value(o.c_mode, ritz.lmin, ritz.lmax, psi, o.c_const)",
+                "c = c_value(o.c_mode, ritz.lmin, ritz.lmax, 1.0, o.c_const)")
+    assert dec.check_first_ritz_c(m) > 1e-6
+
+
+def test_kappa_cut_strict_fails_boundary_pin():
+    m = mutated("cg", "w[0] <= kappa_cut * w[-1]", "w[0] < kappa_cut * w[-1]")
+    assert _fails(dec.test_kappa_cut_boundary, m.kappa_estimates)
