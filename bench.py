@@ -92,8 +92,8 @@ FF_OPS_PER_PRODUCT = 13                       # binary32 instructions per pair a
 MPK_FP64_OPS_PER_CELL = {"newton": 17, "monomial": 17, "chebyshev": 19}
 FP64_PEAK_TOPS = 152 * 4 * 32 / 64 * 2.070e9 / 1e12   # binary64 lane ops/s: 4 sub-partitions x 32 lanes / 64 cycles
 # DRAM bytes per cell and level of stencil_mpk_grid_kernel (read + write),
-# from the one-pass ncu capture of two levels of the 160^3 case
-# (profiles/stencil_mpk_varcoef3d_160.md): 242.9 MB per launch / 4,096,000
+# from a one-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
+# of two levels of the 160^3 case: 242.9 MB per launch / 4,096,000 cells
 MPK_DRAM_BYTES_PER_CELL = 59.30
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -111,6 +111,8 @@ def parse_args():
     ap.add_argument("--cpu-outer", type=int, default=3, help="outer loops in the oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--gram64-steps", type=int, default=2,
+                    help="solves timed with the binary64 FMA Gram beside the line (0: skip)")
     ap.add_argument("--max-outer", type=int, default=0, help="cap outer loops (profiling runs only)")
     ap.add_argument("--s-max", type=int, default=0,
                     help="override the workload's s_max (sigma) for studies; 0 keeps the configuration's")
@@ -147,6 +149,65 @@ def time_oracle_sample(op, b, x0, cfg, n_outer):
     _, info = cg.sstep_cg(A, b, x0, cfg["tol"], opts)
     el = time.perf_counter() - t
     return el, info["outer"], info["inner"]
+
+
+def measure_fp64_peak(torch, dev):
+    """FP64 peak of this GPU measured in this run: cuBLAS DGEMM 4096^3 (best of
+    5, CUDA events).  GB300's FP64 tensor path (DMMA) and its FP64 FMA share one
+    FP64 unit per sub-partition, so DGEMM's rate is the part's FP64 ceiling."""
+    m = 4096
+    a = torch.randn(m, m, dtype=torch.float64, device=dev)
+    bm = torch.randn(m, m, dtype=torch.float64, device=dev)
+    c = a @ bm
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c = a @ bm
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    del a, bm, c
+    tf = 2.0 * m ** 3 / best / 1e12
+    return tf, f"measured in this run: cuBLAS DGEMM {m}^3, best of 5 ({tf:.3f} TFLOP/s)"
+
+
+def oracle_full_solve_rates(reps=5):
+    """Full oracle solves of the 64^2 Poisson workload (the small configuration
+    the oracle finishes in well under a second), timed on the host cores in a
+    fresh interpreter: single-thread (BLAS/OpenMP pinned to one thread) and on
+    all cores.  Returns {mode: {value (solves/s), cores, seconds per solve}}."""
+    code = ("import json, sys, time\n"
+            f"sys.path.insert(0, {ROOT!r})\n"
+            "from oracle import cg\n"
+            "from oracle.operators import as_matrix\n"
+            "from sscg_inputs import generators as gen\n"
+            "op, b, x0, _ = gen.config_problem('poisson2d_64')\n"
+            "A = as_matrix(op)\n"
+            "o = cg.Options(smax=8, basis='chebyshev')\n"
+            "cg.sstep_cg(A, b, x0, 1e-10, o)\n"
+            "ts = []\n"
+            f"for _ in range({reps}):\n"
+            "    t = time.perf_counter(); x, info = cg.sstep_cg(A, b, x0, 1e-10, o); ts.append(time.perf_counter() - t)\n"
+            "ts.sort()\n"
+            "print(json.dumps(dict(seconds=ts[len(ts) // 2], outer=info['outer'], inner=info['inner'], "
+            "status=info['status'])))\n")
+    out = {}
+    for mode, threads in (("single_thread", 1), ("all_cores", os.cpu_count() or 1)):
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = str(threads)
+        try:
+            r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            out[mode] = {"value": 1.0 / d["seconds"], "unit": "solves/s", "cores": threads,
+                         "seconds_per_solve": d["seconds"], "outer_loops": d["outer"], "inner_iters": d["inner"],
+                         "status": d["status"], "sample": f"median of {reps} complete solves"}
+        except (OSError, ValueError, IndexError, KeyError, subprocess.TimeoutExpired) as e:
+            out[mode] = {"value": None, "error": repr(e)[:200]}
+    return out
 
 
 class ClockSampler:
@@ -232,14 +293,16 @@ def run_reference(args, cfg):
     per_outer = statistics.median(times)
     full_outer = counts["sstep_outer"] if counts else None
     value = 1.0 / (per_outer * full_outer) if full_outer else None
-    sample = (f"{n_outer} outer loops of the full-size solve per step, scaled by the oracle's own full-solve "
-              f"outer-loop count ({full_outer}, tests/golden/oracle_counts.json)")
+    sample = (f"PROJECTED, not timed solves: each step times {n_outer} outer loops of the full-size oracle "
+              f"solve, scaled by the oracle's own full-solve outer-loop count ({full_outer}, "
+              f"tests/golden/oracle_counts.json); complete solves of the small 64^2 case are timed in "
+              f"full_solves_64x64_poisson")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_outer * (full_outer or 0) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["desc"], "s_max": cfg["smax"], "basis": cfg["basis"], "tol": cfg["tol"]},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "full_solves_64x64_poisson": oracle_full_solve_rates()},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -515,11 +578,12 @@ def main():
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
 
-    def solve(profile=1):
+    def solve(profile=0, gram_mode=None):
         x.zero_()
         extra = {"max_outer": args.max_outer} if args.max_outer > 0 else {}
-        if args.gram_mode:
-            extra["gram_mode"] = args.gram_mode
+        gm = args.gram_mode if gram_mode is None else gram_mode
+        if gm:
+            extra["gram_mode"] = gm
         return solver.solve(b, x, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], hist_cap=20000,
                             profile=profile, **extra)
 
@@ -527,10 +591,11 @@ def main():
         solve()
     torch.cuda.synchronize()
 
-    # ---- timed region: K complete solves, per-phase CUDA events inside each.
-    # A working set below twice the L2 (129 MB) would stay cached from one solve
-    # to the next, so then L2 is flushed (a 256 MB write) between the timed
-    # solves, outside the events.
+    # ---- timed region: K complete solves on the production path (one CUDA
+    # graph launch per solve, the loop decided on the device, one host wait).
+    # A working set below twice the L2 (129 MB) would stay cached from one
+    # solve to the next, so then L2 is flushed (a 256 MB write) between the
+    # timed solves, outside the events.
     y_bytes = 8.0 * n * (2 * cfg["smax"] + 1)
     flush = None
     if y_bytes + bytes_a < 2 * L2_BYTES:
@@ -562,63 +627,65 @@ def main():
     clocks = clk.summary()
     ok = all(s.status == 0 and s.true_relres <= cfg["tol"] for s in stats)
     ms_per_step = elapsed / args.steps * 1e3
-
-    # rooflines of the Gram (tensor cores in gram_mode 2, else the FP64 or
-    # FP32 pipes) and of the matrix powers (FP64 issue); the slower phase's
-    # kernel is the one reported
-    t_gram = sum(s.t_gram_ms for s in stats) / 1e3
-    f_gram = sum(s.gram_flops for s in stats)
-    n_gram = sum(s.n_gram_launches for s in stats)
-    t_mpk = sum(s.t_mpk_ms for s in stats) / 1e3
-    phase_ms = {k: sum(getattr(s, "t_" + k + "_ms") for s in stats) / args.steps
-                for k in ("mpk", "gram", "kappa", "control", "recombine", "other")}
-    gram_tflops = f_gram / t_gram / 1e12 if t_gram > 0 else None
     st0 = stats[-1]
     hist = pkg.sscg.history(st0)
     alg_bytes = sum(algorithmic_bytes_per_outer(n, h["sbar"], bytes_a) for h in hist)
     hbm_gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
-    # DRAM traffic of a Gram launch, from the ncu capture of the 96^3 case
-    # (profiles/gram_partial_varcoef3d_96.md): 8 B per row and column read once
-    # plus 3.4 MB of block partials; scaled here by the rows and columns each
-    # launch of this run processed (stencil workloads only)
-    gram_traffic = None
-    if hist and hasattr(op, "kx"):
-        gram_traffic = sum(8.0 * n * (2 * h["sbar"] + 1) + 3.4e6 for h in hist) / len(hist)
     launches = sum(s.kernel_launches for s in stats)
+
+    # ---- one more solve, untimed by the line's value: direct launches with
+    # CUDA events on the library's stream around every phase (the per-kernel
+    # durations of the rooflines below come from it)
+    if flush is not None:
+        flush.add_(1)
+    sp = solve(profile=1)
+    torch.cuda.synchronize()
+    hist_p = pkg.sscg.history(sp)
+    phase_ms = {k: getattr(sp, "t_" + k + "_ms") for k in ("mpk", "gram", "kappa", "control", "recombine", "other")}
+    t_gram = sp.t_gram_ms / 1e3
+    f_gram = sp.gram_flops
+    n_gram = sp.n_gram_launches
+    gram_tflops = f_gram / t_gram / 1e12 if t_gram > 0 else None
+    fp64_peak, fp64_note = measure_fp64_peak(torch, dev)
+    gram_traffic = None
+    if hist_p and hasattr(op, "kx"):
+        gram_traffic = sum(8.0 * n * (2 * h["sbar"] + 1) + 3.4e6 for h in hist_p) / len(hist_p)
+    traffic_src = ("scaled from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel "
+                   "on a smaller or earlier case, by the rows and columns each launch processes; not measured "
+                   "in this run")
     # the matrix-powers phase: binary64 issue bound (stencil workloads)
     mpk_roof = None
     if hasattr(op, "kx") and op.kz is not None and phase_ms["mpk"] > 0:
         ops = MPK_FP64_OPS_PER_CELL.get(cfg["basis"], 17)
         # s-bar levels per outer loop; the last one advances the P chain only
-        lane_ops = sum(n * ops * (h["sbar"] - 0.5) for h in hist)
-        levels = sum(h["sbar"] for h in hist)
+        lane_ops = sum(n * ops * (h["sbar"] - 0.5) for h in hist_p)
+        levels = sum(h["sbar"] for h in hist_p)
         mpk_tops = lane_ops / (phase_ms["mpk"] / 1e3) / 1e12
+        peak_ops = fp64_peak / 2.0   # one FMA = 2 flop = one lane operation
         mpk_roof = {"bound": "alu", "kernel": "stencil_mpk_grid_kernel (one matrix-powers level, both chains)",
-                    "achieved": mpk_tops, "peak": FP64_PEAK_TOPS, "unit": "T binary64 lane-ops/s",
-                    "frac": mpk_tops / FP64_PEAK_TOPS,
+                    "achieved": mpk_tops, "peak": peak_ops, "unit": "T binary64 lane-ops/s",
+                    "frac": mpk_tops / peak_ops,
                     "traffic": (MPK_DRAM_BYTES_PER_CELL * n) if MPK_DRAM_BYTES_PER_CELL else None,
-                    "launches": levels,
+                    "traffic_source": traffic_src, "launches": levels,
                     "algorithmic": f"{ops} binary64 lane operations per cell and level",
-                    "peak_note": "derived: 152 SMs x 4 sub-partitions x 32 lanes per 64 cycles x 2070 MHz "
-                                 "(one binary64 instruction holds its sub-partition's unit 64 cycles)"}
+                    "peak_note": fp64_note + " (as lane operations: TFLOP/s / 2)",
+                    "timing": "CUDA events around the matrix-powers phase of a profiled solve"}
     if args.gram_mode == 0:
         roofline = {"bound": "alu", "kernel": "gram_partial+gram_reduce (G = Y^T Y, FP64)",
-                    "achieved": gram_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": (gram_tflops / FP64_PEAK_TFLOPS) if gram_tflops else None,
-                    "traffic": gram_traffic, "launches": n_gram,
-                    "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 is not in "
-                                 "MEASURED_PEAKS.json)"}
+                    "achieved": gram_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": (gram_tflops / fp64_peak) if gram_tflops else None,
+                    "traffic": gram_traffic, "traffic_source": traffic_src, "launches": n_gram,
+                    "peak_note": fp64_note}
     elif args.gram_mode == 2:
         # digit Gram: executed f16 MMA flops (tiles x 78 MMAs per 16 rows) per
         # second of the Gram phase (which includes the chunk-exponent pass)
-        dg_flop = sum(n * dg_tiles(2 * h["sbar"] + 1) * DG_MMA_FLOP_PER_ROW_TILE for h in hist)
-        t_solve_gram = t_gram / max(1, len(stats))
-        dg_tf = dg_flop / t_solve_gram / 1e12 if t_solve_gram > 0 else None
+        dg_flop = sum(n * dg_tiles(2 * h["sbar"] + 1) * DG_MMA_FLOP_PER_ROW_TILE for h in hist_p)
+        dg_tf = dg_flop / t_gram / 1e12 if t_gram > 0 else None
         roofline = {"bound": "tensor", "kernel": "gram_chunk_exp+gram_partial_dg+gram_reduce (G = Y^T Y, "
                                                   "exact 5-bit digit products on f16 tensor cores)",
                     "achieved": dg_tf, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": (dg_tf / BF16_PEAK_TFLOPS) if dg_tf else None,
-                    "traffic": gram_traffic, "launches": n_gram,
+                    "traffic": gram_traffic, "traffic_source": traffic_src, "launches": n_gram,
                     "gram_fp64_equiv_tflops": gram_tflops,
                     "peak_note": f"{BF16_PEAK_SRC} bf16 burst {BF16_PEAK_TFLOPS:.0f} TFLOP/s (same nominal dense rate "
                                  "as f16); mma.sync f16 measured 604 TFLOP/s on this part"}
@@ -629,7 +696,7 @@ def main():
         roofline = {"bound": "alu", "kernel": "gram_partial_ff+gram_reduce (G = Y^T Y, binary32 pairs)",
                     "achieved": tinst, "peak": FP32_PEAK_TINST, "unit": "T binary32 inst/s",
                     "frac": (tinst / FP32_PEAK_TINST) if tinst else None,
-                    "traffic": gram_traffic, "launches": n_gram,
+                    "traffic": gram_traffic, "traffic_source": traffic_src, "launches": n_gram,
                     "gram_fp64_equiv_tflops": gram_tflops,
                     "peak_note": "derived: 152 SMs x 128 binary32 lanes/clk x 2070 MHz"}
     # report the dominant phase's kernel; the other one beside it
@@ -638,6 +705,22 @@ def main():
         roofline = dict(mpk_roof, secondary=gram_roof)
     elif mpk_roof is not None:
         roofline = dict(gram_roof, secondary=mpk_roof)
+
+    # ---- the same solve with the binary64 FMA Gram (the method as written)
+    gram64 = None
+    if args.gram_mode != 0 and args.gram64_steps > 0:
+        solve(gram_mode=0)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        gs = [solve(gram_mode=0) for _ in range(args.gram64_steps)]
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gel = g0.elapsed_time(g1) / 1e3
+        gram64 = {"value": args.gram64_steps / gel, "unit": "solves/s", "steps": args.gram64_steps,
+                  "outer_loops": gs[-1].outer_iters, "inner_iters": gs[-1].inner_iters,
+                  "true_relres": gs[-1].true_relres, "converged": all(g.status == 0 for g in gs),
+                  "note": "gram_mode 0: G = Y^T Y by binary64 FMAs, graph path"}
 
     # ---- HSCG on the same GPU
     hs = []
@@ -683,9 +766,10 @@ def main():
         per_outer = el / max(outer, 1)
         cpu = {"value": 1.0 / (per_outer * st0.outer_iters), "unit": "solves/s", "cores": os.cpu_count(),
                "kind": "oracle",
-               "sample": f"first {outer} outer loops of the full-size oracle solve ({el:.1f} s), scaled by the "
-                         f"GPU solve's {st0.outer_iters} outer loops; numpy/OpenBLAS Gram on all cores, "
-                         f"scipy SpMV single-threaded"}
+               "sample": f"PROJECTED, not a timed solve: the first {outer} outer loops of the full-size oracle "
+                         f"solve ({el:.1f} s), scaled by the GPU solve's {st0.outer_iters} outer loops; "
+                         f"numpy/OpenBLAS Gram on all cores, scipy SpMV single-threaded",
+               "full_solves_64x64_poisson": oracle_full_solve_rates()}
 
     if rank == 0:
         line = {
@@ -695,7 +779,9 @@ def main():
             "config": {"workload": cfg["desc"], "s_max": cfg["smax"], "basis": cfg["basis"], "tol": cfg["tol"],
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "l2": l2_note,
-                       "timing": "CUDA events around K solves; per-phase CUDA events inside each solve",
+                       "timing": "CUDA events around K solves on the production path (one graph launch and "
+                                 "one host wait per solve); the phase split and kernel rooflines come from one "
+                                 "extra profiled solve (direct launches, CUDA events around each phase)",
                        "gram": {0: "binary64 FMA", 1: "binary32-pair products, binary64 accumulation",
                                 2: "G at binary64 normwise accuracy or better: every value written as 12 5-bit "
                                    "digits (exact within 2^7 of its column's largest, else rounded at 2^-60 of "
@@ -708,7 +794,10 @@ def main():
             "hbm_gbs_alg": hbm_gbs, "hbm_frac_alg": hbm_gbs / HBM_PEAK_GBS,
             "hbm_peak_note": "measured copy peak (MEASURED_PEAKS.json); algorithmic bytes per outer loop: "
                              "the operator once plus 8 N (4 s-bar + 6)",
-            "phase_ms_per_solve": phase_ms,
+            "phase_ms_profiled_solve": phase_ms,
+            "profiled_solve": {"outer_loops": sp.outer_iters, "inner_iters": sp.inner_iters,
+                               "ms": sum(phase_ms.values()), "host_syncs": sp.host_syncs},
+            "gram_binary64": gram64,
             "hscg": hscg,
             "roofline": roofline,
             "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,

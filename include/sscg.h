@@ -255,7 +255,7 @@ int sscg_autotune(sscg_t h, const double* b, double tol, const int* candidates, 
 int sscg_solve_batch_hscg(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double* x, double tol,
                           int max_iters, int chunk_rows, sscg_batch_stats* stats, void* cuda_stream);
 
-/* Autotuner for the batched solve's tile shapes/* Autotuner for the batched solve's tile shapes (rows per work chunk and per
+/* Autotuner for the batched solve's tile shapes (rows per work chunk and per
  * Gram block, sscg_opts.batch_chunk_rows / batch_gram_rows): for each of the
  * ncand candidates (chunk_rows[i], gram_rows[i]) run sscg_solve_batch on the
  * given batch (same arguments as there; x0 = 0 in a scratch array, b
@@ -320,7 +320,9 @@ int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, 
  * until exit); the call allocates nothing.  n is unlimited; ncols must be in
  * [1, 33], else SSCG_ERR_INVALID_ARG.  The first call on a device looks up the
  * array's device address (with that device current), so make that first call
- * before any stream capture.  All calls on a device share the array: calls
+ * before any stream capture.  That address is kept for the process: do not
+ * call this entry point on a device after a cudaDeviceReset of it (the reset
+ * moves the array).  All calls on a device share the array: calls
  * that overlap on the GPU (other streams, other host threads) race and must
  * be serialised by the caller.  Enqueued on cuda_stream (NULL: legacy
  * default stream); the call does not wait for the result. */

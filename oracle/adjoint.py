@@ -52,3 +52,16 @@ def loss(st, b, x_target):
     A = stencil_matrix(st).toarray()
     x = np.linalg.solve(A, b)
     return float((x - x_target) @ (x - x_target))
+
+
+def csr_value_gradients(A, b, x_target):
+    """(L, x, lam, gval) for L = ||x - x_target||^2 and a CSR matrix A (scipy),
+    dense solves: gval[k] = dL/dA_ij = -lam_i x_j for the k-th stored entry
+    (i, j) (row i of the CSR order), each entry a free parameter."""
+    M = A.toarray()
+    x = np.linalg.solve(M, b)
+    lam = np.linalg.solve(M.T, 2.0 * (x - x_target))
+    L = float((x - x_target) @ (x - x_target))
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    gval = -lam[rows] * x[A.indices]
+    return L, x, lam, gval

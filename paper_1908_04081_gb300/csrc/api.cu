@@ -72,7 +72,8 @@ struct sscg_ctx {
   DevBuf<double> val, s_val, kx, ky, kz, diag;
   // solve storage
   int64_t ld = 0;
-  DevBuf<double> Y, G, partials, rt, b, x, r, p, q, leja;
+  DevBuf<double> Y, G, partials, rt, b, x, r, p, q;
+  const double* leja = nullptr;  // the device's Leja table (not owned)
   DevBuf<int> chunk_exp;  // gram_mode 2 scratch
   DevBuf<SolveState> state;
   DevBuf<sscg_outer_record> hist;
@@ -94,8 +95,7 @@ int init_common(sscg_ctx* h, void* cuda_stream) {
   CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
   CK(cudaMallocHost(&h->host_state, sizeof(SolveState)));
-  CK(h->leja.ensure(kMaxS));
-  CK(launch_leja(h->leja.p, kMaxS, h->stream));
+  CK(leja_table(&h->leja, h->stream));
   CK(h->state.ensure(1));
   CK(h->G.ensure(kMaxCols * kMaxCols));
   return SSCG_OK;
@@ -185,7 +185,7 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
                   ds->glmax, sigma, st));
   ++count;
   if ((rc = mark(3))) return rc;
-  CK(launch_control(ds, h->G.p, kMaxCols, h->leja.p, h->hist.n ? h->hist.p : nullptr, st));
+  CK(launch_control(ds, h->G.p, kMaxCols, h->leja, h->hist.n ? h->hist.p : nullptr, st));
   ++count;
   if ((rc = mark(4))) return rc;
   CK(launch_recombine(ds, h->Y.p, h->ld, h->x.p, y32 ? h->r.p : nullptr, y32 ? h->p.p : nullptr, h->n, y32, st));
@@ -543,7 +543,6 @@ void sscg_destroy(sscg_t h) {
   h->r.release();
   h->p.release();
   h->q.release();
-  h->leja.release();
   h->state.release();
   h->hist.release();
   if (h->host_state) cudaFreeHost(h->host_state);
@@ -576,15 +575,14 @@ int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg
   const int64_t n = h->n;
   CK(cudaMemcpyAsync(h->b.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(h->x.p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  // configuration -> device state (through the pinned mirror; the copy is
-  // complete before the mirror is touched again, see the syncs below)
-  CK(cudaStreamSynchronize(st));
+  // configuration -> device state, as a kernel argument (no host wait); the
+  // pinned mirror keeps a copy for the host-side choices below
   fill_state_config(*h->host_state, sigma, tol, (int)basis, o, hist_cap);
-  CK(cudaMemcpyAsync(h->state.p, h->host_state, sizeof(SolveState), cudaMemcpyHostToDevice, st));
+  CK(launch_set_state(h->state.p, *h->host_state, st));
   CK(launch_init_state(h->state.p, h->op, h->b.p, h->x.p, h->Y.p, h->ld, y32 ? h->r.p : nullptr,
                        y32 ? h->p.p : nullptr, h->partials.p, reduce_blocks(n), y32, st));
-  int launches = 2;
-  int host_syncs = 1;
+  int launches = 3;
+  int host_syncs = 0;
 
   const bool prof = o.profile != 0;
   const bool graph = o.use_graph && !prof;
@@ -722,17 +720,16 @@ int sscg_solve_hscg(sscg_t h, const double* b, double* x, double tol, int max_it
   if ((rc = join_in(h))) return rc;
   CK(cudaMemcpyAsync(h->b.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(h->x.p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CK(cudaStreamSynchronize(st));
   SolveState& hs = *h->host_state;
   std::memset(&hs, 0, sizeof(hs));
   hs.tol = tol;
   hs.status = SSCG_NOT_CONVERGED;
   hs.h_max_iters = max_iters > 0 ? max_iters : 100000;
   hs.max_outer = hs.h_max_iters;
-  CK(cudaMemcpyAsync(h->state.p, h->host_state, sizeof(SolveState), cudaMemcpyHostToDevice, st));
+  CK(launch_set_state(h->state.p, hs, st));
   const int nb = reduce_blocks(n);
   CK(launch_hscg_init(h->state.p, h->op, h->b.p, h->x.p, h->r.p, h->p.p, h->partials.p, nb, st));
-  int launches = 2, host_syncs = 1;
+  int launches = 3, host_syncs = 0;
   // Iterations run inside one graph: WHILE (not done) { 8 iterations, then the
   // true-residual confirmation }.  Kernels of iterations past convergence exit
   // at once.
@@ -790,17 +787,15 @@ int sscg_solve_hscg(sscg_t h, const double* b, double* x, double tol, int max_it
     cudaGraphExecDestroy(ge);
     return cuda_fail(el, "hscg graph launch");
   }
-  CK(cudaMemcpyAsync(h->host_state, h->state.p, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  cudaGraphExecDestroy(ge);
-  ++host_syncs;
-  launches += 1 + ((h->host_state->h_iters + per_check - 1) / per_check + 1) * body_kernels;
   CK(launch_final_norm(h->state.p, h->op, h->b.p, h->x.p, h->rt.p, h->partials.p, nb, st));
   CK(cudaMemcpyAsync(x, h->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(h->host_state, h->state.p, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  const cudaError_t es = cudaStreamSynchronize(st);
+  cudaGraphExecDestroy(ge);
+  CK(es);
   ++host_syncs;
   const SolveState s = *h->host_state;
+  launches += 1 + ((s.h_iters + per_check - 1) / per_check + 1) * body_kernels;
   if ((rc = join_out(h))) return rc;
   if (stats) {
     stats->status = s.status;
@@ -865,11 +860,12 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
   DevBuf<BatchPair> d_pairs;
   DevBuf<int> d_cp, d_gp;
   DevBuf<SolveState> d_st;
-  DevBuf<double> d_G, d_Y, d_part, d_rt, d_leja;
+  DevBuf<double> d_G, d_Y, d_part, d_rt;
+  const double* d_leja = nullptr;
   DevBuf<unsigned int> d_cnt;
   auto release = [&]() {
     d_pairs.release(); d_cp.release(); d_gp.release(); d_st.release(); d_G.release(); d_Y.release();
-    d_part.release(); d_rt.release(); d_leja.release(); d_cnt.release();
+    d_part.release(); d_rt.release(); d_cnt.release();
   };
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr, t0 = nullptr, t1 = nullptr;
@@ -895,7 +891,6 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
     BK(d_Y.ensure((size_t)LD * (2 * sigma_max + 1)));
     BK(d_part.ensure(std::max(gblk_pair.size() * (size_t)kMaxPairs, chunk_pair.size())));
     BK(d_rt.ensure(total));
-    BK(d_leja.ensure(kMaxS));
     BK(d_cnt.ensure(2));
     BK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     BK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -909,7 +904,7 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
     BK(cudaMemcpyAsync(d_gp.p, gblk_pair.data(), gblk_pair.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     BK(cudaMemcpyAsync(d_st.p, hs.data(), P * sizeof(SolveState), cudaMemcpyHostToDevice, st));
     BK(cudaMemsetAsync(d_cnt.p, 0, 2 * sizeof(unsigned int), st));
-    BK(launch_leja(d_leja.p, kMaxS, st));
+    BK(leja_table(&d_leja, st));
     BatchView v;
     v.pairs = d_pairs.p;
     v.npairs = P;
@@ -935,7 +930,7 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
         if ((e2 = launch_batch_mpk(v, d_Y.p, LD, l, st)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_gram(v, d_Y.p, LD, d_part.p, st)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_kappa(v, sigma_max, st)) != cudaSuccess) return e2;
-      if ((e2 = launch_batch_control(v, d_leja.p, st)) != cudaSuccess) return e2;
+      if ((e2 = launch_batch_control(v, d_leja, st)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_recombine(v, d_Y.p, LD, x, st)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_check(v, b, x, d_rt.p, d_Y.p, LD, d_part.p, st)) != cudaSuccess) return e2;
       return launch_batch_end(v, cond, use_cond, st);

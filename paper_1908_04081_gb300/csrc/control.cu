@@ -748,8 +748,7 @@ __global__ void __launch_bounds__(kControlThreads) batch_control_kernel(BatchVie
 // points the log-product is concave, so its maximiser is the zero of the
 // derivative sum 1/(t - t_m), found by bisection to the last bit; the gap with
 // the largest product wins, ties (within 1e-13 in log) go to the smaller t.
-__global__ void leja_kernel(double* out, int s) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void leja_points(double* out, int s) {
   double pts[kMaxS];
   double srt[kMaxS];
   int np = 0;
@@ -799,7 +798,36 @@ __global__ void leja_kernel(double* out, int s) {
   for (int i = 0; i < s; ++i) out[i] = pts[i];
 }
 
+__global__ void leja_kernel(double* out, int s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  leja_points(out, s);
+}
+
+// The process-wide table of the first kMaxS Leja points (every s-bar uses a
+// prefix of it): it lives in this module's device memory, so each device
+// holds its own copy, and a device reset reloads the module with the flag
+// cleared.  The kernel computes the table only while the flag is clear; the
+// flag is set after the points are written, so a later reader on any stream
+// either sees it set with the points in place, or computes them itself.
+__device__ double g_leja[kMaxS];
+__device__ int g_leja_ready;
+
+__global__ void leja_table_kernel() {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (*(volatile int*)&g_leja_ready) return;
+  leja_points(g_leja, kMaxS);
+  __threadfence();
+  *(volatile int*)&g_leja_ready = 1;
+}
+
 }  // namespace
+
+cudaError_t leja_table(const double** table, cudaStream_t st) {
+  leja_table_kernel<<<1, 32, 0, st>>>();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaGetSymbolAddress((void**)table, g_leja);
+}
 
 cudaError_t launch_kappa(const double* G, int ldg, const SolveState* state, int sbar_fixed, double kappa_cut,
                          double* kappa, double* lmin, double* lmax, int grid, cudaStream_t st) {

@@ -889,7 +889,7 @@ cudaError_t launch_batch_gram(const BatchView& v, const double* Y, int64_t LD, d
 
 int gram_blocks(int64_t n) {
   int64_t tiles = (n + kGramTileRows - 1) / kGramTileRows;
-  int64_t b = 152 * 2;
+  int64_t b = kGramMaxBlocks;
   if (tiles < b) b = tiles;
   return b < 1 ? 1 : (int)b;
 }

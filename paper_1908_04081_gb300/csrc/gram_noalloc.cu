@@ -18,15 +18,18 @@
 namespace sscg {
 namespace {
 
-// One partial sum per (block, pair): at most gram_blocks() = 304 blocks, and
-// kMaxPairs = 561 pairs for 33 columns.  The row count does not enter: longer
-// inputs give each block more rows.
-constexpr int kGramNoAllocBlocks = 304;
-constexpr size_t kGramNoAllocDoubles = (size_t)kGramNoAllocBlocks * kMaxPairs;
+// One partial sum per (block, pair): at most gram_blocks() = kGramMaxBlocks
+// blocks, and kMaxPairs = 561 pairs for 33 columns.  The row count does not
+// enter: longer inputs give each block more rows.
+constexpr size_t kGramNoAllocDoubles = (size_t)kGramMaxBlocks * kMaxPairs;
+static_assert(kGramNoAllocDoubles == (size_t)304 * 561, "scratch size stated in include/sscg.h");
 
 static __device__ __align__(256) double g_gram_scratch[kGramNoAllocDoubles];
 
-// Device address of g_gram_scratch, looked up once per device ordinal.
+// Device address of g_gram_scratch, looked up once per device ordinal.  A
+// device reset (cudaDeviceReset) reloads the module at another address, so
+// the cached pointer is then stale: the entry point must not be used on a
+// device after it was reset.
 constexpr int kMaxDevices = 64;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mu;
@@ -41,7 +44,7 @@ extern "C" int sscg_gram_noalloc(const double* Y, int64_t n, int64_t ldy, int nc
   if (!Y || !G || n <= 0 || ldy < n) return SSCG_ERR_INVALID_ARG;
   if (ncols < 1 || ncols > kMaxCols) return SSCG_ERR_INVALID_ARG;  // scratch holds partials for <= 33 columns
   const int nb = gram_blocks(n);
-  if (nb > kGramNoAllocBlocks || (size_t)nb * kMaxPairs > kGramNoAllocDoubles) return SSCG_ERR_INVALID_ARG;
+  if (nb > kGramMaxBlocks || (size_t)nb * kMaxPairs > kGramNoAllocDoubles) return SSCG_ERR_INVALID_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SSCG_ERR_CUDA;
   double* scratch = nullptr;

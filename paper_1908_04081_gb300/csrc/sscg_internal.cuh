@@ -20,6 +20,7 @@ constexpr int kMaxCols = 2 * kMaxS + 1;                    // 33
 constexpr int kMaxPairs = kMaxCols * (kMaxCols + 1) / 2;   // 561
 constexpr int kGramThreads = 576;                          // >= kMaxPairs, multiple of 32
 constexpr int kGramTileRows = 128;
+constexpr int kGramMaxBlocks = 152 * 2;   // most thread blocks (and partial sums per pair) of one Gram
 
 // ---------------------------------------------------------------- operator
 // A sparse SPD operator: a CSR matrix or a 2D/3D face-coefficient stencil.
@@ -116,6 +117,8 @@ struct SolveState {
   double h_rr, h_pq, h_alpha, h_beta;
   int h_iters, h_max_iters;
 };
+static_assert(sizeof(SolveState) % sizeof(unsigned int) == 0, "SolveState is copied as 32-bit words");
+static_assert(sizeof(SolveState) <= 4000, "SolveState travels as a kernel argument");
 
 // ----------------------------------------------------------------- launchers
 // operator kernels (ops_stencil.cu / ops_csr.cu)
@@ -158,6 +161,9 @@ cudaError_t launch_kappa(const double* G, int ldg, const SolveState* state, int 
 cudaError_t launch_control(SolveState* state, const double* G, int ldg, const double* leja,
                            sscg_outer_record* hist, cudaStream_t st);
 cudaError_t launch_leja(double* t, int s, cudaStream_t st);
+// the device's table of the first kMaxS Leja points (computed on `st` by the
+// first call on a device, a no-op kernel afterwards) and its device address
+cudaError_t leja_table(const double** table, cudaStream_t st);
 
 // vec.cu
 // Basis storage: y32 = false: Y is double and columns 0/1 are p and r
@@ -251,5 +257,7 @@ cudaError_t launch_batch_hscg_check(const BatchView& v, const double* b, const d
 cudaError_t launch_batch_end(const BatchView& v, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
 cudaError_t launch_batch_arm(cudaGraphConditionalHandle cond, cudaStream_t st);
 cudaError_t launch_solve_cond(const SolveState* state, cudaGraphConditionalHandle cond, cudaStream_t st);
+// *state = config, by a kernel on `st` (the configuration travels as a kernel argument)
+cudaError_t launch_set_state(SolveState* state, const SolveState& config, cudaStream_t st);
 
 }  // namespace sscg

@@ -627,6 +627,15 @@ __global__ void batch_cond_kernel(BatchView v, cudaGraphConditionalHandle cond) 
 
 // Loop condition of a single solve's graph: repeat the outer loop until the
 // device has set done (convergence, breakdown, stagnation or the outer-loop cap).
+// The configuration of a solve, passed by value: the host writes no device
+// memory it would have to wait for before the solve's first kernel.
+__global__ void set_state_kernel(SolveState* __restrict__ dst, const SolveState src) {
+  const int nw = (int)(sizeof(SolveState) / sizeof(unsigned int));
+  const unsigned int* s = reinterpret_cast<const unsigned int*>(&src);
+  unsigned int* d = reinterpret_cast<unsigned int*>(dst);
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) d[i] = s[i];
+}
+
 __global__ void solve_cond_kernel(const SolveState* st, cudaGraphConditionalHandle cond) {
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
 }
@@ -891,6 +900,11 @@ cudaError_t launch_batch_end(const BatchView& v, cudaGraphConditionalHandle cond
   const int g = (v.npairs + 255) / 256;
   batch_end_kernel<<<g < 1 ? 1 : g, 256, 0, st>>>(v);
   if (use_cond) batch_cond_kernel<<<1, 32, 0, st>>>(v, cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(SolveState* state, const SolveState& config, cudaStream_t st) {
+  set_state_kernel<<<1, 128, 0, st>>>(state, config);
   return cudaGetLastError();
 }
 

@@ -425,6 +425,112 @@ def test_hscg_matches_oracle(pkg, name):
     assert err <= 1e-8
 
 
+@pytest.mark.parametrize("case", ["poisson32", "varcoef12"])
+@pytest.mark.parametrize("tol,status,replacements", [(1e-15, 0, 1), (1e-16, 3, 2)])
+def test_residual_replacement_and_stagnation_stop(pkg, case, tol, status, replacements):
+    """Reading C16 forced on the GPU.  tol = 1e-15 sits just above these
+    systems' attainable accuracy: the updated residual reaches tol first, the
+    true residual does not, r := b - A x, p := r (one replacement), and the
+    solve then converges.  tol = 1e-16 is below it: the second failed check
+    has not halved the true residual, so the solve stops NOT_CONVERGED after
+    two replacements.  Status and replacement counts equal the oracle's (and
+    those of a second oracle run that sums G in another order: the outcome is
+    not a rounding accident); the same for HSCG."""
+    if case == "poisson32":
+        A = gen.poisson2d_csr(32)
+        M = as_matrix(A)
+        b = gen.random_rhs(A.n, 9)
+        s = pkg.Solver.csr(A.rowptr, A.col, A.val)
+    else:
+        st_ = gen.varcoef_stencil((12, 10, 9), seed=11)
+        M = as_matrix(st_)
+        b = gen.random_rhs(st_.n, 12)
+        s = stencil_solver(pkg, st_)
+    n = b.size
+
+    def chunked(Y):
+        G = np.zeros((Y.shape[1], Y.shape[1]))
+        for i in range(0, Y.shape[0], 97):
+            G += Y[i:i + 97].T @ Y[i:i + 97]
+        return G
+
+    outs = []
+    for g in (None, chunked):
+        _, info = cg.sstep_cg(M, b, np.zeros(n), tol, cg.Options(smax=8, basis="newton", gram=g))
+        outs.append((info["status"], info["replacements"]))
+    assert outs == [(status, replacements)] * 2, outs
+    for gram_mode in (0, 2):
+        xt = dev(np.zeros(n))
+        st = s.solve(dev(b), xt, tol=tol, s_max=8, basis="newton", gram_mode=gram_mode)
+        assert (st.status, st.replacements) == (status, replacements), (gram_mode, st.status, st.replacements)
+        x = xt.cpu().numpy()
+        rel = np.linalg.norm(b - M @ x) / np.linalg.norm(b)
+        if status == 0:   # recomputed on the CPU: rounding of the residual itself is ~1e-16
+            assert st.true_relres <= tol and rel <= 2 * tol, (st.true_relres, rel)
+    _, h = cg.hscg(M, b, np.zeros(n), tol)
+    xt = dev(np.zeros(n))
+    hs = s.hscg(dev(b), xt, tol=tol)
+    assert (hs.status, hs.replacements) == (h["status"], h["replacements"])
+
+
+def test_kappa_estimates_up_to_the_cut(pkg):
+    """kappa over the whole finite range, up to the cut of reading C14
+    (lambda_min = 2^-44 lambda_max, kappa = 2^22 ~ 4.2e6): Gram matrices with
+    prescribed spectra Q diag(lambda) Q^T.  A backward-stable eigensolver
+    (LAPACK's, or the GPU's Householder + Sturm) finds lambda_min to an
+    absolute error of a few eps lambda_max, so kappa agrees to
+    1e-8 + 4e-14 kappa^2 relative (2e-2 at kappa = 1e6, 0.7 at 4.2e6); both stay
+    finite, and both agree with the exact kappa to the same bound."""
+    rng = np.random.default_rng(23)
+    for sbar in (4, 8, 16):
+        ncols = 2 * sbar + 1
+        for kap_target in (1e3, 1e5, 1e6, 2e6, 3.5e6, 4.0e6):
+            Q, _ = np.linalg.qr(rng.standard_normal((ncols, ncols)))
+            lam = np.sort(rng.uniform(0.1, 1.0, ncols))
+            lam[-1] = 1.0
+            lam[0] = 1.0 / kap_target ** 2
+            G = (Q * lam) @ Q.T
+            G = 0.5 * (G + G.T)
+            kap_o, lmin_o, lmax_o = cg.kappa_estimates(G, sbar)
+            kap = torch.zeros(sbar + 1, dtype=torch.float64, device="cuda")
+            lmn = torch.zeros_like(kap)
+            lmx = torch.zeros_like(kap)
+            pkg.sscg.sscg_kappa(dev(G.ravel()), ncols, sbar, 2.0 ** -44, kap, lmn, lmx)
+            kap, lmn, lmx = kap.cpu().numpy(), lmn.cpu().numpy(), lmx.cpu().numpy()
+            k_full = kap[sbar]
+            bound = 1e-8 + 4e-14 * kap_target ** 2
+            assert math.isfinite(kap_o[sbar]) and math.isfinite(k_full), (sbar, kap_target, kap_o[sbar], k_full)
+            assert abs(k_full - kap_o[sbar]) <= bound * kap_o[sbar], (sbar, kap_target, k_full, kap_o[sbar])
+            assert abs(k_full - kap_target) <= bound * kap_target, (sbar, kap_target, k_full)
+            for l in range(1, sbar + 1):
+                assert abs(lmx[l] - lmax_o[l]) <= 1e-13 * lmax_o[l]
+                assert abs(lmn[l] - lmin_o[l]) <= 2e-14 * lmax_o[l]
+                kl = kap_o[l]
+                if math.isinf(kl) or math.isinf(kap[l]):
+                    assert math.isinf(kl) and math.isinf(kap[l]), (l, kl, kap[l])
+                else:
+                    assert abs(kap[l] - kl) <= (1e-8 + 4e-14 * kl * kl) * kl, (l, kap[l], kl)
+
+
+def check_x_sample(x, name):
+    """||x - x_oracle|| / ||x_oracle|| on the oracle's stored sample of rows of
+    its full-size solution (tests/golden/make_oracle_counts.py), and the full
+    norms; returns (sample error, norm error) or None when not recorded."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_counts.json")
+    if not os.path.exists(path):
+        return None
+    ref = json.load(open(path)).get(name)
+    if not ref or "x_sample" not in ref:
+        return None
+    idx = np.array(ref["x_sample_idx"])
+    xo = np.array(ref["x_sample"])
+    err = np.linalg.norm(x[idx] - xo) / np.linalg.norm(xo)
+    nerr = abs(np.linalg.norm(x) - ref["x_norm"]) / ref["x_norm"]
+    return err, nerr
+
+
 def test_not_converged_cap(pkg):
     st_ = gen.varcoef_stencil((16, 16, 16), seed=3)
     b = gen.random_rhs(st_.n, 2)
@@ -466,6 +572,10 @@ def test_full_size_varcoef3d_160(pkg, gram_mode):
         if ref:
             assert abs(st.outer_iters - ref["sstep_outer"]) <= 0.1 * ref["sstep_outer"]
             assert abs(st.inner_iters - ref["sstep_inner"]) <= 0.1 * ref["sstep_inner"]
+    chk = check_x_sample(x, "varcoef3d_160")
+    if chk is not None:
+        print(f"x vs oracle (sample of 4096 rows): {chk[0]:.3e}, norms {chk[1]:.3e}")
+        assert chk[0] <= 1e-8 and chk[1] <= 1e-8, chk
 
 
 @pytest.mark.parametrize("gram_mode", [2, 0])
@@ -494,6 +604,10 @@ def test_full_size_rgg_2m(pkg, gram_mode):
         assert relres <= 1e-10, (y32, relres)
         xs[y32], sts[y32] = x, st
     assert np.linalg.norm(xs[1] - xs[0]) <= 1e-7 * np.linalg.norm(xs[0])
+    chk = check_x_sample(xs[0], "rgg_2m")
+    if chk is not None:
+        print(f"x vs oracle (sample of 4096 rows): {chk[0]:.3e}, norms {chk[1]:.3e}")
+        assert chk[0] <= 1e-8 and chk[1] <= 1e-8, chk
     hist = pkg.sscg.history(sts[0])
     _, info = cg.sstep_cg(A, b, x0, 1e-10, cg.Options(smax=16, basis="newton", max_outer=3))
     dec_g = [(h["sbar"], h["stilde"], h["sk"]) for h in hist[:3]]

@@ -40,3 +40,30 @@ def test_b_gradient_is_adjoint_state():
         bm[i] -= h
         fd = (adjoint.loss(st, bp, xt) - adjoint.loss(st, bm, xt)) / (2 * h)
         assert abs(fd - lam[i]) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_csr_value_gradients_match_central_differences():
+    # each stored entry of a small RGG Laplacian (diagonally scaled, SPD) is a
+    # free parameter; perturbing one entry alone gives a non-symmetric matrix,
+    # solved densely in both the finite difference and the adjoint
+    prob = gen.rgg_laplacian_csr(300, 7)
+    A = prob.scipy()
+    b = gen.random_rhs(A.shape[0], 1)
+    xt = gen.random_rhs(A.shape[0], 2)
+    L, x, lam, gval = adjoint.csr_value_gradients(A, b, xt)
+    M = A.toarray()
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    rng = np.random.default_rng(4)
+
+    def loss_of(Mp):
+        xp = np.linalg.solve(Mp, b)
+        return float((xp - xt) @ (xp - xt))
+
+    for k in rng.choice(A.nnz, 12, replace=False):
+        i, j = rows[k], A.indices[k]
+        h = 1e-5 * abs(M[i, j])
+        Mp, Mm = M.copy(), M.copy()
+        Mp[i, j] += h
+        Mm[i, j] -= h
+        fd = (loss_of(Mp) - loss_of(Mm)) / (2 * h)
+        assert abs(fd - gval[k]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(gval).max()), (i, j, fd, gval[k])
