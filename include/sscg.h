@@ -87,6 +87,12 @@ typedef struct {
   int batch_chunk_rows;  /* sscg_solve_batch only: rows per work chunk of the row kernels (matrix powers,
                             recombination, residual checks); 0 = 2048, else 128..1048576 */
   int batch_gram_rows;   /* sscg_solve_batch only: rows per Gram block; 0 = 2048, else 128..1048576 */
+  int mpk_fp64_per16;    /* stencil matrix-powers levels with a binary64 basis: of every 16 warps, this many
+                            form each cell's (A - theta I) v - mu v' as the binary64 FMA chain and the others
+                            as exact integer products summed exactly and rounded once (both binary64-accurate;
+                            the two share the level between GB300's FP64 unit and its integer pipes);
+                            16 = FMA chain only, 0 = integer products only; default -1 = the library's
+                            tuned share */
 } sscg_opts;
 
 /* Per-outer-loop decision record (Alg. 5): s-bar_k, s-tilde_k, s_k, c at the
@@ -284,6 +290,13 @@ int sscg_spmv(sscg_t h, const double* v, double* y);
  * leading dimension ldy >= n, 2s+1 columns, written.  1 <= s <= SSCG_MAX_S. */
 int sscg_build_basis(sscg_t h, const double* p, const double* r, int s, const double* theta,
                const double* gamma, const double* mu, double* Y, int64_t ldy);
+
+/* sscg_build_basis with the split of sscg_opts.mpk_fp64_per16 for stencil
+ * operators (0..16 warps of every 16 on the binary64 FMA chain, the others on
+ * exact integer products; -1: the library's default).  Outside -1..16:
+ * SSCG_ERR_INVALID_ARG. */
+int sscg_build_basis_ex(sscg_t h, const double* p, const double* r, int s, const double* theta,
+                        const double* gamma, const double* mu, double* Y, int64_t ldy, int mpk_fp64_per16);
 
 /* G = Y^T Y (Section 2, the block inner product of Alg. 5), Y device column
  * major n x ncols with leading dimension ldy, G device ncols x ncols row major

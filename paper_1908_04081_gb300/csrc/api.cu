@@ -83,6 +83,7 @@ struct sscg_ctx {
   int graph_sigma = -1;
   bool graph_y32 = false;
   int graph_gram_mode = 0;
+  int graph_mpk_split = -1;
   int graph_launches = 0;
   double last_lmin = 0.0, last_lmax = 0.0;
 };
@@ -173,7 +174,7 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
   int rc;
   if ((rc = mark(0))) return rc;
   for (int l = 0; l < sigma; ++l) {
-    CK(launch_mpk_level(h->op, h->Y.p, h->ld, l, ds, 0, coef, y32, st));
+    CK(launch_mpk_level(h->op, h->Y.p, h->ld, l, ds, 0, coef, y32, st, h->host_state->mpk_fp64_per16));
     ++count;
   }
   if ((rc = mark(1))) return rc;
@@ -208,7 +209,8 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
 // The whole solve loop as one graph: a kernel arms the loop condition, then a
 // WHILE node repeats one outer loop until the device sets done.
 int build_graph(sscg_ctx* h, int sigma, bool y32) {
-  if (h->graph && h->graph_sigma == sigma && h->graph_y32 == y32 && h->graph_gram_mode == h->host_state->gram_mode)
+  if (h->graph && h->graph_sigma == sigma && h->graph_y32 == y32 && h->graph_gram_mode == h->host_state->gram_mode &&
+      h->graph_mpk_split == h->host_state->mpk_fp64_per16)
     return SSCG_OK;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
@@ -261,6 +263,7 @@ int build_graph(sscg_ctx* h, int sigma, bool y32) {
   h->graph_sigma = sigma;
   h->graph_y32 = y32;
   h->graph_gram_mode = h->host_state->gram_mode;
+  h->graph_mpk_split = h->host_state->mpk_fp64_per16;
   h->graph_launches = nl + 1;
   return SSCG_OK;
 }
@@ -289,6 +292,7 @@ void fill_state_config(SolveState& s, int sigma, double tol, int basis, const ss
   s.psi = 1.0;
   s.fp32_drop = std::ldexp(1.0, -4);  // FP32 basis: replace r after a 2^-4 drop
   s.gram_mode = o.gram_mode;
+  s.mpk_fp64_per16 = o.mpk_fp64_per16;
   s.rho_last = 1.0;
   for (int l = 0; l < kMaxS; ++l) {
     s.theta[l] = 0.0;  // monomial basis until Ritz values exist
@@ -306,6 +310,7 @@ int validate_opts(const sscg_opts& o) {
   if (o.batch_gram_rows != 0 && (o.batch_gram_rows < 128 || o.batch_gram_rows > (1 << 20)))
     return SSCG_ERR_INVALID_ARG;
   if (!(o.eps > 0.0) || !(o.kappa_cut >= 0.0)) return SSCG_ERR_INVALID_ARG;
+  if (o.mpk_fp64_per16 < -1 || o.mpk_fp64_per16 > 16) return SSCG_ERR_INVALID_ARG;
   return SSCG_OK;
 }
 
@@ -353,6 +358,7 @@ void sscg_opts_default(sscg_opts* o) {
   o->gram_mode = 0;
   o->batch_chunk_rows = 0;
   o->batch_gram_rows = 0;
+  o->mpk_fp64_per16 = -1;
 }
 
 int sscg_create_csr(sscg_t* out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
@@ -1339,8 +1345,14 @@ int sscg_spmv(sscg_t h, const double* v, double* y) {
 
 int sscg_build_basis(sscg_t h, const double* p, const double* r, int s, const double* theta, const double* gamma,
                const double* mu, double* Y, int64_t ldy) {
+  return sscg_build_basis_ex(h, p, r, s, theta, gamma, mu, Y, ldy, -1);
+}
+
+int sscg_build_basis_ex(sscg_t h, const double* p, const double* r, int s, const double* theta,
+                        const double* gamma, const double* mu, double* Y, int64_t ldy, int mpk_fp64_per16) {
   if (!h || !p || !r || !theta || !gamma || !mu || !Y || s < 1 || s > kMaxS || ldy < h->n)
     return SSCG_ERR_INVALID_ARG;
+  if (mpk_fp64_per16 < -1 || mpk_fp64_per16 > 16) return SSCG_ERR_INVALID_ARG;
   double coef[3 * kMaxS];
   for (int l = 0; l < s; ++l) {
     if (!(gamma[l] != 0.0)) return SSCG_ERR_INVALID_ARG;
@@ -1357,7 +1369,7 @@ int sscg_build_basis(sscg_t h, const double* p, const double* r, int s, const do
   CK(cudaMemcpyAsync(Y, p, h->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(Y + ldy, r, h->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   LevelCoef lc{dc.p, dc.p + kMaxS, dc.p + 2 * kMaxS};
-  for (int l = 0; l < s; ++l) CK(launch_mpk_level(h->op, Y, ldy, l, nullptr, s, lc, false, st));
+  for (int l = 0; l < s; ++l) CK(launch_mpk_level(h->op, Y, ldy, l, nullptr, s, lc, false, st, mpk_fp64_per16));
   CK(cudaStreamSynchronize(st));
   if ((rc = join_out(h))) return rc;
   dc.release();

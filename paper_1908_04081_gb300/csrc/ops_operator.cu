@@ -12,6 +12,7 @@
 // mu term is skipped (uniform branch) when mu = 0.  Every lane of a warp does
 // the same FP64 work (boundary neighbours read as 0 by predication), because
 // masked lanes do not free FP64 issue slots.
+#include "exact_sum.cuh"
 #include "sscg_internal.cuh"
 
 namespace sscg {
@@ -226,6 +227,163 @@ __global__ void __launch_bounds__(256) stencil_mpk_grid_kernel(Operator A, T* __
     }
     if (mu != 0.0) acc = fma(-mu, ld_val(Y + (int64_t)(2 * level - 1) * ld + i), acc);
     Rn[i] = (T)(acc * ig);
+  }
+}
+
+// The binary64 FMA chain of one cell and chain of a matrix-powers level, from
+// global memory (the rare cells whose integer form does not apply: Inf/NaN
+// inputs, or a sum outside the normal binary64 range).  Kept out of line so
+// that the integer path does not hold its operands in registers.
+template <bool DIM3>
+__device__ __noinline__ double mpk_cell_fma(const Operator& A, const double* __restrict__ Vl,
+                                            const double* __restrict__ Vm, int64_t i, int x, int yy, int z,
+                                            double ds, double mu) {
+  double w = stencil_apply<DIM3>(A, Vl, i, x, yy, z, ds);
+  if (mu != 0.0) w = fma(-mu, __ldg(Vm + i), w);
+  return w;
+}
+
+// One matrix-powers level for a stencil with a binary64 basis, its binary64
+// work split between two units: of every 16 warps, `fp64_per16` form their
+// cells' sums as the binary64 FMA chain of stencil_mpk_grid_kernel, the others
+// with exact integer products (exact_sum.cuh: the 5 or 7 stencil products,
+// and the mu term, summed exactly and rounded once, then times 1/gamma in
+// binary64).  GB300's FP64 unit and its integer pipes run concurrently, so
+// the level's time falls towards that of the slower share.  Both forms are
+// binary64-accurate (the integer one more so); a cell's result depends only
+// on which form its warp takes, which depends only on the warp's position, so
+// results are reproducible.  Inf or NaN among a cell's inputs, or a sum
+// outside the normal binary64 range, sends that cell to the FMA chain.
+template <bool DIM3>
+__global__ void __launch_bounds__(256, 4) stencil_mpk_hybrid_kernel(Operator A, double* __restrict__ Y, int64_t ld,
+                                                                      int level, const SolveState* __restrict__ st,
+                                                                      int sbar_fixed, LevelCoef coef, int fp64_per16) {
+  int sbar = sbar_fixed;
+  if (sbar <= 0) {
+    if (st->done) return;
+    sbar = st->sbar;
+  }
+  const bool doP = level < sbar;
+  const bool doR = level + 1 < sbar;
+  if (!doP) return;
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+  const int x = x0 + tx, yy = y0 + ty, z = blockIdx.z;
+  __shared__ double sv[2][10][34];   // P_l, R_l tiles (halo included, zero outside the domain)
+  __shared__ int2 lv[2][10][34];     // their limbs a, b
+  __shared__ int ev[2][10][34];      // and exponents
+  const int64_t zoff = (int64_t)z * ny * nx;
+  unsigned bad = 0;
+  for (int e = ty * 32 + tx; e < 340; e += 256) {
+    const int ly = e / 34, lx = e - ly * 34;
+    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    const int64_t gi = (int64_t)(2 * level) * ld + zoff + (int64_t)gy * nx + gx;
+    const double vp = in ? __ldg(Y + gi) : 0.0;
+    const double vr = in && doR ? __ldg(Y + gi + ld) : 0.0;
+    sv[0][ly][lx] = vp;
+    sv[1][ly][lx] = vr;
+    const Limbs lp = to_limbs(vp, bad), lr = to_limbs(vr, bad);
+    lv[0][ly][lx] = make_int2(lp.a, lp.b);
+    ev[0][ly][lx] = lp.e;
+    lv[1][ly][lx] = make_int2(lr.a, lr.b);
+    ev[1][ly][lx] = lr.e;
+  }
+  const int tile_bad = __syncthreads_or((int)bad);
+  if (x >= nx || yy >= ny) return;
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t i = zoff + (int64_t)yy * nx + x;
+  const int64_t fx = ((int64_t)z * ny + yy) * (nx + 1) + x;
+  const int64_t fy = ((int64_t)z * (ny + 1) + yy) * nx + x;
+  const double theta = coef.theta[level];
+  const double ig = coef.inv_gamma[level];
+  const double mu = level >= 1 ? coef.mu[level - 1] : 0.0;
+  const double ds = __ldg(A.diag + i) - theta;
+  const int ly = ty + 1, lx = tx + 1;
+  const unsigned warp = ((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * 8u + (unsigned)ty;
+  const bool fma_warp = ((warp * (unsigned)fp64_per16) & 15u) < (unsigned)fp64_per16;
+  if (fma_warp || tile_bad) {
+    // the binary64 FMA chain (the form and order of stencil_mpk_grid_kernel)
+    const double kw = -__ldg(A.kx + fx), ke = -__ldg(A.kx + fx + 1);
+    const double ks = -__ldg(A.ky + fy), kn = -__ldg(A.ky + fy + nx);
+    const double kd = DIM3 ? -__ldg(A.kz + i) : 0.0, ku = DIM3 ? -__ldg(A.kz + i + plane) : 0.0;
+#pragma unroll 1
+    for (int ch = 0; ch < (doR ? 2 : 1); ++ch) {
+      const double* Vl = Y + (int64_t)(2 * level + ch) * ld;
+      double acc = ds * sv[ch][ly][lx];
+      acc = fma(kw, sv[ch][ly][lx - 1], acc);
+      acc = fma(ke, sv[ch][ly][lx + 1], acc);
+      acc = fma(ks, sv[ch][ly - 1][lx], acc);
+      acc = fma(kn, sv[ch][ly + 1][lx], acc);
+      if (DIM3) {
+        acc = fma(kd, z > 0 ? __ldg(Vl + i - plane) : 0.0, acc);
+        acc = fma(ku, z < nz - 1 ? __ldg(Vl + i + plane) : 0.0, acc);
+      }
+      if (mu != 0.0) acc = fma(-mu, __ldg(Y + (int64_t)(2 * level - 2 + ch) * ld + i), acc);
+      Y[(int64_t)(2 * level + 2 + ch) * ld + i] = acc * ig;
+    }
+    return;
+  }
+  // exact integer products: coefficients -k_f and (diag - theta), shared by both chains
+  constexpr int K = DIM3 ? 7 : 5;
+  unsigned cbad = 0;
+  Limbs c[K + 1];
+  c[0] = to_limbs(ds, cbad);
+  c[1] = to_limbs<true>(__ldg(A.kx + fx), cbad);
+  c[2] = to_limbs<true>(__ldg(A.kx + fx + 1), cbad);
+  c[3] = to_limbs<true>(__ldg(A.ky + fy), cbad);
+  c[4] = to_limbs<true>(__ldg(A.ky + fy + nx), cbad);
+  if (DIM3) {
+    c[5] = to_limbs<true>(__ldg(A.kz + i), cbad);
+    c[6] = to_limbs<true>(__ldg(A.kz + i + plane), cbad);
+  }
+  c[K] = to_limbs<true>(mu, cbad);
+  const int nterm = mu != 0.0 ? K + 1 : K;
+#pragma unroll 1
+  for (int ch = 0; ch < (doR ? 2 : 1); ++ch) {
+    const double* Vl = Y + (int64_t)(2 * level + ch) * ld;
+    unsigned ybad = cbad;
+    Limbs yz[3];   // the global operands: z - 1, z + 1 and the mu term's value
+    yz[0] = to_limbs(DIM3 && z > 0 ? __ldg(Vl + i - plane) : 0.0, ybad);
+    yz[1] = to_limbs(DIM3 && z < nz - 1 ? __ldg(Vl + i + plane) : 0.0, ybad);
+    yz[2] = to_limbs(mu != 0.0 ? __ldg(Y + (int64_t)(2 * level - 2 + ch) * ld + i) : 0.0, ybad);
+    // exponent sums first, then the aligned products
+    const int e0 = ev[ch][ly][lx], e1 = ev[ch][ly][lx - 1], e2 = ev[ch][ly][lx + 1];
+    const int e3 = ev[ch][ly - 1][lx], e4 = ev[ch][ly + 1][lx];
+    int E[K + 1];
+    E[0] = c[0].e + e0;
+    E[1] = c[1].e + e1;
+    E[2] = c[2].e + e2;
+    E[3] = c[3].e + e3;
+    E[4] = c[4].e + e4;
+    if (DIM3) {
+      E[5] = c[5].e + yz[0].e;
+      E[6] = c[6].e + yz[1].e;
+    }
+    E[K] = c[K].e + yz[2].e;
+    int Em = 0;
+#pragma unroll
+    for (int j = 0; j < K + 1; ++j)
+      if (j < nterm) Em = E[j] > Em ? E[j] : Em;
+    long long S = 0;
+    auto add = [&](int j, const Limbs& y) { S += shift_down(limb_product(c[j], y), Em - E[j] + 3); };
+    int2 t;
+    t = lv[ch][ly][lx];     add(0, Limbs{t.x, t.y, e0});
+    t = lv[ch][ly][lx - 1]; add(1, Limbs{t.x, t.y, e1});
+    t = lv[ch][ly][lx + 1]; add(2, Limbs{t.x, t.y, e2});
+    t = lv[ch][ly - 1][lx]; add(3, Limbs{t.x, t.y, e3});
+    t = lv[ch][ly + 1][lx]; add(4, Limbs{t.x, t.y, e4});
+    if (DIM3) {
+      add(5, yz[0]);
+      add(6, yz[1]);
+    }
+    if (mu != 0.0) add(K, yz[2]);
+    bool ok = true;
+    double w = to_binary64(S, Em, ok);
+    if (!ok || ybad)
+      w = mpk_cell_fma<DIM3>(A, Vl, Y + (int64_t)(2 * level - 2 + ch) * ld, i, x, yy, z, ds, mu);
+    Y[(int64_t)(2 * level + 2 + ch) * ld + i] = w * ig;
   }
 }
 
@@ -525,7 +683,7 @@ cudaError_t launch_residual(const Operator& A, const double* b, const double* x,
 }
 
 cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level, const SolveState* state,
-                             int sbar_fixed, LevelCoef coef, bool y32, cudaStream_t st) {
+                             int sbar_fixed, LevelCoef coef, bool y32, cudaStream_t st, int fp64_per16) {
   int g = grid_for(A.n, 4);
   if (y32) {
     float* Yf = static_cast<float*>(Y);
@@ -541,16 +699,23 @@ cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level, 
                                                                                   sbar_fixed, coef);
   } else {
     double* Yd = static_cast<double*>(Y);
+    const int f16 = fp64_per16 < 0 ? kMpkFp64Per16 : fp64_per16;
     if (A.kind == 0)
       sell_mpk_kernel<double><<<sell_grid(A), kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);
     else if (A.nz > 65535)  // beyond the grid's z extent: grid-stride kernel
       stencil_mpk_kernel<true, double><<<g, kOpThreads, 0, st>>>(A, Yd, ld, level, state, sbar_fixed, coef);
-    else if (A.dim == 3)
+    else if (f16 >= 16 && A.dim == 3)
       stencil_mpk_grid_kernel<true, double><<<cell_grid3(A), dim3(32, 8), 0, st>>>(A, Yd, ld, level, state,
                                                                                   sbar_fixed, coef);
-    else
+    else if (f16 >= 16)
       stencil_mpk_grid_kernel<false, double><<<cell_grid3(A), dim3(32, 8), 0, st>>>(A, Yd, ld, level, state,
                                                                                    sbar_fixed, coef);
+    else if (A.dim == 3)
+      stencil_mpk_hybrid_kernel<true><<<cell_grid3(A), dim3(32, 8), 0, st>>>(A, Yd, ld, level, state, sbar_fixed,
+                                                                            coef, f16);
+    else
+      stencil_mpk_hybrid_kernel<false><<<cell_grid3(A), dim3(32, 8), 0, st>>>(A, Yd, ld, level, state, sbar_fixed,
+                                                                             coef, f16);
   }
   return cudaGetLastError();
 }

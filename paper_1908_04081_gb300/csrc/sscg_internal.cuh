@@ -95,6 +95,7 @@ struct SolveState {
   double fp32_drop, rho_last;
   double prev_fail;   // relative true residual at the last failed convergence check
   int gram_mode;      // 0: binary64 Gram; 1: binary32-pair products; 2: f16 digit products
+  int mpk_fp64_per16; // warps (of 16) on the binary64 FMA chain in stencil levels; -1: library default
   int fp32_replace_pending, fp32_replacements;
   double c, psi, normb, upd_relres;
   // Meurant-Tichy state (Algs. 3-4)
@@ -134,10 +135,14 @@ cudaError_t launch_residual(const Operator& A, const double* b, const double* x,
                             cudaStream_t st, const SolveState* gate = nullptr, int gmode = 0);
 // one matrix-powers level l (computes P_{l+1} and R_{l+1} when within the block size
 // read from st->sbar, or from `sbar_fixed` when > 0, with coefficients from `coef`).
+// Stencil levels with a binary64 basis: fp64_per16 of every 16 warps form the
+// binary64 FMA chain, the others exact integer products (16: FMA chain only;
+// negative: kMpkFp64Per16).
 struct LevelCoef { const double* theta; const double* inv_gamma; const double* mu; };
+constexpr int kMpkFp64Per16 = 6;
 cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level,
                              const SolveState* state, int sbar_fixed, LevelCoef coef, bool y32,
-                             cudaStream_t st);
+                             cudaStream_t st, int fp64_per16 = -1);
 
 // gram.cu
 int gram_blocks(int64_t n);

@@ -34,7 +34,7 @@ class Opts(C.Structure):
                 ("y_fp32", C.c_int), ("variant", C.c_int), ("check_every", C.c_int),
                 ("use_graph", C.c_int), ("profile", C.c_int), ("c_const", C.c_double),
                 ("eps", C.c_double), ("kappa_cut", C.c_double), ("gram_mode", C.c_int),
-                ("batch_chunk_rows", C.c_int), ("batch_gram_rows", C.c_int)]
+                ("batch_chunk_rows", C.c_int), ("batch_gram_rows", C.c_int), ("mpk_fp64_per16", C.c_int)]
 
 
 class OuterRecord(C.Structure):
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sscg_ritz": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "sscg_spmv": (C.c_int, [_P, _P, _P]),
         "sscg_build_basis": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, _P, _I64]),
+        "sscg_build_basis_ex": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, _P, _I64, C.c_int]),
         "sscg_gram": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _P]),
         "sscg_gram_noalloc": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _P]),
         "sscg_gram_ex": (C.c_int, [_P, _I64, _I64, C.c_int, _P, C.c_int, _P]),
@@ -274,12 +275,17 @@ def sscg_spmv(h: int, v, y) -> None:
     _check(load_library().sscg_spmv(h, _f64(v), _f64(y)), "sscg_spmv")
 
 
-def sscg_build_basis(h: int, p, r, s: int, theta, gamma, mu, Y, ldy: int) -> None:
+def sscg_build_basis(h: int, p, r, s: int, theta, gamma, mu, Y, ldy: int, mpk_fp64_per16: int | None = None) -> None:
     th = np.ascontiguousarray(theta, dtype=np.float64)
     ga = np.ascontiguousarray(gamma, dtype=np.float64)
     mu_ = np.ascontiguousarray(mu, dtype=np.float64)
-    _check(load_library().sscg_build_basis(h, _f64(p), _f64(r), s, th.ctypes.data, ga.ctypes.data,
-                                           mu_.ctypes.data, _f64(Y), ldy), "sscg_build_basis")
+    if mpk_fp64_per16 is None:
+        _check(load_library().sscg_build_basis(h, _f64(p), _f64(r), s, th.ctypes.data, ga.ctypes.data,
+                                               mu_.ctypes.data, _f64(Y), ldy), "sscg_build_basis")
+    else:
+        _check(load_library().sscg_build_basis_ex(h, _f64(p), _f64(r), s, th.ctypes.data, ga.ctypes.data,
+                                                  mu_.ctypes.data, _f64(Y), ldy, mpk_fp64_per16),
+               "sscg_build_basis_ex")
 
 
 def sscg_gram(Y, n: int, ldy: int, ncols: int, G, stream=None) -> None:

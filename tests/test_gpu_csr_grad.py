@@ -3,7 +3,8 @@
 The differentiable CSR solve (``autograd.csr_solve``: forward s-step solve,
 adjoint s-step solve, ``sscg_csr_value_grad`` gather) is checked
 - on tiny random-geometric-graph Laplacians against the oracle's dense adjoint
-  (every stored entry, 1e-7 relative to the largest entry), and
+  (every stored entry, 1e-7 relative to the largest entry; solves at tol
+  1e-11, above these systems' attainable accuracy), and
 - on the RGG stand-in (the 2M workload's recipe at N = 20,000, condition ~1e8)
   against central finite differences of the forward map: a symmetric pair of
   entries (A_ij and A_ji move together, so A stays SPD) has derivative
@@ -44,7 +45,7 @@ def test_csr_value_gradient_matches_dense_adjoint(pkg, n, decades, gram_mode):
     L, x_o, lam_o, g_o = oadj.csr_value_gradients(A, b, xt)
     val = dev(P.val).requires_grad_()
     bt = dev(b).requires_grad_()
-    x = csr_solve(dev(P.rowptr, torch.int64), dev(P.col, torch.int32), val, bt, tol=1e-13, s_max=8,
+    x = csr_solve(dev(P.rowptr, torch.int64), dev(P.col, torch.int32), val, bt, tol=1e-11, s_max=8,
                   basis="newton", gram_mode=gram_mode)
     loss = ((x - dev(xt)) ** 2).sum()
     loss.backward()
@@ -59,14 +60,13 @@ def test_csr_value_gradient_matches_dense_adjoint(pkg, n, decades, gram_mode):
 def test_csr_value_gradient_vs_finite_differences(pkg):
     from paper_1908_04081_gb300.autograd import csr_solve
     P = gen.rgg_laplacian_csr(20000, 1003)
-    A = P.scipy()
     n = P.n
     b = gen.random_rhs(n, 1004)
     xt = gen.random_rhs(n, 1005)
     rp, cl = dev(P.rowptr, torch.int64), dev(P.col, torch.int32)
     val = dev(P.val).requires_grad_()
     bt, xtt = dev(b), dev(xt)
-    tol = 1e-12
+    tol = 1e-11    # this system's attainable accuracy is near 1e-12 (reading C16 stops below it)
     x = csr_solve(rp, cl, val, bt, tol=tol, s_max=16, basis="newton", gram_mode=2)
     loss = ((x - xtt) ** 2).sum()
     loss.backward()
@@ -74,8 +74,6 @@ def test_csr_value_gradient_vs_finite_differences(pkg):
     g = val.grad.cpu().numpy()
     rows = np.repeat(np.arange(n), np.diff(P.rowptr))
     # position of (j, i) for every stored (i, j): the matrix is structurally symmetric
-    At = A.T.tocsr()
-    At.sort_indices()
     key = {(int(i), int(j)): k for k, (i, j) in enumerate(zip(rows, P.col))}
     rng = np.random.default_rng(1006)
     offdiag = np.nonzero(rows != P.col)[0]

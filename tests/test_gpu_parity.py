@@ -144,6 +144,65 @@ def test_basis_columns(pkg, kind, s):
         assert np.linalg.norm(Yg[:, c] - Yo[:, c]) <= 1e-13 * nrm * (1 + c), (kind, s, c)
 
 
+@pytest.mark.parametrize("split", [0, 7, 16])
+@pytest.mark.parametrize("kind", ["newton", "chebyshev"])
+@pytest.mark.parametrize("shape", [(19, 17, 7), (37, 29), (40, 9, 3)])
+def test_basis_columns_integer_products(pkg, shape, kind, split):
+    """The stencil matrix-powers level with every split of its warps between
+    the binary64 FMA chain (16 of 16), exact integer products rounded once
+    (0 of 16) and the library's mixed default: columns against the oracle to
+    the same per-column bound as the FMA chain, inputs spread over 2^+-300
+    with exact zeros and binary64 subnormals included."""
+    st = gen.varcoef_stencil(shape, seed=9)
+    A = as_matrix(st)
+    n = st.n
+    rng = np.random.default_rng(len(shape) * 10 + split)
+    p = rng.standard_normal(n) * 2.0 ** rng.integers(-300, 300, n)
+    r = rng.standard_normal(n)
+    p[rng.integers(0, n, n // 10)] = 0.0
+    r[rng.integers(0, n, n // 10)] = 0.0
+    r[rng.integers(0, n, 20)] = 3e-310        # subnormal
+    s = 8
+    lmax = 2.2 * float(A.diagonal().max())
+    th, ga, mu = obs.basis_params(obs.BASIS_NAMES[kind], s, 0.01 * lmax, lmax)
+    ld = n + 3
+    Y = torch.zeros(ld * (2 * s + 1), dtype=torch.float64, device="cuda")
+    solver = stencil_solver(pkg, st)
+    pkg.sscg.sscg_build_basis(solver.h, dev(p), dev(r), s, th, ga, mu, Y, ld, mpk_fp64_per16=split)
+    Yg = Y.reshape(2 * s + 1, ld)[:, :n].cpu().numpy().T
+    Yo = obs.krylov_basis(A, p, r, s, th, ga, mu)
+    for c in range(2 * s + 1):
+        nrm = np.linalg.norm(Yo[:, c])
+        assert np.linalg.norm(Yg[:, c] - Yo[:, c]) <= 1e-13 * nrm * (1 + c), (kind, split, c)
+
+
+@pytest.mark.parametrize("bad", [np.inf, np.nan])
+def test_basis_integer_products_nonfinite_inputs(pkg, bad):
+    """Inf or NaN among a cell's inputs sends it to the binary64 FMA chain: the
+    all-integer split gives the same non-finite pattern as the FMA chain, and
+    the finite cells agree to rounding."""
+    st = gen.varcoef_stencil((33, 20, 6), seed=4)
+    n = st.n
+    rng = np.random.default_rng(8)
+    p, r = rng.standard_normal(n), rng.standard_normal(n)
+    p[1234] = bad
+    r[77] = -bad if bad == np.inf else bad
+    s = 3
+    th, ga, mu = obs.basis_params(obs.BASIS_NAMES["newton"], s, 0.1, 20.0)
+    solver = stencil_solver(pkg, st)
+    out = {}
+    for split in (0, 16):
+        Y = torch.zeros(n * (2 * s + 1), dtype=torch.float64, device="cuda")
+        pkg.sscg.sscg_build_basis(solver.h, dev(p), dev(r), s, th, ga, mu, Y, n, mpk_fp64_per16=split)
+        out[split] = Y.reshape(2 * s + 1, n).cpu().numpy()
+    a, b = out[0], out[16]
+    assert np.array_equal(np.isnan(a), np.isnan(b)) and np.array_equal(np.isinf(a), np.isinf(b))
+    fin = np.isfinite(b)
+    assert fin.sum() > 0.5 * b.size
+    assert np.max(np.abs(a[fin] - b[fin]) / (np.abs(b[fin]) + 1e-300)) <= 1e-12 or \
+        np.linalg.norm(a[fin] - b[fin]) <= 1e-13 * np.linalg.norm(b[fin])
+
+
 @pytest.mark.parametrize("n,ncols", [(1, 1), (31, 3), (1000, 17), (10007, 33), (300000, 33), (777, 2)])
 def test_gram(pkg, n, ncols):
     rng = np.random.default_rng(n + ncols)
