@@ -83,7 +83,9 @@ typedef struct {
                             256-row tiles, binary64 across tiles; 2: every value written as 12 signed
                             5-bit digits after a per-4096-row-chunk power-of-two column scale, all digit
                             products on the f16 tensor cores with exact binary32 sums over 1024 rows,
-                            binary64 across them (normwise error below binary64 FMAs'); default 0 */
+                            binary64 across them (normwise error below binary64 FMAs'); 3: the arithmetic of
+                            mode 2 run as tcgen05.mma with the sums in tensor memory (the same G up to the
+                            order of the final binary64 additions); default 0 */
   int batch_chunk_rows;  /* sscg_solve_batch only: rows per work chunk of the row kernels (matrix powers,
                             recombination, residual checks); 0 = 2048, else 128..1048576 */
   int batch_gram_rows;   /* sscg_solve_batch only: rows per Gram block; 0 = 2048, else 128..1048576 */
@@ -318,9 +320,11 @@ int sscg_gram(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, voi
  * (normwise error below binary64 FMAs'; componentwise, an entry made only of
  * products far below the two columns' largest values keeps just that
  * absolute accuracy); a column with an Inf or NaN in a chunk gives NaN
- * entries.  Mode 2 also allocates an integer scratch of 33 entries per 4096
- * rows.  Same arguments and allocation behaviour as sscg_gram otherwise; mode
- * outside 0..2: SSCG_ERR_INVALID_ARG. */
+ * entries.  Mode 3 is mode 2's arithmetic on the 5th-generation tensor
+ * cores (tcgen05.mma, accumulators in tensor memory).  Modes 2 and 3 also
+ * allocate an integer scratch of 33 entries per 4096 rows.  Same arguments
+ * and allocation behaviour as sscg_gram otherwise; mode outside 0..3:
+ * SSCG_ERR_INVALID_ARG. */
 int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, int mode, void* cuda_stream);
 
 /* Same result as sscg_gram, for callers that cannot allocate device memory
@@ -340,6 +344,14 @@ int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, 
  * be serialised by the caller.  Enqueued on cuda_stream (NULL: legacy
  * default stream); the call does not wait for the result. */
 int sscg_gram_noalloc(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, void* cuda_stream);
+
+/* Whether a bounded wait inside a kernel of this library gave up since the
+ * flag was last cleared (the gram_mode 3 kernel's hand-offs between its
+ * warps: each wait ends after about a second, records the failure and lets
+ * the kernel finish, so a result computed after it is not to be trusted).
+ * Synchronises the current device, writes 0 or 1 to *flag (host) and
+ * clears the flag when `clear` is nonzero. */
+int sscg_wait_failures(int* flag, int clear);
 
 /* kappa_l ~ sqrt(kappa(G_l)) for the leading (2l+1) blocks of G, l = 1..sbar
  * (Section 3), from the extreme eigenvalues of each block.  G: device,

@@ -180,7 +180,7 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
   if ((rc = mark(1))) return rc;
   CK(launch_gram(h->Y.p, h->n, h->ld, nullptr, 0, ds, h->partials.p, gram_blocks(h->n), h->G.p, kMaxCols, y32,
                  st, h->host_state->gram_mode, h->chunk_exp.p));
-  count += h->host_state->gram_mode == 2 ? 3 : 2;
+  count += h->host_state->gram_mode >= 2 ? 3 : 2;
   if ((rc = mark(2))) return rc;
   CK(launch_kappa(h->G.p, kMaxCols, ds, 0, 0.0 /* taken from the state */, ds->kappa, ds->glmin,
                   ds->glmax, sigma, st));
@@ -304,7 +304,7 @@ void fill_state_config(SolveState& s, int sigma, double tol, int basis, const ss
 
 int validate_opts(const sscg_opts& o) {
   if (o.c_mode < 0 || o.c_mode > SSCG_C_CONST) return SSCG_ERR_INVALID_ARG;
-  if (o.gram_mode < 0 || o.gram_mode > 2) return SSCG_ERR_INVALID_ARG;
+  if (o.gram_mode < 0 || o.gram_mode > 3) return SSCG_ERR_INVALID_ARG;
   if (o.batch_chunk_rows != 0 && (o.batch_chunk_rows < 128 || o.batch_chunk_rows > (1 << 20)))
     return SSCG_ERR_INVALID_ARG;
   if (o.batch_gram_rows != 0 && (o.batch_gram_rows < 128 || o.batch_gram_rows > (1 << 20)))
@@ -1389,7 +1389,7 @@ int sscg_gram(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, voi
 }
 
 int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, int mode, void* cuda_stream) {
-  if (!Y || !G || n <= 0 || ldy < n || ncols < 1 || ncols > kMaxCols || mode < 0 || mode > 2)
+  if (!Y || !G || n <= 0 || ldy < n || ncols < 1 || ncols > kMaxCols || mode < 0 || mode > 3)
     return SSCG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int nb = gram_blocks(n);
@@ -1397,10 +1397,17 @@ int sscg_gram_ex(const double* Y, int64_t n, int64_t ldy, int ncols, double* G, 
   DevBuf<double> part;
   DevBuf<int> cexp;
   CK(part.ensure((size_t)nb * kMaxPairs));
-  if (mode == 2) CK(cexp.ensure((size_t)gram_exp_ints(n)));
+  if (mode >= 2) CK(cexp.ensure((size_t)gram_exp_ints(n)));
   CK(launch_gram(Y, n, ldy, nullptr, ncols, nullptr, part.p, nb, G, ncols, false, st, mode, cexp.p));
   CK(cudaStreamSynchronize(st));
   part.release();
+  return SSCG_OK;
+}
+
+int sscg_wait_failures(int* flag, int clear) {
+  if (!flag) return SSCG_ERR_INVALID_ARG;
+  CK(cudaDeviceSynchronize());
+  CK(gram_tc_error(flag, clear != 0));
   return SSCG_OK;
 }
 

@@ -779,6 +779,425 @@ gram_partial_dg_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
   }
 }
 
+// ------------------------------------------------------------------------
+// The digit Gram on the 5th-generation tensor cores (gram_mode = 3).
+//
+// Columns 0..31: the arithmetic of gram_mode 2 (the same 60-bit integers per
+// value and chunk, the same 12 signed 5-bit digits as f16 subnormals, exact
+// binary32 sums of digit products, combined in two 64-bit integers per entry
+// and added in binary64; here once per 4096-row scale chunk, since each
+// accumulator sums a single plane pair), run as tcgen05.mma (kind::f16,
+// M = N = 128, K = 16, f32 accumulators in tensor memory) issued by one
+// thread.  Since H_u = sum_{s+t=u} D_s^T D_t (D_s the digit plane s of the
+// columns) is symmetric, it is formed from the pairs s <= t only:
+//   H_u = sum_{s<t, s+t=u} (X_st + X_st^T) + [u even] X_{u/2,u/2},
+//   X_st = D_s^T D_t,
+// 42 plane pairs.  Each MMA takes four consecutive planes on each side (A:
+// planes a..a+3 x 32 columns = 128 rows, B: planes b..b+3 = 128 columns), so
+// block (k, l) of its 128 x 128 accumulator is X_{a+k, b+l}; the four
+// accumulators (a, b) = (0, 0), (0, 4), (0, 8), (4, 4) hold every pair with
+// s <= t and s + t <= 11, and fill tensor memory (4 x 128 columns).  Four
+// MMAs per 16 rows; 42 of the 64 plane-pair blocks computed are used.
+// Column 32 (ncols = 33): its 33 entries are binary64 FMA sums (the FP64
+// unit is otherwise idle here), formed by three warps from Y in global memory.
+//
+// Shared memory holds each 64-row stage in the no-swizzle canonical K-major
+// layout: the 16-byte unit of 8 rows of (plane, column) at
+// [8-row block][plane][column] (LBO = one 8-row block, 6,144 bytes; SBO = 128
+// bytes between groups of 8 operand rows).
+//
+// Warp roles (512 threads): warp 0 allocates tensor memory and one of its
+// threads issues the MMAs; warps 1..3 the column-32 dot products; warps 4..7
+// the epilogue of each scale chunk (tcgen05.ld reaches lane quadrant w % 4
+// from warp w); warps 8..15 stage and convert the rows (the conversion of
+// gram_mode 2).  Hand-offs are mbarriers: full[b] (conversion -> MMA, per
+// stage buffer), empty[b] (tcgen05.commit -> conversion), tfull
+// (tcgen05.commit -> epilogue), tempty (epilogue -> MMA, before a block's
+// first MMA overwrites the accumulators).  Every wait gives up after about a
+// second of clock cycles, records the failure in g_gram_tc_error and lets the
+// block finish (G is then not to be trusted; the flag is the error report).
+constexpr int kTcStageRows = 64;
+constexpr int kTcKB = kTcStageRows / 8;
+constexpr int kTcCols = 32;
+constexpr uint32_t kTcCore = 128;                                      // 8 rows x 16 bytes
+constexpr uint32_t kTcPlaneBytes = (kTcCols / 8) * kTcCore;            // 512: one plane of 32 columns
+constexpr uint32_t kTcKBBytes = kDgPlanes * kTcPlaneBytes;             // 6,144: LBO
+constexpr uint32_t kTcStage = kTcKB * kTcKBBytes;                      // 49,152
+constexpr int kTcThreads = 512;
+constexpr int kTcC32W0 = 1, kTcEpi0 = 4, kTcConv0 = 8;                 // first column-32 / epilogue / conversion warp
+constexpr uint32_t kTcTmemCols = 512;
+constexpr int kTcAcc = 4;                                              // accumulators (a, b)
+__device__ __constant__ int kTcAccA[kTcAcc] = {0, 0, 0, 4};
+__device__ __constant__ int kTcAccB[kTcAcc] = {0, 4, 8, 4};
+static_assert(kTcStageRows == kDgStageRows, "the conversion of gram_mode 2 is reused");
+template <typename T>
+constexpr size_t tc_smem_bytes() { return 2 * (size_t)kTcStage + 2 * dg_raw_bytes<T>(); }   // 133,152 for binary64
+
+__device__ int g_gram_tc_error;   // set when a wait of gram_partial_tc_kernel gave up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major; start, LBO and SBO in
+// 16-byte units, descriptor version 1 (bits 46-47) for tcgen05
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: f32 accumulator (bits 4-5 = 1), A and
+// B f16 (0), both K-major, N / 8 at bits 17-22, M / 16 at bits 24-28
+constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+               "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+// wait for the phase of the given parity to complete, for about a second at
+// most; a give-up is recorded (block-wide, so later waits return at once)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+    if (ok) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > 2000000000ll) {
+      *abort = 1;
+      atomicOr(&g_gram_tc_error, 1);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// 16 consecutive accumulator columns of this warp's lane quadrant (raw bits)
+__device__ __forceinline__ void tc_ld16(uint32_t (&r)[16], uint32_t taddr) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// the 12 digit planes of 8 rows of one column into the 16-byte units
+// unit + t * plane_stride (two f16 bit patterns per word, row 2w in the low half)
+__device__ __forceinline__ void tc_store8(const double (&v)[8], int ce, unsigned char* unit, uint32_t plane_stride) {
+  unsigned h[8], l[8], sg[4];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const unsigned long long F = dg_fixed(v[k], ce);
+    h[k] = (unsigned)(F >> 32);
+    l[k] = (unsigned)F;
+  }
+#pragma unroll
+  for (int w = 0; w < 4; ++w)
+    sg[w] = (((unsigned)((unsigned long long)__double_as_longlong(v[2 * w]) >> 63)) << 15) |
+            (((unsigned)((unsigned long long)__double_as_longlong(v[2 * w + 1]) >> 63)) << 31);
+#define TC_PLANE(t)                                                                                       \
+  *reinterpret_cast<uint4*>(unit + (t) * plane_stride) =                                                  \
+      make_uint4(dg_digit<t>(h[0], l[0]) | (dg_digit<t>(h[1], l[1]) << 16) | sg[0],                       \
+                 dg_digit<t>(h[2], l[2]) | (dg_digit<t>(h[3], l[3]) << 16) | sg[1],                       \
+                 dg_digit<t>(h[4], l[4]) | (dg_digit<t>(h[5], l[5]) << 16) | sg[2],                       \
+                 dg_digit<t>(h[6], l[6]) | (dg_digit<t>(h[7], l[7]) << 16) | sg[3]);
+  TC_PLANE(0) TC_PLANE(1) TC_PLANE(2) TC_PLANE(3) TC_PLANE(4) TC_PLANE(5)
+  TC_PLANE(6) TC_PLANE(7) TC_PLANE(8) TC_PLANE(9) TC_PLANE(10) TC_PLANE(11)
+#undef TC_PLANE
+}
+
+// conversion of one stage into stage buffer `stage` (thread assignment of
+// dg_convert: column 8 (cw % 4) + lane % 8 and 8-row block 4 (cw / 4) + lane / 8)
+template <typename T>
+__device__ __forceinline__ void tc_convert(const T* raw, unsigned char* stage, const int* __restrict__ ce_g,
+                                           int ncols, int cw) {
+  constexpr int LD = dg_raw_ld<T>();
+  const int lane = threadIdx.x & 31;
+  const int c = 8 * (cw & 3) + (lane & 7), kb = 4 * (cw >> 2) + (lane >> 3);
+  if (c < ncols) {
+    const T* src = raw + c * LD + 8 * kb;
+    double v[8];
+    if (sizeof(T) == 8) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double2 p = reinterpret_cast<const double2*>(src)[k];
+        v[2 * k] = p.x;
+        v[2 * k + 1] = p.y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float4 p = reinterpret_cast<const float4*>(src)[k];
+        v[4 * k] = widen(p.x);
+        v[4 * k + 1] = widen(p.y);
+        v[4 * k + 2] = widen(p.z);
+        v[4 * k + 3] = widen(p.w);
+      }
+    }
+    tc_store8(v, __ldg(ce_g + c), stage + kb * kTcKBBytes + c * 16, kTcPlaneBytes);
+  }
+}
+
+// Each accumulator sums one plane pair: below 961 R for R rows, exact in
+// binary32 up to R = 17,458, so the block sums are read out once per scale
+// chunk (4096 rows), where the scales change.
+constexpr int kTcFlushShift = kDgChunkShift;
+static_assert((1 << kTcFlushShift) * 961 < (1 << 24), "exact binary32 sums of one plane pair");
+
+// whether stage rows r0..r0+63 end a flush block within [.., r_end)
+__device__ __forceinline__ bool tc_block_end(int64_t r0, int64_t r_end) {
+  const int64_t r1 = r0 + kTcStageRows;
+  return r1 >= r_end || (r1 >> kTcFlushShift) != (r0 >> kTcFlushShift);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTcThreads, 1)
+gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const SolveState* __restrict__ st,
+                       int ncols_fixed, const int* __restrict__ cexp, double* __restrict__ partials, bool vec16) {
+  int ncols = ncols_fixed;
+  if (ncols <= 0) {
+    if (st->done) return;
+    ncols = 2 * st->sbar + 1;
+  }
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const bool c32 = ncols > kTcCols;
+  const int np = ncols * (ncols + 1) / 2;
+  const int nct = ncols < kTcCols ? ncols : kTcCols;   // columns on the tensor cores
+
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  T* raw[2] = {reinterpret_cast<T*>(tc_smem + 2 * kTcStage),
+               reinterpret_cast<T*>(tc_smem + 2 * kTcStage + dg_raw_bytes<T>())};
+  __shared__ __align__(8) uint64_t bars[7];          // full[2], empty[2], tfull, tempty, drain
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ unsigned long long s_hi[kMaxPairs], s_lo[kMaxPairs];
+  __shared__ double gacc[kMaxPairs];
+  __shared__ double c32sum[3][kMaxCols];
+  const uint32_t b_full = smem_addr(&bars[0]), b_empty = smem_addr(&bars[2]);
+  const uint32_t b_tfull = smem_addr(&bars[4]), b_tempty = smem_addr(&bars[5]), b_drain = smem_addr(&bars[6]);
+
+  const int64_t nst_all = (n + kTcStageRows - 1) / kTcStageRows;
+  const int64_t spb = (nst_all + gridDim.x - 1) / gridDim.x;
+  const int64_t r_begin = (int64_t)blockIdx.x * spb * kTcStageRows;
+  int64_t r_end = r_begin + spb * kTcStageRows;
+  if (r_end > n) r_end = n;
+  const int64_t nst = r_begin < r_end ? (r_end - r_begin + kTcStageRows - 1) / kTcStageRows : 0;
+
+  // both stage buffers zero (columns >= ncols are never written)
+  for (int e = t; e < (int)(2 * kTcStage / 16); e += kTcThreads)
+    reinterpret_cast<uint4*>(tc_smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+  for (int e = t; e < kMaxPairs; e += kTcThreads) {
+    s_hi[e] = 0ull;
+    s_lo[e] = 0ull;
+    gacc[e] = 0.0;
+  }
+  if (t == 0) {
+    abort_flag = 0;
+    mbar_init(b_full, 8);   // one arrival per conversion warp
+    mbar_init(b_full + 8, 8);
+    mbar_init(b_empty, 1);
+    mbar_init(b_empty + 8, 1);
+    mbar_init(b_tfull, 1);
+    mbar_init(b_tempty, 4);   // one arrival per epilogue warp
+    mbar_init(b_drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(kTcTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int* abort = &abort_flag;
+
+  if (warp >= kTcConv0) {
+    // ---- conversion warps (as in gram_partial_dg_kernel; buffer b = k & 1)
+    const int cw = warp - kTcConv0;
+    dg_issue_raw(raw[0], Y, ld, r_begin, r_end, nct, cw, vec16);
+    dg_issue_raw(raw[1], Y, ld, r_begin + kTcStageRows, r_end, nct, cw, vec16);
+    for (int64_t k = 0; k < nst; ++k) {
+      const int b = (int)(k & 1);
+      const int64_t r0 = r_begin + k * kTcStageRows;
+      const int* ce_g = cexp + (r0 >> kDgChunkShift) * kMaxCols;
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      if (k >= 2) mbar_wait(b_empty + 8 * b, (uint32_t)(((k - 2) >> 1) & 1), abort);   // MMAs of stage k - 2 done
+      tc_convert(raw[b], tc_smem + (size_t)b * kTcStage, ce_g, nct, cw);
+      dg_issue_raw(raw[b], Y, ld, r0 + 2 * kTcStageRows, r_end, nct, cw, vec16);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // digits visible to the tensor cores
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_full + 8 * b);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp == 0) {
+    // ---- MMA issue (one thread)
+    if (lane == 0) {
+      const uint32_t sbase = smem_addr(tc_smem);
+      constexpr uint32_t idesc = tc_idesc(128, 128);
+      int64_t blk = -1;
+      bool new_block = true;
+      for (int64_t k = 0; k < nst; ++k) {
+        const int b = (int)(k & 1);
+        const int64_t r0 = r_begin + k * kTcStageRows;
+        if (new_block) {
+          ++blk;
+          if (blk >= 1) mbar_wait(b_tempty, (uint32_t)((blk - 1) & 1), abort);   // previous block read out
+        }
+        mbar_wait(b_full + 8 * b, (uint32_t)((k >> 1) & 1), abort);
+        tc_fence_after();
+        const uint32_t stb = sbase + (uint32_t)b * kTcStage;
+#pragma unroll
+        for (int ks = 0; ks < kTcKB / 2; ++ks) {
+          const uint32_t km = stb + (uint32_t)(2 * ks) * kTcKBBytes;
+          const uint32_t acc = (new_block && ks == 0) ? 0u : 1u;
+#pragma unroll
+          for (int q = 0; q < kTcAcc; ++q) {
+            const uint64_t da = tc_desc(km + (uint32_t)kTcAccA[q] * kTcPlaneBytes, kTcKBBytes, kTcCore);
+            const uint64_t db = tc_desc(km + (uint32_t)kTcAccB[q] * kTcPlaneBytes, kTcKBBytes, kTcCore);
+            tc_mma(tmem + 128u * (uint32_t)q, da, db, idesc, acc);
+          }
+        }
+        tc_commit(b_empty + 8 * b);                     // stage buffer b may be refilled
+        new_block = tc_block_end(r0, r_end);
+        if (new_block) tc_commit(b_tfull);              // the block's sums are complete
+      }
+      // every MMA of this thread complete before tensor memory is freed
+      tc_commit(b_drain);
+      mbar_wait(b_drain, 0u, abort);
+    }
+    __syncwarp();
+  } else if (warp < kTcEpi0) {
+    // ---- column 32: binary64 FMA sums of y_i y_32, i = 0..32, rows split over three warps
+    if (c32) {
+      const int w = warp - kTcC32W0;
+      double acc[kMaxCols];
+#pragma unroll
+      for (int i = 0; i < kMaxCols; ++i) acc[i] = 0.0;
+      for (int64_t r = r_begin + 32 * w + lane; r < r_end; r += 96) {
+        const double y32 = widen(__ldg(Y + 32 * ld + r));
+#pragma unroll
+        for (int i = 0; i < kMaxCols; ++i) acc[i] = fma(widen(__ldg(Y + (int64_t)i * ld + r)), y32, acc[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < kMaxCols; ++i) {
+        double v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) c32sum[w][i] = v;
+      }
+    }
+  } else {
+    // ---- epilogue: warp q = warp - 4 reads lane quadrant q: rows s = a + q
+    // of accumulator (a, b), i = lane, column 32 l + j = (t = b + l, column j)
+    const int q = warp - kTcEpi0, i = lane;
+    int64_t blk = -1;
+    for (int64_t k = 0; k < nst; ++k) {
+      const int64_t r0 = r_begin + k * kTcStageRows;
+      if (!tc_block_end(r0, r_end)) continue;
+      ++blk;
+      const int* ce_g = cexp + (r0 >> kDgChunkShift) * kMaxCols;
+      mbar_wait(b_tfull, (uint32_t)(blk & 1), abort);
+      tc_fence_after();
+      const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
+      // Half a row of columns j at a time, summed over every plane-pair block
+      // of this quadrant: 2^48 X is an integer below 2^24; u = s + t < 6 goes
+      // to the high Horner sum (weight 32^(5 - u)), u >= 6 to the low one
+      // (32^(11 - u)).  X_st (s < t) enters entry (min(i,j), max(i,j)) from
+      // both (i, j) and (j, i) (twice on the diagonal); X_ss only once, from
+      // i <= j.
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+        long long hi[16], lo[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) hi[jj] = lo[jj] = 0;
+#pragma unroll 1
+        for (int acc = 0; acc < kTcAcc; ++acc) {
+          const int s = kTcAccA[acc] + q;
+#pragma unroll 1
+          for (int l = 0; l < 4; ++l) {
+            const int tt = kTcAccB[acc] + l;
+            if (s > tt || s + tt > 11) continue;       // uniform: pairs s <= t, s + t <= 11
+            uint32_t x[16];
+            tc_ld16(x, tq + (uint32_t)(128 * acc + 32 * l + 16 * half));
+            tc_wait_ld();
+            const int u = s + tt;
+            const long long w = u < 6 ? (1ll << (5 * (5 - u))) : (1ll << (5 * (11 - u)));
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int j = 16 * half + jj;
+              if (s < tt || i <= j) {
+                const long long v =
+                    (long long)__float2int_rz(__uint_as_float(x[jj]) * 0x1p48f) * (s < tt && i == j ? 2 * w : w);
+                if (u < 6) hi[jj] += v;
+                else lo[jj] += v;
+              }
+            }
+          }
+        }
+        if (i < nct) {
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = 16 * half + jj;
+            if (j < nct) {
+              const int a = i < j ? i : j, bb = i < j ? j : i;
+              const int p = a * ncols - a * (a - 1) / 2 + (bb - a);
+              if (hi[jj] != 0) atomicAdd(&s_hi[p], (unsigned long long)hi[jj]);
+              if (lo[jj] != 0) atomicAdd(&s_lo[p], (unsigned long long)lo[jj]);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_tempty);              // the accumulators may be overwritten
+      bar_sync(1, 128);                                 // all four quadrants added
+      for (int p = t - 32 * kTcEpi0; p < np; p += 128) {
+        int pi, pj;
+        pair_of(p, ncols, &pi, &pj);
+        if (pj >= kTcCols) continue;                    // column 32: binary64 sums
+        const long long shi = (long long)s_hi[p], slo = (long long)s_lo[p];
+        s_hi[p] = 0ull;
+        s_lo[p] = 0ull;
+        const int ci_ = __ldg(ce_g + pi), cj_ = __ldg(ce_g + pj);
+        if (ci_ == 2047 || cj_ == 2047) {
+          gacc[p] = __longlong_as_double(0x7ff8000000000000ll);
+        } else {
+          const int kk = ci_ + cj_ - 2006;
+          if (shi != 0) gacc[p] += dg_scale((double)shi, kk - 5 * 5 - 48);
+          if (slo != 0) gacc[p] += dg_scale((double)slo, kk - 5 * 11 - 48);
+        }
+      }
+      bar_sync(1, 128);                                 // sums cleared before the next block
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
+  for (int p = t; p < np; p += kTcThreads) {
+    int pi, pj;
+    pair_of(p, ncols, &pi, &pj);
+    const double v = pj >= kTcCols ? (c32sum[0][pi] + c32sum[1][pi]) + c32sum[2][pi] : gacc[p];
+    partials[(int64_t)blockIdx.x * kMaxPairs + p] = v;
+  }
+}
+
 // One warp per pair: fixed-order sum of the per-block partials.
 __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restrict__ partials, int nblocks,
                                                           const SolveState* __restrict__ st, int ncols_fixed,
@@ -913,8 +1332,21 @@ cudaError_t gram_prepare() {
   e = cudaFuncSetAttribute(gram_partial_dg_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)dg_smem_bytes<float>());
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gram_partial_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_bytes<double>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gram_partial_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_bytes<float>());
+  if (e != cudaSuccess) return e;
   done[dev] = true;
   return cudaSuccess;
+}
+
+cudaError_t gram_tc_error(int* flag, bool clear) {
+  cudaError_t e = cudaMemcpyFromSymbol(flag, g_gram_tc_error, sizeof(int));
+  if (e != cudaSuccess || !clear) return e;
+  const int zero = 0;
+  return cudaMemcpyToSymbol(g_gram_tc_error, &zero, sizeof(int));
 }
 
 int64_t gram_exp_ints(int64_t n) { return ((n + kDgChunkRows - 1) / kDgChunkRows) * kMaxCols; }
@@ -922,7 +1354,7 @@ int64_t gram_exp_ints(int64_t n) { return ((n + kDgChunkRows - 1) / kDgChunkRows
 cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* /*ncols_dev*/, int ncols_fixed,
                         const SolveState* state, double* partials, int nblocks, double* G, int ldg, bool y32,
                         cudaStream_t st, int gram_mode, int* chunk_exp) {
-  if (gram_mode == 2) {
+  if (gram_mode == 2 || gram_mode == 3) {
     if (!chunk_exp) return cudaErrorInvalidValue;
     const int64_t nchunks = (n + kDgChunkRows - 1) / kDgChunkRows;
     if (nchunks > 0x7fffffff) return cudaErrorInvalidValue;
@@ -938,13 +1370,21 @@ cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* /*ncols
     if (y32) {
       gram_chunk_exp_kernel<float><<<egrid, 256, 0, st>>>(static_cast<const float*>(Y), n, ld, state, ncols_fixed,
                                                           chunk_exp);
-      gram_partial_dg_kernel<float><<<nblocks, kDgThreads, dg_smem_bytes<float>(), st>>>(
-          static_cast<const float*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
+      if (gram_mode == 3)
+        gram_partial_tc_kernel<float><<<nblocks, kTcThreads, tc_smem_bytes<float>(), st>>>(
+            static_cast<const float*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
+      else
+        gram_partial_dg_kernel<float><<<nblocks, kDgThreads, dg_smem_bytes<float>(), st>>>(
+            static_cast<const float*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
     } else {
       gram_chunk_exp_kernel<double><<<egrid, 256, 0, st>>>(static_cast<const double*>(Y), n, ld, state,
                                                            ncols_fixed, chunk_exp);
-      gram_partial_dg_kernel<double><<<nblocks, kDgThreads, dg_smem_bytes<double>(), st>>>(
-          static_cast<const double*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
+      if (gram_mode == 3)
+        gram_partial_tc_kernel<double><<<nblocks, kTcThreads, tc_smem_bytes<double>(), st>>>(
+            static_cast<const double*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
+      else
+        gram_partial_dg_kernel<double><<<nblocks, kDgThreads, dg_smem_bytes<double>(), st>>>(
+            static_cast<const double*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
     }
   } else if (gram_mode == 1) {
     // one block per SM, at most one block per 256-row tile

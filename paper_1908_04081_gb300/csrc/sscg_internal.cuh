@@ -94,7 +94,7 @@ struct SolveState {
   // FP32-stored basis: periodic residual replacement (r := b - A x, p kept)
   double fp32_drop, rho_last;
   double prev_fail;   // relative true residual at the last failed convergence check
-  int gram_mode;      // 0: binary64 Gram; 1: binary32-pair products; 2: f16 digit products
+  int gram_mode;      // 0: binary64 Gram; 1: binary32-pair products; 2, 3: f16 digit products (mma.sync, tcgen05)
   int mpk_fp64_per16; // warps (of 16) on the binary64 FMA chain in stencil levels; -1: library default
   int fp32_replace_pending, fp32_replacements;
   double c, psi, normb, upd_relres;
@@ -151,10 +151,13 @@ int gram_blocks(int64_t n);
 cudaError_t gram_prepare();
 // gram_mode 0: binary64 products and sums; 1: binary32-pair products on the
 // FP32 pipes, compensated binary32 sums per tile, binary64 across tiles;
-// 2: exact products of 5-bit digits on the f16 tensor cores, exact binary32
-// sums over 1024 rows, binary64 across them (needs `chunk_exp`, an int
-// scratch of gram_exp_ints(n) entries).
+// 2: exact products of 5-bit digits on the f16 tensor cores (mma.sync), exact
+// binary32 sums over 1024 rows, binary64 across them; 3: the same digit
+// arithmetic as tcgen05.mma with tensor-memory accumulators (modes 2 and 3
+// need `chunk_exp`, an int scratch of gram_exp_ints(n) entries).
 int64_t gram_exp_ints(int64_t n);
+// the give-up flag of the gram_mode 3 kernel's bounded waits (read, optionally cleared)
+cudaError_t gram_tc_error(int* flag, bool clear);
 cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* ncols_dev, int ncols_fixed,
                         const SolveState* state, double* partials, int nblocks, double* G, int ldg,
                         bool y32, cudaStream_t st, int gram_mode = 0, int* chunk_exp = nullptr);

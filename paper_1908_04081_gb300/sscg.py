@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sscg_ritz": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "sscg_spmv": (C.c_int, [_P, _P, _P]),
         "sscg_build_basis": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, _P, _I64]),
+        "sscg_wait_failures": (C.c_int, [_P, C.c_int]),
         "sscg_build_basis_ex": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, _P, _I64, C.c_int]),
         "sscg_gram": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _P]),
         "sscg_gram_noalloc": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _P]),
@@ -171,7 +172,7 @@ def sscg_opts_default(**kw) -> Opts:
         if k == "variant" and isinstance(v, str):
             v = {"improved": 0, "fixed": 1, "old": 2}[v]
         if k == "gram_mode" and isinstance(v, str):
-            v = {"binary64": 0, "binary32_pair": 1, "digits": 2}[v]
+            v = {"binary64": 0, "binary32_pair": 1, "digits": 2, "digits_tcgen05": 3}[v]
         setattr(o, k, v)
     return o
 
@@ -293,7 +294,8 @@ def sscg_gram(Y, n: int, ldy: int, ncols: int, G, stream=None) -> None:
 
 
 def sscg_gram_ex(Y, n: int, ldy: int, ncols: int, G, mode: int, stream=None) -> None:
-    """G = Y^T Y with binary64 products (mode 0) or binary32-pair products (mode 1)."""
+    """G = Y^T Y: binary64 products (mode 0), binary32-pair products (mode 1), exact
+    digit products on the tensor cores by mma.sync (mode 2) or tcgen05.mma (mode 3)."""
     _check(load_library().sscg_gram_ex(_f64(Y), n, ldy, ncols, _f64(G), mode, _stream_ptr(stream)), "sscg_gram_ex")
 
 
@@ -301,6 +303,13 @@ def sscg_gram_noalloc(Y, n: int, ldy: int, ncols: int, G, stream=None) -> None:
     """G = Y^T Y with the library's fixed scratch (no device allocation)."""
     _check(load_library().sscg_gram_noalloc(_f64(Y), n, ldy, ncols, _f64(G), _stream_ptr(stream)),
            "sscg_gram_noalloc")
+
+
+def sscg_wait_failures(clear: bool = True) -> int:
+    """1 if a bounded in-kernel wait gave up since the last clear (see include/sscg.h)."""
+    f = C.c_int(0)
+    _check(load_library().sscg_wait_failures(C.byref(f), int(clear)), "sscg_wait_failures")
+    return f.value
 
 
 def sscg_kappa(G, ldg: int, sbar: int, kappa_cut: float, kappa, lmin, lmax, stream=None) -> None:

@@ -736,7 +736,7 @@ def test_failure_detection_injected_on_the_host(pkg):
     assert st4.status == 0 and st4.true_relres <= 1e-10
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("n,ncols", [(1, 1), (2, 2), (777, 5), (513, 4), (10007, 33), (70001, 17),
                                      (300000, 33), (1000003, 9), (8193, 3), (4095, 32), (12289, 31),
                                      (155000, 33), (4102, 33)])
@@ -764,10 +764,12 @@ def test_gram_fast_modes(pkg, n, ncols, mode):
     d[d == 0] = 1.0
     assert np.max(np.abs(Gg - Go) / d) <= 1e-13
     assert np.array_equal(Gg, Gg.T)
+    assert pkg.sscg.sscg_wait_failures() == 0
 
 
-@pytest.mark.parametrize("n,ncols", [(10007, 33), (70001, 17), (5000, 6)])
-def test_gram_digits_exact_on_integers(pkg, n, ncols):
+@pytest.mark.parametrize("mode", [2, 3])
+@pytest.mark.parametrize("n,ncols", [(10007, 33), (70001, 17), (5000, 6), (4099, 32), (300000, 33)])
+def test_gram_digits_exact_on_integers(pkg, n, ncols, mode):
     """gram_mode 2 is exact where the products and sums are: integer entries
     below 2^16 have every digit exact, every 1024-row sum below 2^24 x 2^-48
     is exact in binary32 and the binary64 combination stays below 2^53, so G
@@ -779,12 +781,14 @@ def test_gram_digits_exact_on_integers(pkg, n, ncols):
     Gi = Yi.T @ Yi  # exact in int64
     Yd = dev(np.ascontiguousarray(Yi.T.astype(np.float64)).ravel())
     G1 = torch.zeros(ncols * ncols, dtype=torch.float64, device="cuda")
-    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G1, 2)
+    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G1, mode)
     Gg = G1.reshape(ncols, ncols).cpu().numpy()
     assert np.array_equal(Gg, Gi.astype(np.float64))
+    assert pkg.sscg.sscg_wait_failures() == 0
 
 
-def test_gram_digits_wide_exponents(pkg):
+@pytest.mark.parametrize("mode", [2, 3])
+def test_gram_digits_wide_exponents(pkg, mode):
     """gram_mode 2 with values spread over 2^-60 .. 2^60 inside one column and
     chunk: entries far below the chunk's largest value lose their low bits,
     which the normwise bound absorbs (each row's error is below about 2^-56
@@ -794,14 +798,15 @@ def test_gram_digits_wide_exponents(pkg):
     Y = rng.standard_normal((n, ncols)) * np.exp2(rng.integers(-60, 61, (n, ncols)))
     Yd = dev(np.ascontiguousarray(Y.T).ravel())
     G1 = torch.zeros(ncols * ncols, dtype=torch.float64, device="cuda")
-    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G1, 2)
+    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G1, mode)
     Gg = G1.reshape(ncols, ncols).cpu().numpy()
     Go = Y.T @ Y
     d = np.sqrt(np.outer(np.diag(Go), np.diag(Go)))
     assert np.max(np.abs(Gg - Go) / d) <= 1e-13
 
 
-def test_gram_digits_subnormal_columns(pkg):
+@pytest.mark.parametrize("mode", [2, 3])
+def test_gram_digits_subnormal_columns(pkg, mode):
     """gram_mode 2 with binary64 subnormals: a column of subnormals only (its
     scale exponent is the subnormal one, so its digits are exact) and a
     column mixing subnormals with unit-size values (the subnormals fall below
@@ -816,7 +821,7 @@ def test_gram_digits_subnormal_columns(pkg):
     Y[mix, 1] *= 2.0 ** -1060
     Yd = dev(np.ascontiguousarray(Y.T).ravel())
     G2 = torch.zeros(ncols * ncols, dtype=torch.float64, device="cuda")
-    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G2, 2)
+    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G2, mode)
     Gg = G2.reshape(ncols, ncols).cpu().numpy()
     Go = Y.T @ Y
     assert np.all(np.isfinite(Gg))
@@ -826,7 +831,7 @@ def test_gram_digits_subnormal_columns(pkg):
     assert Gg[0, 0] == 0.0 and Go[0, 0] == 0.0
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_gram_fast_modes_nonfinite(pkg, mode):
     """A NaN or Inf in Y reaches the entries of G that it touches in
     gram_mode 1 and 2, as it does in binary64 (the solver's non-finite check
@@ -846,7 +851,7 @@ def test_gram_fast_modes_nonfinite(pkg, mode):
     assert np.all(np.isfinite(Gg[np.ix_(keep, keep)]))
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("name", ["poisson", "varcoef3d", "varcoef3d_y32"])
 def test_solve_with_fast_gram(pkg, name, mode):
     if name == "poisson":
@@ -867,3 +872,24 @@ def test_solve_with_fast_gram(pkg, name, mode):
     st = s.solve(dev(b), xt, tol=1e-10, s_max=smax, basis=basis, hist_cap=4000, gram_mode=mode,
                  y_fp32=int(y32))
     compare_solves(xt.cpu().numpy(), st, pkg.sscg.history(st), x_o, info, 1e-10, strict=(name == "poisson"))
+    assert pkg.sscg.sscg_wait_failures() == 0
+
+
+@pytest.mark.parametrize("n,ncols", [(10007, 33), (70001, 31), (4096 * 9 + 77, 33), (1000003, 33), (65, 3)])
+def test_gram_tcgen05_equals_mma_sync(pkg, n, ncols):
+    """gram_mode 3 (tcgen05.mma, sums in tensor memory) runs gram_mode 2's
+    arithmetic: the same exact digit sums per 1024-row block, added in
+    binary64 in another order, so the two agree to a few ulps of
+    sqrt(G_ii G_jj)."""
+    rng = np.random.default_rng(n + ncols)
+    Y = rng.standard_normal((n, ncols)) * np.logspace(-3, 3, ncols)[None, :]
+    Yd = dev(np.ascontiguousarray(Y.T).ravel())
+    G2 = torch.zeros(ncols * ncols, dtype=torch.float64, device="cuda")
+    G3 = torch.zeros_like(G2)
+    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G2, 2)
+    pkg.sscg.sscg_gram_ex(Yd, n, n, ncols, G3, 3)
+    a = G2.reshape(ncols, ncols).cpu().numpy()
+    b = G3.reshape(ncols, ncols).cpu().numpy()
+    d = np.sqrt(np.outer(np.diag(a), np.diag(a)))
+    assert np.max(np.abs(a - b) / d) <= 1e-15
+    assert pkg.sscg.sscg_wait_failures() == 0

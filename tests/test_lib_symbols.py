@@ -54,6 +54,10 @@ def test_binding_defaults(lib):
     assert o.gram_mode == 0  # the method as written
     assert sscg.sscg_opts_default(gram_mode="digits").gram_mode == 2
     assert sscg.sscg_opts_default(gram_mode="binary32_pair").gram_mode == 1
+    assert sscg.sscg_opts_default(gram_mode="digits_tcgen05").gram_mode == 3
+    # the FP64/integer split of the stencil matrix-powers level: -1 (library default) .. 16
+    assert sscg.sscg_opts_default().mpk_fp64_per16 == -1
+    assert L_opts_rejects_split(sscg)
 
 
 def test_invalid_arguments_rejected_without_gpu(lib):
@@ -63,7 +67,15 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert L.sscg_create_csr(ctypes.byref(h), 0, 0, None, None, None, 0, None) == -1
     assert L.sscg_solve(None, None, None, 1e-10, 8, 2, None, None) == -1
     assert L.sscg_leja(0, None) == -1
-    # Gram product arithmetic outside 0..2 is rejected before any pointer is used
+    # Gram product arithmetic outside 0..3 is rejected before any pointer is used
     fake = ctypes.c_void_p(16)
-    for mode in (-1, 3):
+    for mode in (-1, 4):
         assert L.sscg_gram_ex(fake, ctypes.c_int64(10), ctypes.c_int64(10), 3, fake, mode, None) == -1
+
+
+def L_opts_rejects_split(sscg):
+    """A split outside -1..16 is rejected (before any GPU work)."""
+    L = sscg.load_library()
+    o = sscg.sscg_opts_default(mpk_fp64_per16=17)
+    return L.sscg_solve(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 1e-10, 8, 2,
+                        ctypes.byref(o), None) == -1
