@@ -86,6 +86,8 @@ def dg_tiles(ncols):
 
 
 DG_MMA_FLOP_PER_ROW_TILE = 78 * 16 * 8 * 16 * 2 // 16   # 78 f16 m16n8k16 MMAs per 16 rows and tile
+# gram_mode 3: four tcgen05.mma of M = N = 128, K = 16 per 16 rows (columns 0..31)
+TC_MMA_FLOP_PER_ROW = 4 * 128 * 128 * 16 * 2 // 16
 FF_OPS_PER_PRODUCT = 13                       # binary32 instructions per pair and row (gram_mode 1)
 # binary64 lane operations per cell of one 3D matrix-powers level (both chains,
 # stencil_mpk_grid_kernel): 17 (Newton and monomial, mu = 0), 19 (Chebyshev)
@@ -118,9 +120,10 @@ def parse_args():
                     help="override the workload's s_max (sigma) for studies; 0 keeps the configuration's")
     ap.add_argument("--gram-mode", type=int, default=None,
                     help="0: binary64 Gram (the method as written); 1: binary32-pair products on the FP32 pipes; "
-                         "2: exact 5-bit digit products on the f16 tensor cores.  Default: the workload's "
-                         "(2, except 0 for the 64^2 Poisson case, where the tensor-core kernel's fixed cost "
-                         "per launch exceeds the binary64 kernel's time)")
+                         "2: exact 5-bit digit products on the f16 tensor cores (mma.sync); 3: the same digit "
+                         "products by tcgen05.mma into tensor memory.  Default: the workload's (3, except 0 for "
+                         "the 64^2 Poisson case, where the tensor-core kernels' fixed cost per launch exceeds "
+                         "the binary64 kernel's time)")
     return ap.parse_args()
 
 
@@ -387,7 +390,9 @@ def run_batched(args, cfg, pkg, torch, dev):
     shapes = [(1024, 1024), (2048, 2048), (4096, 4096), (8192, 8192), (2048, 8192)]
     ib, shape_us = pkg.sscg.sscg_autotune_batch([s.h for s in solvers], nrhs, b, cfg["tol"], s_max, shapes,
                                                 trial_outer=20, basis=cfg["basis"])
-    opts = pkg.sscg.sscg_opts_default(batch_chunk_rows=shapes[ib][0], batch_gram_rows=shapes[ib][1])
+    batch_gram = 3 if args.gram_mode == 3 else 0   # the batch runs the binary64 or the tcgen05 Gram
+    opts = pkg.sscg.sscg_opts_default(batch_chunk_rows=shapes[ib][0], batch_gram_rows=shapes[ib][1],
+                                      gram_mode=batch_gram)
     t_tune = time.perf_counter() - t_tune
     x = torch.zeros_like(b)
     for _ in range(args.warmup):
@@ -467,6 +472,7 @@ def run_batched(args, cfg, pkg, torch, dev):
                        "unknowns": int(b_np.size), "sigma_by_class": {f"{k[0]}d_4^{k[1]}": v for k, v in classes.items()},
                        "tile_rows": {"chunk": shapes[ib][0], "gram": shapes[ib][1]},
                        "tile_us_per_inner": {f"{c}x{g}": t for (c, g), t in zip(shapes, shape_us)},
+                       "gram_mode": batch_gram,
                        "autotune_s": t_tune},
             "status": rc, "converged": stats["converged"], "outer_loops": stats["outer_loops"],
             "inner_iters_total": stats["inner_iters"], "max_true_relres": stats["max_true_relres"],
@@ -536,7 +542,7 @@ def main():
     args = parse_args()
     cfg = dict(WORKLOADS[args.workload])
     if args.gram_mode is None:
-        args.gram_mode = cfg.get("gram_mode", 2)
+        args.gram_mode = cfg.get("gram_mode", 3)
     if args.s_max > 0:
         cfg["smax"] = args.s_max
     rank = int(os.environ.get("RANK", "0"))
@@ -676,6 +682,18 @@ def main():
                     "frac": (gram_tflops / fp64_peak) if gram_tflops else None,
                     "traffic": gram_traffic, "traffic_source": traffic_src, "launches": n_gram,
                     "peak_note": fp64_note}
+    elif args.gram_mode == 3:
+        # executed tcgen05 f16 MMA flops (4 MMAs of 128 x 128 x 16 per 16 rows)
+        tc_flop = sum(n * TC_MMA_FLOP_PER_ROW for h in hist_p)
+        tc_tf = tc_flop / t_gram / 1e12 if t_gram > 0 else None
+        roofline = {"bound": "tensor", "kernel": "gram_chunk_exp+gram_partial_tc+gram_reduce (G = Y^T Y, exact "
+                                                  "5-bit digit products by tcgen05.mma into tensor memory)",
+                    "achieved": tc_tf, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": (tc_tf / BF16_PEAK_TFLOPS) if tc_tf else None,
+                    "traffic": gram_traffic, "traffic_source": traffic_src, "launches": n_gram,
+                    "gram_fp64_equiv_tflops": gram_tflops,
+                    "peak_note": f"{BF16_PEAK_SRC} bf16 burst {BF16_PEAK_TFLOPS:.0f} TFLOP/s (same nominal dense rate "
+                                 "as f16)"}
     elif args.gram_mode == 2:
         # digit Gram: executed f16 MMA flops (tiles x 78 MMAs per 16 rows) per
         # second of the Gram phase (which includes the chunk-exponent pass)
@@ -786,7 +804,10 @@ def main():
                                 2: "G at binary64 normwise accuracy or better: every value written as 12 5-bit "
                                    "digits (exact within 2^7 of its column's largest, else rounded at 2^-60 of "
                                    "it), digit products exact on the f16 tensor cores, exact binary32 sums over "
-                                   "1024 rows, binary64 across blocks (normwise error below binary64 FMAs')"}
+                                   "1024 rows, binary64 across blocks (normwise error below binary64 FMAs')",
+                                3: "G at binary64 normwise accuracy or better: the digit arithmetic of mode 2 as "
+                                   "tcgen05.mma with f32 accumulators in tensor memory (one plane pair each, exact "
+                                   "binary32 sums over 4096 rows); the 33rd column by binary64 FMAs"}
                        [args.gram_mode]},
             "converged": ok, "true_relres": max(s.true_relres for s in stats),
             "outer_loops": st0.outer_iters, "inner_iters": st0.inner_iters, "host_syncs": st0.host_syncs,

@@ -231,7 +231,9 @@ typedef struct {
  * offset sum_{s' < s} nrhs[s'] n_{s'} + k n_s; x holds the initial guesses on
  * entry and the solutions on exit.  s_max: per-system sigma in
  * [1, SSCG_MAX_S] (e.g. from sscg_autotune).  opts: as for sscg_solve
- * (y_fp32 and gram_mode != 0 are unsupported here: SSCG_ERR_UNSUPPORTED;
+ * (y_fp32 and gram_mode 1 and 2 are unsupported here: SSCG_ERR_UNSUPPORTED;
+ * gram_mode 3, the tcgen05 digit Gram, runs one thread block per Gram block
+ * and needs batch_gram_rows <= 16384, else SSCG_ERR_INVALID_ARG;
  * batch_chunk_rows / batch_gram_rows set the tile shapes; use_graph = 0
  * replaces the WHILE node by host polling every check_every outer loops).
  * Returns SSCG_OK if every pair

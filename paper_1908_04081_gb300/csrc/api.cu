@@ -828,10 +828,14 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
   if (opts) o = *opts;
   int rc = validate_opts(o);
   if (rc) return rc;
-  if (o.y_fp32 || o.gram_mode != 0) return SSCG_ERR_UNSUPPORTED;
+  if (o.y_fp32 || (o.gram_mode != 0 && o.gram_mode != 3)) return SSCG_ERR_UNSUPPORTED;
   // ---- pairs, chunks and Gram blocks (host)
   const int chunk_rows = o.batch_chunk_rows > 0 ? o.batch_chunk_rows : kBatchChunk;
   const int gram_rows = o.batch_gram_rows > 0 ? o.batch_gram_rows : kBatchGramRows;
+  if (o.gram_mode == 3) {
+    if (gram_rows > (1 << 14)) return SSCG_ERR_INVALID_ARG;   // one tcgen05 Gram block sums at most 16384 rows
+    CK(gram_prepare());
+  }
   std::vector<BatchPair> pairs;
   std::vector<int> chunk_pair, gblk_pair, pair_sigma;
   int64_t off = 0;
@@ -934,7 +938,7 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
       if ((e2 = launch_batch_begin(v, st)) != cudaSuccess) return e2;
       for (int l = 0; l < sigma_max; ++l)
         if ((e2 = launch_batch_mpk(v, d_Y.p, LD, l, st)) != cudaSuccess) return e2;
-      if ((e2 = launch_batch_gram(v, d_Y.p, LD, d_part.p, st)) != cudaSuccess) return e2;
+      if ((e2 = launch_batch_gram(v, d_Y.p, LD, d_part.p, st, o.gram_mode)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_kappa(v, sigma_max, st)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_control(v, d_leja, st)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_recombine(v, d_Y.p, LD, x, st)) != cudaSuccess) return e2;

@@ -806,11 +806,11 @@ gram_partial_dg_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
 // [8-row block][plane][column] (LBO = one 8-row block, 6,144 bytes; SBO = 128
 // bytes between groups of 8 operand rows).
 //
-// Warp roles (512 threads): warp 0 allocates tensor memory and one of its
+// Warp roles (768 threads): warp 0 allocates tensor memory and one of its
 // threads issues the MMAs; warps 1..3 the column-32 dot products; warps 4..7
 // the epilogue of each scale chunk (tcgen05.ld reaches lane quadrant w % 4
-// from warp w); warps 8..15 stage and convert the rows (the conversion of
-// gram_mode 2).  Hand-offs are mbarriers: full[b] (conversion -> MMA, per
+// from warp w); warps 8..23 stage and convert the rows (the digits of
+// gram_mode 2, four rows per thread).  Hand-offs are mbarriers: full[b] (conversion -> MMA, per
 // stage buffer), empty[b] (tcgen05.commit -> conversion), tfull
 // (tcgen05.commit -> epilogue), tempty (epilogue -> MMA, before a block's
 // first MMA overwrites the accumulators).  Every wait gives up after about a
@@ -823,7 +823,8 @@ constexpr uint32_t kTcCore = 128;                                      // 8 rows
 constexpr uint32_t kTcPlaneBytes = (kTcCols / 8) * kTcCore;            // 512: one plane of 32 columns
 constexpr uint32_t kTcKBBytes = kDgPlanes * kTcPlaneBytes;             // 6,144: LBO
 constexpr uint32_t kTcStage = kTcKB * kTcKBBytes;                      // 49,152
-constexpr int kTcThreads = 512;
+constexpr int kTcConvWarps = 16;                                       // conversion warps (4 rows per thread)
+constexpr int kTcThreads = 32 * (8 + kTcConvWarps);                    // 768
 constexpr int kTcC32W0 = 1, kTcEpi0 = 4, kTcConv0 = 8;                 // first column-32 / epilogue / conversion warp
 constexpr uint32_t kTcTmemCols = 512;
 constexpr int kTcAcc = 4;                                              // accumulators (a, b)
@@ -885,11 +886,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volati
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-// 16 consecutive accumulator columns of this warp's lane quadrant (raw bits)
-__device__ __forceinline__ void tc_ld16(uint32_t (&r)[16], uint32_t taddr) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+// 8 consecutive accumulator columns of this warp's lane quadrant (raw bits)
+__device__ __forceinline__ void tc_ld8(uint32_t (&r)[8], uint32_t taddr) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -919,35 +919,85 @@ __device__ __forceinline__ void tc_store8(const double (&v)[8], int ce, unsigned
 #undef TC_PLANE
 }
 
-// conversion of one stage into stage buffer `stage` (thread assignment of
-// dg_convert: column 8 (cw % 4) + lane % 8 and 8-row block 4 (cw / 4) + lane / 8)
+// the 12 digit planes of 4 consecutive rows of one column: words 2h, 2h + 1
+// of the 16-byte units unit + t * plane_stride
+__device__ __forceinline__ void tc_store4(const double (&v)[4], int ce, unsigned char* unit, uint32_t plane_stride,
+                                          int h2) {
+  unsigned h[4], l[4], sg[2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const unsigned long long F = dg_fixed(v[k], ce);
+    h[k] = (unsigned)(F >> 32);
+    l[k] = (unsigned)F;
+  }
+#pragma unroll
+  for (int w = 0; w < 2; ++w)
+    sg[w] = (((unsigned)((unsigned long long)__double_as_longlong(v[2 * w]) >> 63)) << 15) |
+            (((unsigned)((unsigned long long)__double_as_longlong(v[2 * w + 1]) >> 63)) << 31);
+  unsigned char* u = unit + 8 * h2;
+#define TC_PLANE4(t)                                                                                      \
+  *reinterpret_cast<uint2*>(u + (t) * plane_stride) =                                                     \
+      make_uint2(dg_digit<t>(h[0], l[0]) | (dg_digit<t>(h[1], l[1]) << 16) | sg[0],                       \
+                 dg_digit<t>(h[2], l[2]) | (dg_digit<t>(h[3], l[3]) << 16) | sg[1]);
+  TC_PLANE4(0) TC_PLANE4(1) TC_PLANE4(2) TC_PLANE4(3) TC_PLANE4(4) TC_PLANE4(5)
+  TC_PLANE4(6) TC_PLANE4(7) TC_PLANE4(8) TC_PLANE4(9) TC_PLANE4(10) TC_PLANE4(11)
+#undef TC_PLANE4
+}
+
+// Conversion threads: warp cw (0..15), lane: column 8 (cw % 4) + lane % 8,
+// 4-row group q = 4 (cw / 4) + lane / 8 (8-row block q / 2, half q % 2), so 8
+// consecutive columns per 8-lane phase (the 8-byte shared stores do not
+// conflict).  Each thread stages its own rows by cp.async into
+// [column][dg_raw_ld] and waits for its own copies only.
+__device__ __forceinline__ void tc_conv_slot(int cw, int lane, int& c, int& kb, int& h2) {
+  c = 8 * (cw & 3) + (lane & 7);
+  const int q = 4 * (cw >> 2) + (lane >> 3);
+  kb = q >> 1;
+  h2 = q & 1;
+}
+
+template <typename T>
+__device__ __forceinline__ void tc_issue_raw(T* raw, const T* __restrict__ Y, int64_t ld, int64_t r0, int64_t r_end,
+                                             int ncols, int cw, bool vec16) {
+  constexpr int LD = dg_raw_ld<T>();
+  int c, kb, h2;
+  tc_conv_slot(cw, threadIdx.x & 31, c, kb, h2);
+  if (c < ncols) {
+    const int off = 8 * kb + 4 * h2;
+    const int64_t row = r0 + off;
+    const int64_t nv = r_end - row;
+    // rows past the end are zero filled; their source address is never read
+    // but stays inside Y (row 0 of the column)
+    cp_async_elems<T>((unsigned)__cvta_generic_to_shared(raw) + (unsigned)((c * LD + off) * sizeof(T)),
+                      Y + (int64_t)c * ld + (nv > 0 ? row : 0), nv < 0 ? 0 : (nv > 4 ? 4 : (int)nv), 4, vec16);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ void tc_convert(const T* raw, unsigned char* stage, const int* __restrict__ ce_g,
                                            int ncols, int cw) {
   constexpr int LD = dg_raw_ld<T>();
-  const int lane = threadIdx.x & 31;
-  const int c = 8 * (cw & 3) + (lane & 7), kb = 4 * (cw >> 2) + (lane >> 3);
+  int c, kb, h2;
+  tc_conv_slot(cw, threadIdx.x & 31, c, kb, h2);
   if (c < ncols) {
-    const T* src = raw + c * LD + 8 * kb;
-    double v[8];
+    const T* src = raw + c * LD + 8 * kb + 4 * h2;
+    double v[4];
     if (sizeof(T) == 8) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 2; ++k) {
         const double2 p = reinterpret_cast<const double2*>(src)[k];
         v[2 * k] = p.x;
         v[2 * k + 1] = p.y;
       }
     } else {
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const float4 p = reinterpret_cast<const float4*>(src)[k];
-        v[4 * k] = widen(p.x);
-        v[4 * k + 1] = widen(p.y);
-        v[4 * k + 2] = widen(p.z);
-        v[4 * k + 3] = widen(p.w);
-      }
+      const float4 p = *reinterpret_cast<const float4*>(src);
+      v[0] = widen(p.x);
+      v[1] = widen(p.y);
+      v[2] = widen(p.z);
+      v[3] = widen(p.w);
     }
-    tc_store8(v, __ldg(ce_g + c), stage + kb * kTcKBBytes + c * 16, kTcPlaneBytes);
+    tc_store4(v, ce_g[c], stage + kb * kTcKBBytes + c * 16, kTcPlaneBytes, h2);
   }
 }
 
@@ -963,14 +1013,41 @@ __device__ __forceinline__ bool tc_block_end(int64_t r0, int64_t r_end) {
   return r1 >= r_end || (r1 >> kTcFlushShift) != (r0 >> kTcFlushShift);
 }
 
-template <typename T>
+// BATCH = false: one basis Y (n rows), thread blocks over contiguous ranges of
+// 64-row stages, scales from the pre-pass (cexp, per 4096-row chunk).
+// BATCH = true: thread block g is Gram block g of a batch (one pair's
+// v.gram_rows rows, at most 16,384), its column scales computed here over its
+// own rows, its partials in row g of `partials`.
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(kTcThreads, 1)
 gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const SolveState* __restrict__ st,
-                       int ncols_fixed, const int* __restrict__ cexp, double* __restrict__ partials, bool vec16) {
+                       int ncols_fixed, const int* __restrict__ cexp, double* __restrict__ partials, bool vec16,
+                       BatchView v) {
   int ncols = ncols_fixed;
-  if (ncols <= 0) {
-    if (st->done) return;
-    ncols = 2 * st->sbar + 1;
+  int64_t r_begin, r_end;
+  __shared__ int ce_blk[kMaxCols];   // BATCH: the block's column scales
+  if (BATCH) {
+    const int j = v.gblk_pair[blockIdx.x];
+    const BatchPair& bp = v.pairs[j];
+    const SolveState* sj = v.states + j;
+    if (sj->done) return;
+    ncols = 2 * sj->sbar + 1;
+    Y += bp.off;
+    n = bp.n;
+    // 16-byte copies need every column of this pair 16-byte aligned
+    vec16 = vec16 && ((uintptr_t)Y % 16 == 0);
+    r_begin = (int64_t)(blockIdx.x - bp.gblk0) * v.gram_rows;
+    r_end = r_begin + v.gram_rows < n ? r_begin + v.gram_rows : n;
+  } else {
+    if (ncols <= 0) {
+      if (st->done) return;
+      ncols = 2 * st->sbar + 1;
+    }
+    const int64_t nst_all = (n + kTcStageRows - 1) / kTcStageRows;
+    const int64_t spb = (nst_all + gridDim.x - 1) / gridDim.x;
+    r_begin = (int64_t)blockIdx.x * spb * kTcStageRows;
+    r_end = r_begin + spb * kTcStageRows;
+    if (r_end > n) r_end = n;
   }
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const bool c32 = ncols > kTcCols;
@@ -985,16 +1062,24 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
   __shared__ int abort_flag;
   __shared__ unsigned long long s_hi[kMaxPairs], s_lo[kMaxPairs];
   __shared__ double gacc[kMaxPairs];
-  __shared__ double c32sum[3][kMaxCols];
+  __shared__ double c32sum[1][kMaxCols];
   const uint32_t b_full = smem_addr(&bars[0]), b_empty = smem_addr(&bars[2]);
   const uint32_t b_tfull = smem_addr(&bars[4]), b_tempty = smem_addr(&bars[5]), b_drain = smem_addr(&bars[6]);
 
-  const int64_t nst_all = (n + kTcStageRows - 1) / kTcStageRows;
-  const int64_t spb = (nst_all + gridDim.x - 1) / gridDim.x;
-  const int64_t r_begin = (int64_t)blockIdx.x * spb * kTcStageRows;
-  int64_t r_end = r_begin + spb * kTcStageRows;
-  if (r_end > n) r_end = n;
   const int64_t nst = r_begin < r_end ? (r_end - r_begin + kTcStageRows - 1) / kTcStageRows : 0;
+  if (BATCH) {
+    // the largest biased exponent (dg_exp) of every column over this block's rows
+    for (int c = warp; c < ncols; c += kTcThreads / 32) {
+      int m = 1;
+      for (int64_t r = r_begin + lane; r < r_end; r += 32) m = max(m, dg_exp(widen(__ldg(Y + (int64_t)c * ld + r))));
+      m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
+      if (lane == 0) ce_blk[c] = m;
+    }
+  }
+  // scale exponents of the columns for the stage starting at row r0
+  auto ce_for = [&](int64_t r0) -> const int* {
+    return BATCH ? ce_blk : cexp + (r0 >> kDgChunkShift) * kMaxCols;
+  };
 
   // both stage buffers zero (columns >= ncols are never written)
   for (int e = t; e < (int)(2 * kTcStage / 16); e += kTcThreads)
@@ -1006,8 +1091,8 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
   }
   if (t == 0) {
     abort_flag = 0;
-    mbar_init(b_full, 8);   // one arrival per conversion warp
-    mbar_init(b_full + 8, 8);
+    mbar_init(b_full, kTcConvWarps);   // one arrival per conversion warp
+    mbar_init(b_full + 8, kTcConvWarps);
     mbar_init(b_empty, 1);
     mbar_init(b_empty + 8, 1);
     mbar_init(b_tfull, 1);
@@ -1030,16 +1115,16 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
   if (warp >= kTcConv0) {
     // ---- conversion warps (as in gram_partial_dg_kernel; buffer b = k & 1)
     const int cw = warp - kTcConv0;
-    dg_issue_raw(raw[0], Y, ld, r_begin, r_end, nct, cw, vec16);
-    dg_issue_raw(raw[1], Y, ld, r_begin + kTcStageRows, r_end, nct, cw, vec16);
+    tc_issue_raw(raw[0], Y, ld, r_begin, r_end, nct, cw, vec16);
+    tc_issue_raw(raw[1], Y, ld, r_begin + kTcStageRows, r_end, nct, cw, vec16);
     for (int64_t k = 0; k < nst; ++k) {
       const int b = (int)(k & 1);
       const int64_t r0 = r_begin + k * kTcStageRows;
-      const int* ce_g = cexp + (r0 >> kDgChunkShift) * kMaxCols;
+      const int* ce_g = ce_for(r0);
       asm volatile("cp.async.wait_group 1;" ::: "memory");
       if (k >= 2) mbar_wait(b_empty + 8 * b, (uint32_t)(((k - 2) >> 1) & 1), abort);   // MMAs of stage k - 2 done
       tc_convert(raw[b], tc_smem + (size_t)b * kTcStage, ce_g, nct, cw);
-      dg_issue_raw(raw[b], Y, ld, r0 + 2 * kTcStageRows, r_end, nct, cw, vec16);
+      tc_issue_raw(raw[b], Y, ld, r0 + 2 * kTcStageRows, r_end, nct, cw, vec16);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // digits visible to the tensor cores
       __syncwarp();
       if (lane == 0) mbar_arrive(b_full + 8 * b);
@@ -1083,23 +1168,23 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
     }
     __syncwarp();
   } else if (warp < kTcEpi0) {
-    // ---- column 32: binary64 FMA sums of y_i y_32, i = 0..32, rows split over three warps
+    // ---- column 32: binary64 FMA sums of y_i y_32, warp w taking i = 11 w .. 11 w + 10
     if (c32) {
       const int w = warp - kTcC32W0;
-      double acc[kMaxCols];
+      double acc[11];
 #pragma unroll
-      for (int i = 0; i < kMaxCols; ++i) acc[i] = 0.0;
-      for (int64_t r = r_begin + 32 * w + lane; r < r_end; r += 96) {
+      for (int k = 0; k < 11; ++k) acc[k] = 0.0;
+      for (int64_t r = r_begin + lane; r < r_end; r += 32) {
         const double y32 = widen(__ldg(Y + 32 * ld + r));
 #pragma unroll
-        for (int i = 0; i < kMaxCols; ++i) acc[i] = fma(widen(__ldg(Y + (int64_t)i * ld + r)), y32, acc[i]);
+        for (int k = 0; k < 11; ++k) acc[k] = fma(widen(__ldg(Y + (int64_t)(11 * w + k) * ld + r)), y32, acc[k]);
       }
 #pragma unroll
-      for (int i = 0; i < kMaxCols; ++i) {
-        double v = acc[i];
+      for (int k = 0; k < 11; ++k) {
+        double v = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) c32sum[w][i] = v;
+        if (lane == 0) c32sum[0][11 * w + k] = v;
       }
     }
   } else {
@@ -1111,7 +1196,7 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
       const int64_t r0 = r_begin + k * kTcStageRows;
       if (!tc_block_end(r0, r_end)) continue;
       ++blk;
-      const int* ce_g = cexp + (r0 >> kDgChunkShift) * kMaxCols;
+      const int* ce_g = ce_for(r0);
       mbar_wait(b_tfull, (uint32_t)(blk & 1), abort);
       tc_fence_after();
       const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
@@ -1122,10 +1207,10 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
       // both (i, j) and (j, i) (twice on the diagonal); X_ss only once, from
       // i <= j.
 #pragma unroll 1
-      for (int half = 0; half < 2; ++half) {
-        long long hi[16], lo[16];
+      for (int half = 0; half < 4; ++half) {
+        long long hi[8], lo[8];
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) hi[jj] = lo[jj] = 0;
+        for (int jj = 0; jj < 8; ++jj) hi[jj] = lo[jj] = 0;
 #pragma unroll 1
         for (int acc = 0; acc < kTcAcc; ++acc) {
           const int s = kTcAccA[acc] + q;
@@ -1133,14 +1218,14 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
           for (int l = 0; l < 4; ++l) {
             const int tt = kTcAccB[acc] + l;
             if (s > tt || s + tt > 11) continue;       // uniform: pairs s <= t, s + t <= 11
-            uint32_t x[16];
-            tc_ld16(x, tq + (uint32_t)(128 * acc + 32 * l + 16 * half));
+            uint32_t x[8];
+            tc_ld8(x, tq + (uint32_t)(128 * acc + 32 * l + 8 * half));
             tc_wait_ld();
             const int u = s + tt;
             const long long w = u < 6 ? (1ll << (5 * (5 - u))) : (1ll << (5 * (11 - u)));
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const int j = 16 * half + jj;
+            for (int jj = 0; jj < 8; ++jj) {
+              const int j = 8 * half + jj;
               if (s < tt || i <= j) {
                 const long long v =
                     (long long)__float2int_rz(__uint_as_float(x[jj]) * 0x1p48f) * (s < tt && i == j ? 2 * w : w);
@@ -1152,8 +1237,8 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
         }
         if (i < nct) {
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int j = 16 * half + jj;
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = 8 * half + jj;
             if (j < nct) {
               const int a = i < j ? i : j, bb = i < j ? j : i;
               const int p = a * ncols - a * (a - 1) / 2 + (bb - a);
@@ -1174,7 +1259,7 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
         const long long shi = (long long)s_hi[p], slo = (long long)s_lo[p];
         s_hi[p] = 0ull;
         s_lo[p] = 0ull;
-        const int ci_ = __ldg(ce_g + pi), cj_ = __ldg(ce_g + pj);
+        const int ci_ = ce_g[pi], cj_ = ce_g[pj];
         if (ci_ == 2047 || cj_ == 2047) {
           gacc[p] = __longlong_as_double(0x7ff8000000000000ll);
         } else {
@@ -1193,7 +1278,7 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
   for (int p = t; p < np; p += kTcThreads) {
     int pi, pj;
     pair_of(p, ncols, &pi, &pj);
-    const double v = pj >= kTcCols ? (c32sum[0][pi] + c32sum[1][pi]) + c32sum[2][pi] : gacc[p];
+    const double v = pj >= kTcCols ? c32sum[0][pi] : gacc[p];
     partials[(int64_t)blockIdx.x * kMaxPairs + p] = v;
   }
 }
@@ -1298,8 +1383,16 @@ __global__ void __launch_bounds__(256) batch_gram_reduce_kernel(BatchView v, con
 
 }  // namespace
 
-cudaError_t launch_batch_gram(const BatchView& v, const double* Y, int64_t LD, double* partials, cudaStream_t st) {
-  batch_gram_partial_kernel<<<v.ngblk, kGramThreads, 0, st>>>(v, Y, LD, partials);
+cudaError_t launch_batch_gram(const BatchView& v, const double* Y, int64_t LD, double* partials, cudaStream_t st,
+                              int gram_mode) {
+  if (gram_mode == 3) {
+    if (v.gram_rows > (1 << 14)) return cudaErrorInvalidValue;   // exact binary32 sums of one plane pair
+    const bool vec16 = ((uintptr_t)Y % 16 == 0) && ((size_t)LD * 8) % 16 == 0;
+    gram_partial_tc_kernel<double, true><<<v.ngblk, kTcThreads, tc_smem_bytes<double>(), st>>>(
+        Y, 0, LD, nullptr, 0, nullptr, partials, vec16, v);
+  } else {
+    batch_gram_partial_kernel<<<v.ngblk, kGramThreads, 0, st>>>(v, Y, LD, partials);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   batch_gram_reduce_kernel<<<v.npairs, 256, 0, st>>>(v, partials);
@@ -1332,11 +1425,14 @@ cudaError_t gram_prepare() {
   e = cudaFuncSetAttribute(gram_partial_dg_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)dg_smem_bytes<float>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(gram_partial_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(gram_partial_tc_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc_smem_bytes<double>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(gram_partial_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(gram_partial_tc_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc_smem_bytes<float>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gram_partial_tc_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_bytes<double>());
   if (e != cudaSuccess) return e;
   done[dev] = true;
   return cudaSuccess;
@@ -1371,8 +1467,8 @@ cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* /*ncols
       gram_chunk_exp_kernel<float><<<egrid, 256, 0, st>>>(static_cast<const float*>(Y), n, ld, state, ncols_fixed,
                                                           chunk_exp);
       if (gram_mode == 3)
-        gram_partial_tc_kernel<float><<<nblocks, kTcThreads, tc_smem_bytes<float>(), st>>>(
-            static_cast<const float*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
+        gram_partial_tc_kernel<float, false><<<nblocks, kTcThreads, tc_smem_bytes<float>(), st>>>(
+            static_cast<const float*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16, BatchView{});
       else
         gram_partial_dg_kernel<float><<<nblocks, kDgThreads, dg_smem_bytes<float>(), st>>>(
             static_cast<const float*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
@@ -1380,8 +1476,8 @@ cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* /*ncols
       gram_chunk_exp_kernel<double><<<egrid, 256, 0, st>>>(static_cast<const double*>(Y), n, ld, state,
                                                            ncols_fixed, chunk_exp);
       if (gram_mode == 3)
-        gram_partial_tc_kernel<double><<<nblocks, kTcThreads, tc_smem_bytes<double>(), st>>>(
-            static_cast<const double*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
+        gram_partial_tc_kernel<double, false><<<nblocks, kTcThreads, tc_smem_bytes<double>(), st>>>(
+            static_cast<const double*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16, BatchView{});
       else
         gram_partial_dg_kernel<double><<<nblocks, kDgThreads, dg_smem_bytes<double>(), st>>>(
             static_cast<const double*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);

@@ -245,7 +245,9 @@ struct BatchView {
 
 // batch.cu / per-file batched kernels
 cudaError_t launch_batch_mpk(const BatchView& v, double* Y, int64_t LD, int level, cudaStream_t st);
-cudaError_t launch_batch_gram(const BatchView& v, const double* Y, int64_t LD, double* partials, cudaStream_t st);
+// gram_mode 0: binary64 FMAs; 3: the tcgen05 digit Gram (v.gram_rows <= 16384)
+cudaError_t launch_batch_gram(const BatchView& v, const double* Y, int64_t LD, double* partials, cudaStream_t st,
+                              int gram_mode = 0);
 cudaError_t launch_batch_kappa(const BatchView& v, int sigma_max, cudaStream_t st);
 cudaError_t launch_batch_control(const BatchView& v, const double* leja, cudaStream_t st);
 cudaError_t launch_batch_recombine(const BatchView& v, double* Y, int64_t LD, double* x, cudaStream_t st);

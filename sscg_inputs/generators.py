@@ -23,7 +23,6 @@ import math
 
 import numpy as np
 import scipy.sparse as sp
-from scipy.sparse.csgraph import reverse_cuthill_mckee
 
 # seed = 1000 + index of the workload in the list of configurations
 CONFIG_SEEDS = {"poisson2d_64": 1000, "varcoef3d_160": 1001, "rgg_2m": 1002,
@@ -119,6 +118,81 @@ def uniform_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.n
     return np.random.default_rng(seed).uniform(lo, hi, n)
 
 
+def _exp_portable(y: np.ndarray) -> np.ndarray:
+    """exp(y) from IEEE-rounded multiplies and adds only (no libm), so that the
+    same inputs give the same bits on every platform: y = k ln2 + f with
+    0 <= f < ln2, exp(f) by its Taylor series to degree 24 (Horner), times 2^k."""
+    ln2 = 0.6931471805599453
+    k = np.floor(y / ln2)
+    f = y - k * ln2
+    p = np.ones_like(f)
+    for d in range(24, 0, -1):
+        p = p * f
+        p = p / float(d)
+        p = p + 1.0
+    return np.ldexp(p, k.astype(np.int64))
+
+
+def _icbrt(v: int) -> int:
+    """floor(v^(1/3)) for an integer v >= 0, by integer Newton steps."""
+    if v < 2:
+        return v
+    x = 1 << ((v.bit_length() + 2) // 3)
+    while True:
+        y = (2 * x + v // (x * x)) // 3
+        if y >= x:
+            break
+        x = y
+    while x * x * x > v:
+        x -= 1
+    while (x + 1) ** 3 <= v:
+        x += 1
+    return x
+
+
+def _rcm(A: sp.csr_matrix) -> np.ndarray:
+    """Reverse Cuthill-McKee order of a structurally symmetric matrix with every
+    tie broken by node index (a library's own ordering may break ties by its
+    sort's order, which differs between platforms).  Level by level from the
+    unvisited node of least degree: each level's new nodes are the frontier's
+    unvisited neighbours, taken in frontier order, each parent's sorted by
+    (degree, index), a node reached twice kept at its first parent."""
+    N = A.shape[0]
+    indptr, indices = A.indptr, A.indices
+    deg = np.diff(indptr)
+    visited = np.zeros(N, dtype=bool)
+    order = []
+    by_degree = np.lexsort((np.arange(N), deg))     # nodes by (degree, index)
+    start_at = 0
+    while True:
+        while start_at < N and visited[by_degree[start_at]]:
+            start_at += 1
+        if start_at >= N:
+            break
+        frontier = np.array([by_degree[start_at]], dtype=np.int64)
+        visited[frontier] = True
+        order.append(frontier)
+        while frontier.size:
+            counts = deg[frontier]
+            tot = int(counts.sum())
+            if tot == 0:
+                break
+            starts = indptr[frontier]
+            offs = np.arange(tot) - np.repeat(np.cumsum(counts) - counts, counts)
+            nb = indices[np.repeat(starts, counts) + offs].astype(np.int64)
+            parent = np.repeat(np.arange(frontier.size), counts)
+            m = ~visited[nb]
+            nb, parent = nb[m], parent[m]
+            o = np.lexsort((nb, deg[nb], parent))
+            nb = nb[o]
+            _, first = np.unique(nb, return_index=True)
+            nb = nb[np.sort(first)]
+            visited[nb] = True
+            order.append(nb)
+            frontier = nb
+    return np.concatenate(order)[::-1].astype(np.int64)
+
+
 def rgg_laplacian_csr(N: int, seed: int, avg_nnz: float = 27.0, shift_frac: float = 1e-4,
                       scale_decades: float = 3.0) -> CsrProblem:
     """Graph Laplacian of a 3D random geometric graph, RCM-ordered, shifted and scaled.
@@ -128,19 +202,29 @@ def rgg_laplacian_csr(N: int, seed: int, avg_nnz: float = 27.0, shift_frac: floa
     weights.  A = L + shift_frac * mean_degree * I, symmetrically permuted by
     reverse Cuthill-McKee, then S A S with S = diag(10^{U(0, scale_decades)/2})
     so that the diagonal scaling d_i = S_i^2 = 10^{U(0, scale_decades)}.
+
+    Every step is exact or IEEE-rounded arithmetic with a fixed tie order, so
+    the matrix is the same bit for bit on every platform: points on a 2^20
+    integer grid with integer squared distances, the radius as an integer cube
+    root, the ordering by _rcm, and 10^u from _exp_portable (a platform's libm
+    or sort could round or order differently, which would move edges at the
+    radius and with them the whole ordering).
     """
     rng = np.random.default_rng(seed)
     pts = rng.random((N, 3))
-    r = ((avg_nnz - 1.0) / (N * 4.0 * math.pi / 3.0)) ** (1.0 / 3.0)
-    ncell = max(1, int(1.0 / r))
-    cell = np.minimum((pts * ncell).astype(np.int64), ncell - 1)
+    Q = 1 << 20
+    qp = np.floor(pts * Q).astype(np.int64)                   # exact: pts * 2^20 is exact
+    c = (avg_nnz - 1.0) / (N * 4.0 * math.pi / 3.0)           # r^3
+    R = _icbrt(int(c * float(Q) ** 3))                          # radius in grid units
+    R2 = R * R
+    ncell = max(1, Q // max(R, 1))                             # cells at least R wide
+    cell = (qp * ncell) >> 20
     key = (cell[:, 2] * ncell + cell[:, 1]) * ncell + cell[:, 0]
     order = np.argsort(key, kind="stable")
     key_s = key[order]
     starts = np.searchsorted(key_s, np.arange(ncell ** 3), side="left")
     ends = np.searchsorted(key_s, np.arange(ncell ** 3), side="right")
     src_all, dst_all = [], []
-    r2 = r * r
     for dz in (-1, 0, 1):
         for dy in (-1, 0, 1):
             for dx in (-1, 0, 1):
@@ -156,8 +240,8 @@ def rgg_laplacian_csr(N: int, seed: int, avg_nnz: float = 27.0, shift_frac: floa
                 src = np.repeat(ii, cnt)
                 offs = np.arange(tot) - np.repeat(np.cumsum(cnt) - cnt, cnt)
                 dst = order[np.repeat(s0, cnt) + offs]
-                d = pts[src] - pts[dst]
-                keep = (np.einsum("ij,ij->i", d, d) < r2) & (src != dst)
+                d = qp[src] - qp[dst]
+                keep = (np.einsum("ij,ij->i", d, d) < R2) & (src != dst)
                 src_all.append(src[keep])
                 dst_all.append(dst[keep])
     src = np.concatenate(src_all)
@@ -166,14 +250,14 @@ def rgg_laplacian_csr(N: int, seed: int, avg_nnz: float = 27.0, shift_frac: floa
     deg = np.asarray(W.sum(axis=1)).ravel()
     L = sp.diags(deg) - W
     A = (L + shift_frac * deg.mean() * sp.identity(N)).tocsr()
-    perm = reverse_cuthill_mckee(A, symmetric_mode=True)
+    perm = _rcm(A)
     A = A[perm][:, perm].tocsr()
-    s = 10.0 ** (0.5 * rng.uniform(0.0, scale_decades, N))
-    A = sp.diags(s) @ A @ sp.diags(s)
-    A = A.tocsr()
     A.sort_indices()
-    return CsrProblem(N, A.indptr.astype(np.int64), A.indices.astype(np.int32),
-                      A.data.astype(np.float64))
+    s = _exp_portable(rng.uniform(0.0, scale_decades, N) * (0.5 * math.log(10.0)))
+    rows = np.repeat(np.arange(N), np.diff(A.indptr))
+    val = A.data * s[rows]
+    val = val * s[A.indices]
+    return CsrProblem(N, A.indptr.astype(np.int64), A.indices.astype(np.int32), val.astype(np.float64))
 
 
 def batched_stencils(count: int, seed: int, n_lo: float = 1e3, n_hi: float = 2.6e5,

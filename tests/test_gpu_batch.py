@@ -46,12 +46,17 @@ def split(systems, v):
     return out
 
 
-def test_batch_matches_oracle_per_pair(pkg):
+@pytest.mark.parametrize("gram_mode", [0, 3])
+def test_batch_matches_oracle_per_pair(pkg, gram_mode):
+    """With the binary64 Gram and with the tcgen05 digit Gram (one thread block
+    per 2048-row Gram block of a pair, its scales computed over its rows)."""
     systems, solvers, nrhs, b = build(pkg, 7, 1003, 300, 9000, 3)
     bt = torch.tensor(b, device="cuda")
     xt = torch.zeros_like(bt)
     s_max = [8 if st.dim == 2 else 12 for st, _ in systems]
-    rc, stats = pkg.sscg.sscg_solve_batch([s.h for s in solvers], nrhs, bt, xt, 1e-10, s_max, "newton")
+    rc, stats = pkg.sscg.sscg_solve_batch([s.h for s in solvers], nrhs, bt, xt, 1e-10, s_max, "newton",
+                                          pkg.sscg.sscg_opts_default(gram_mode=gram_mode))
+    assert pkg.sscg.sscg_wait_failures() == 0
     assert rc == 0 and stats["converged"] == stats["npairs"] == sum(nrhs)
     assert stats["graph_launches"] == 1 and stats["host_syncs"] == 1
     x = xt.cpu().numpy()
@@ -129,10 +134,14 @@ def test_batch_tile_shapes_and_their_autotuner(pkg):
     with pytest.raises(pkg.sscg.SscgError):
         pkg.sscg.sscg_solve_batch(hs, nrhs, bt, torch.zeros_like(bt), 1e-10, s_max, "newton",
                                   pkg.sscg.sscg_opts_default(batch_chunk_rows=64))
-    for mode in (1, 2):  # the batch has neither the binary32-pair nor the tensor-core Gram
+    for mode in (1, 2):  # the batch has neither the binary32-pair nor the mma.sync digit Gram
         with pytest.raises(pkg.sscg.SscgError):
             pkg.sscg.sscg_solve_batch(hs, nrhs, bt, torch.zeros_like(bt), 1e-10, s_max, "newton",
                                       pkg.sscg.sscg_opts_default(gram_mode=mode))
+    # the tcgen05 Gram sums at most 16384 rows per thread block
+    with pytest.raises(pkg.sscg.SscgError):
+        pkg.sscg.sscg_solve_batch(hs, nrhs, bt, torch.zeros_like(bt), 1e-10, s_max, "newton",
+                                  pkg.sscg.sscg_opts_default(gram_mode=3, batch_gram_rows=32768))
 
 
 def test_batched_hscg_matches_per_pair_hscg(pkg):
