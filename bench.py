@@ -668,13 +668,23 @@ def main():
         levels = sum(h["sbar"] for h in hist_p)
         mpk_tops = lane_ops / (phase_ms["mpk"] / 1e3) / 1e12
         peak_ops = fp64_peak / 2.0   # one FMA = 2 flop = one lane operation
-        mpk_roof = {"bound": "alu", "kernel": "stencil_mpk_grid_kernel (one matrix-powers level, both chains)",
+        # algorithmic HBM bytes of the phase: per level the operator (diag and
+        # the three face arrays, 32 B per cell) and P_l, R_l read, P_{l+1},
+        # R_{l+1} written (the last level of a block advances P only)
+        mpk_bytes = sum(n * (32.0 * h["sbar"] + 32.0 * (h["sbar"] - 0.5)) for h in hist_p)
+        mpk_gbs = mpk_bytes / (phase_ms["mpk"] / 1e3) / 1e9
+        mpk_roof = {"bound": "alu", "kernel": "stencil_mpk_hybrid_kernel (one matrix-powers level, both chains; "
+                                              "cells split between binary64 FMAs and exact integer products)",
                     "achieved": mpk_tops, "peak": peak_ops, "unit": "T binary64 lane-ops/s",
                     "frac": mpk_tops / peak_ops,
                     "traffic": (MPK_DRAM_BYTES_PER_CELL * n) if MPK_DRAM_BYTES_PER_CELL else None,
                     "traffic_source": traffic_src, "launches": levels,
-                    "algorithmic": f"{ops} binary64 lane operations per cell and level",
-                    "peak_note": fp64_note + " (as lane operations: TFLOP/s / 2)",
+                    "algorithmic": f"{ops} binary64 operations per cell and level (formed by the FP64 unit or, in "
+                                   f"the integer warps, exactly by the integer pipes)",
+                    "peak_note": fp64_note + " (as lane operations: TFLOP/s / 2); the integer warps add work "
+                                 "beyond the FP64 unit, so frac can exceed 1",
+                    "hbm": {"achieved_gbs": mpk_gbs, "peak_gbs": HBM_PEAK_GBS, "frac": mpk_gbs / HBM_PEAK_GBS,
+                            "algorithmic": "64 B per cell and level (operator 32, two columns read, two written)"},
                     "timing": "CUDA events around the matrix-powers phase of a profiled solve"}
     if args.gram_mode == 0:
         roofline = {"bound": "alu", "kernel": "gram_partial+gram_reduce (G = Y^T Y, FP64)",
