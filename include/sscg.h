@@ -95,6 +95,12 @@ typedef struct {
                             the two share the level between GB300's FP64 unit and its integer pipes);
                             16 = FMA chain only, 0 = integer products only; default -1 = the library's
                             tuned share */
+  int rec_fp64_per16;    /* the recovery x += Y x', r = Y r', p = Y p' (eq. coords) with a binary64 basis:
+                            of every 16 groups of 32 rows, this many are summed by binary64 FMA chains and
+                            the others as exact integer dot products rounded once per output (within
+                            m (1 + 2^-5) 2^-54 of the largest term before that rounding, m <= 34 terms;
+                            an FMA chain is bounded by m 2^-53 sum|terms|); 16 = FMA only, 0 = integer
+                            only; default -1 = the library's tuned share */
 } sscg_opts;
 
 /* Per-outer-loop decision record (Alg. 5): s-bar_k, s-tilde_k, s_k, c at the
@@ -361,6 +367,16 @@ int sscg_wait_failures(int* flag, int clear);
  * length sbar+1 (entry 0 unused).  kappa_l = +inf when lmin <= kappa_cut * lmax. */
 int sscg_kappa(const double* G, int ldg, int sbar, double kappa_cut, double* kappa, double* lmin,
                double* lmax, void* cuda_stream);
+
+/* The recovery of eq. (coords), Algorithm 5: x += Y x', then Y[:,0] = Y p'
+ * and Y[:,1] = Y r' (p and r overwrite columns 0 and 1, as in a solve), over
+ * the first ncols columns of Y (1 <= ncols <= 33).  Y: device, column major,
+ * leading dimension ldy >= n, at least max(ncols, 2) columns, read and written.  coef: HOST array of 3*ncols
+ * doubles, x' then r' then p'.  x: device, length n, read and written.
+ * rec_fp64_per16: the split of sscg_opts.rec_fp64_per16 (-1..16).  Waits for
+ * the stream; SSCG_ERR_INVALID_ARG on bad sizes or split. */
+int sscg_recombine(double* Y, int64_t n, int64_t ldy, int ncols, const double* coef, double* x, int rec_fp64_per16,
+                   void* cuda_stream);
 
 /* The first s Leja points of [-1, 1] starting 1, -1 (eq. newtbasis on the
  * reference interval), computed on the device.  t: HOST array of length s. */

@@ -137,6 +137,10 @@ class Options:
     # gram: a callable Y -> G used instead of Y^T Y (G = Y^T Y of Section 2
     # computed another way, for studies of that arithmetic); None: Y.T @ Y
     gram: object = None
+    # recover: a callable (Y, x', r', p', x) -> (x, r, p) used instead of
+    # eq. (coords) as written (for studies of the recovery's rounding); None:
+    # x + Y x', Y r', Y p'
+    recover: object = None
 
 
 def kappa_estimates(G: np.ndarray, sbar: int, kappa_cut: float = KAPPA_CUT):
@@ -339,9 +343,12 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
             hist.append(dict(sbar=sbar, stilde=stilde, sk=0, kappa=kap.tolist(), c=c_start))
             break
         Yn = Y[:, :n]
-        x = x + Yn @ xc
-        r = Yn @ rc
-        p = Yn @ pc
+        if o.recover is None:
+            x = x + Yn @ xc
+            r = Yn @ rc
+            p = Yn @ pc
+        else:
+            x, r, p = o.recover(Yn, xc, rc, pc, x)
         m += sk
         s_prev = sk
         hist.append(dict(sbar=sbar, stilde=stilde, sk=sk, kappa=kap.tolist(), c_start=c_start,

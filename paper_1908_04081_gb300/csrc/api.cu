@@ -84,6 +84,7 @@ struct sscg_ctx {
   bool graph_y32 = false;
   int graph_gram_mode = 0;
   int graph_mpk_split = -1;
+  int graph_rec_split = -1;
   int graph_launches = 0;
   double last_lmin = 0.0, last_lmax = 0.0;
 };
@@ -189,7 +190,8 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
   CK(launch_control(ds, h->G.p, kMaxCols, h->leja, h->hist.n ? h->hist.p : nullptr, st));
   ++count;
   if ((rc = mark(4))) return rc;
-  CK(launch_recombine(ds, h->Y.p, h->ld, h->x.p, y32 ? h->r.p : nullptr, y32 ? h->p.p : nullptr, h->n, y32, st));
+  CK(launch_recombine(ds, h->Y.p, h->ld, h->x.p, y32 ? h->r.p : nullptr, y32 ? h->p.p : nullptr, h->n, y32, st,
+                      h->host_state->rec_fp64_per16));
   ++count;
   if ((rc = mark(5))) return rc;
   if (y32) {
@@ -210,7 +212,7 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
 // WHILE node repeats one outer loop until the device sets done.
 int build_graph(sscg_ctx* h, int sigma, bool y32) {
   if (h->graph && h->graph_sigma == sigma && h->graph_y32 == y32 && h->graph_gram_mode == h->host_state->gram_mode &&
-      h->graph_mpk_split == h->host_state->mpk_fp64_per16)
+      h->graph_mpk_split == h->host_state->mpk_fp64_per16 && h->graph_rec_split == h->host_state->rec_fp64_per16)
     return SSCG_OK;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
@@ -264,6 +266,7 @@ int build_graph(sscg_ctx* h, int sigma, bool y32) {
   h->graph_y32 = y32;
   h->graph_gram_mode = h->host_state->gram_mode;
   h->graph_mpk_split = h->host_state->mpk_fp64_per16;
+  h->graph_rec_split = h->host_state->rec_fp64_per16;
   h->graph_launches = nl + 1;
   return SSCG_OK;
 }
@@ -293,6 +296,7 @@ void fill_state_config(SolveState& s, int sigma, double tol, int basis, const ss
   s.fp32_drop = std::ldexp(1.0, -4);  // FP32 basis: replace r after a 2^-4 drop
   s.gram_mode = o.gram_mode;
   s.mpk_fp64_per16 = o.mpk_fp64_per16;
+  s.rec_fp64_per16 = o.rec_fp64_per16;
   s.rho_last = 1.0;
   for (int l = 0; l < kMaxS; ++l) {
     s.theta[l] = 0.0;  // monomial basis until Ritz values exist
@@ -311,6 +315,7 @@ int validate_opts(const sscg_opts& o) {
     return SSCG_ERR_INVALID_ARG;
   if (!(o.eps > 0.0) || !(o.kappa_cut >= 0.0)) return SSCG_ERR_INVALID_ARG;
   if (o.mpk_fp64_per16 < -1 || o.mpk_fp64_per16 > 16) return SSCG_ERR_INVALID_ARG;
+  if (o.rec_fp64_per16 < -1 || o.rec_fp64_per16 > 16) return SSCG_ERR_INVALID_ARG;
   return SSCG_OK;
 }
 
@@ -359,6 +364,7 @@ void sscg_opts_default(sscg_opts* o) {
   o->batch_chunk_rows = 0;
   o->batch_gram_rows = 0;
   o->mpk_fp64_per16 = -1;
+  o->rec_fp64_per16 = -1;
 }
 
 int sscg_create_csr(sscg_t* out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
@@ -941,7 +947,7 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
       if ((e2 = launch_batch_gram(v, d_Y.p, LD, d_part.p, st, o.gram_mode)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_kappa(v, sigma_max, st)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_control(v, d_leja, st)) != cudaSuccess) return e2;
-      if ((e2 = launch_batch_recombine(v, d_Y.p, LD, x, st)) != cudaSuccess) return e2;
+      if ((e2 = launch_batch_recombine(v, d_Y.p, LD, x, st, o.rec_fp64_per16)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_check(v, b, x, d_rt.p, d_Y.p, LD, d_part.p, st)) != cudaSuccess) return e2;
       return launch_batch_end(v, cond, use_cond, st);
     };
@@ -1421,6 +1427,28 @@ int sscg_kappa(const double* G, int ldg, int sbar, double kappa_cut, double* kap
   cudaStream_t st = (cudaStream_t)cuda_stream;
   CK(launch_kappa(G, ldg, nullptr, sbar, kappa_cut, kappa, lmin, lmax, sbar, st));
   CK(cudaStreamSynchronize(st));
+  return SSCG_OK;
+}
+
+int sscg_recombine(double* Y, int64_t n, int64_t ldy, int ncols, const double* coef, double* x, int rec_fp64_per16,
+                   void* cuda_stream) {
+  if (!Y || !coef || !x || n <= 0 || ldy < n || ncols < 1 || ncols > kMaxCols) return SSCG_ERR_INVALID_ARG;
+  if (rec_fp64_per16 < -1 || rec_fp64_per16 > 16) return SSCG_ERR_INVALID_ARG;
+  SolveState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  hs.nc = ncols;
+  for (int c = 0; c < ncols; ++c) {
+    hs.xc[c] = coef[c];
+    hs.rc[c] = coef[ncols + c];
+    hs.pc[c] = coef[2 * ncols + c];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  DevBuf<SolveState> ds;
+  CK(ds.ensure(1));
+  CK(cudaMemcpyAsync(ds.p, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+  CK(launch_recombine(ds.p, Y, ldy, x, nullptr, nullptr, n, false, st, rec_fp64_per16));
+  CK(cudaStreamSynchronize(st));
+  ds.release();
   return SSCG_OK;
 }
 

@@ -105,4 +105,35 @@ __device__ __forceinline__ double exact_dot(const Limbs (&c)[K], const Limbs (&y
   return to_binary64(S, Em, ok);
 }
 
+// x / 2^d rounded to nearest (ties toward +infinity), d >= 1
+__device__ __forceinline__ long long shift_round(long long x, int d) { return shift_down(shift_down(x, d - 1) + 1, 1); }
+
+// A running sum of up to 2^H products whose exponents are not known in
+// advance (a long dot product streamed term by term).  The sum is held in
+// units of 2^(E - 2106 + H), E the largest exponent sum seen so far: a product
+// with a larger one first re-aligns the running sum, and each product is
+// added at the current alignment; both roundings are to nearest.  Bound, for
+// m terms of normal operands: each product is off by at most 1/2 + 2^(1-H)
+// units and each re-alignment by 1/2 unit of the final alignment, while the
+// largest |term| is at least 2^(60-H) units, so before the final rounding the
+// sum is within m (1 + 2^(1-H)) 2^(H-60) of the largest |term| (2^-48.9 for
+// m = 34, H = 6; a binary64 FMA chain is bounded by m 2^-53 sum|terms|).
+// |S| stays below 2^H (2^(62-H) + 1) < 2^63.
+template <int H>
+struct OnlineSum {
+  long long S;
+  int E;
+  __device__ __forceinline__ OnlineSum() : S(0), E(0) {}
+  __device__ __forceinline__ void add(const Limbs& c, const Limbs& y) {
+    const int Ej = c.e + y.e;
+    if (Ej > E) {
+      S = shift_round(S, Ej - E);
+      E = Ej;
+    }
+    S += shift_round(limb_product(c, y), E - Ej + H);
+  }
+  // the sum rounded once to binary64; ok cleared outside the normal range
+  __device__ __forceinline__ double result(bool& ok) const { return to_binary64(S, E + H - 3, ok); }
+};
+
 }  // namespace sscg

@@ -894,31 +894,6 @@ __device__ __forceinline__ void tc_ld8(uint32_t (&r)[8], uint32_t taddr) {
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// the 12 digit planes of 8 rows of one column into the 16-byte units
-// unit + t * plane_stride (two f16 bit patterns per word, row 2w in the low half)
-__device__ __forceinline__ void tc_store8(const double (&v)[8], int ce, unsigned char* unit, uint32_t plane_stride) {
-  unsigned h[8], l[8], sg[4];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const unsigned long long F = dg_fixed(v[k], ce);
-    h[k] = (unsigned)(F >> 32);
-    l[k] = (unsigned)F;
-  }
-#pragma unroll
-  for (int w = 0; w < 4; ++w)
-    sg[w] = (((unsigned)((unsigned long long)__double_as_longlong(v[2 * w]) >> 63)) << 15) |
-            (((unsigned)((unsigned long long)__double_as_longlong(v[2 * w + 1]) >> 63)) << 31);
-#define TC_PLANE(t)                                                                                       \
-  *reinterpret_cast<uint4*>(unit + (t) * plane_stride) =                                                  \
-      make_uint4(dg_digit<t>(h[0], l[0]) | (dg_digit<t>(h[1], l[1]) << 16) | sg[0],                       \
-                 dg_digit<t>(h[2], l[2]) | (dg_digit<t>(h[3], l[3]) << 16) | sg[1],                       \
-                 dg_digit<t>(h[4], l[4]) | (dg_digit<t>(h[5], l[5]) << 16) | sg[2],                       \
-                 dg_digit<t>(h[6], l[6]) | (dg_digit<t>(h[7], l[7]) << 16) | sg[3]);
-  TC_PLANE(0) TC_PLANE(1) TC_PLANE(2) TC_PLANE(3) TC_PLANE(4) TC_PLANE(5)
-  TC_PLANE(6) TC_PLANE(7) TC_PLANE(8) TC_PLANE(9) TC_PLANE(10) TC_PLANE(11)
-#undef TC_PLANE
-}
-
 // the 12 digit planes of 4 consecutive rows of one column: words 2h, 2h + 1
 // of the 16-byte units unit + t * plane_stride
 __device__ __forceinline__ void tc_store4(const double (&v)[4], int ce, unsigned char* unit, uint32_t plane_stride,

@@ -96,6 +96,7 @@ struct SolveState {
   double prev_fail;   // relative true residual at the last failed convergence check
   int gram_mode;      // 0: binary64 Gram; 1: binary32-pair products; 2, 3: f16 digit products (mma.sync, tcgen05)
   int mpk_fp64_per16; // warps (of 16) on the binary64 FMA chain in stencil levels; -1: library default
+  int rec_fp64_per16; // row groups (of 16) on the binary64 FMA chains in the recovery; -1: library default
   int fp32_replace_pending, fp32_replacements;
   double c, psi, normb, upd_relres;
   // Meurant-Tichy state (Algs. 3-4)
@@ -177,8 +178,12 @@ cudaError_t leja_table(const double** table, cudaStream_t st);
 // Basis storage: y32 = false: Y is double and columns 0/1 are p and r
 // themselves; y32 = true: Y is float and p, r live in the binary64 vectors
 // p64, r64 (columns 0/1 of Y hold their binary32 roundings).
+// With a binary64 basis, fp64_per16 of every 16 groups of 32 rows are summed
+// by binary64 FMAs and the others by exact integer dot products (16: FMA only;
+// negative: kRecFp64Per16); a binary32 basis always takes the FMA chains.
+constexpr int kRecFp64Per16 = 9;
 cudaError_t launch_recombine(const SolveState* state, void* Y, int64_t ld, double* x, double* r64, double* p64,
-                             int64_t n, bool y32, cudaStream_t st);
+                             int64_t n, bool y32, cudaStream_t st, int fp64_per16 = 16);
 cudaError_t launch_init_state(SolveState* state, const Operator& A, const double* b, const double* x,
                               void* Y, int64_t ld, double* r64, double* p64, double* partials, int nblocks,
                               bool y32, cudaStream_t st);
@@ -250,7 +255,8 @@ cudaError_t launch_batch_gram(const BatchView& v, const double* Y, int64_t LD, d
                               int gram_mode = 0);
 cudaError_t launch_batch_kappa(const BatchView& v, int sigma_max, cudaStream_t st);
 cudaError_t launch_batch_control(const BatchView& v, const double* leja, cudaStream_t st);
-cudaError_t launch_batch_recombine(const BatchView& v, double* Y, int64_t LD, double* x, cudaStream_t st);
+cudaError_t launch_batch_recombine(const BatchView& v, double* Y, int64_t LD, double* x, cudaStream_t st,
+                                   int fp64_per16 = -1);
 cudaError_t launch_batch_check(const BatchView& v, const double* b, const double* x, double* rt, double* Y,
                                int64_t LD, double* partials, cudaStream_t st);
 cudaError_t launch_batch_init(const BatchView& v, const double* b, double* x, double* Y, int64_t LD,

@@ -9,6 +9,7 @@
 // stay a small fraction of the FP64 work.
 #include <math.h>
 
+#include "exact_sum.cuh"
 #include "sscg_internal.cuh"
 
 namespace sscg {
@@ -103,6 +104,117 @@ __global__ void __launch_bounds__(kVecThreads) recombine_kernel(const SolveState
     }
     Y[i] = (T)sp;
     Y[ld + i] = (T)sr;
+  }
+}
+
+// One row of the recovery as binary64 FMA chains (the order of
+// recombine_kernel).  Out of line: the integer path calls it only for rows
+// with Inf/NaN operands or a sum outside the normal range.
+__device__ __noinline__ void recombine_row_fma(const double* __restrict__ Y, int64_t ld, int nc,
+                                               const double* cx, const double* cr, const double* cp,
+                                               int64_t i, double& sx, double& sr, double& sp) {
+  sx = 0.0;
+  sr = 0.0;
+  sp = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    const double y = Y[(int64_t)c * ld + i];
+    sx = fma(y, cx[c], sx);
+    sr = fma(y, cr[c], sr);
+    sp = fma(y, cp[c], sp);
+  }
+}
+
+// The recovery with a binary64 basis, its binary64 work split between two
+// units (as the stencil matrix-powers level): rows go in groups of 32 (one
+// warp), and of every 16 groups `fp64_per16` are summed as the binary64 FMA
+// chains of recombine_kernel, the others as exact integer dot products
+// (exact_sum.cuh): each of x + Y x', Y r', Y p' is a streamed sum of at most
+// 34 products (x itself enters as x * 1), aligned online, rounded once.  The
+// coefficients are the same for every row, so their limbs are formed once
+// per block; each y is split once and feeds three sums.  A row's form
+// depends only on its position, so results are reproducible.
+constexpr int kRecHead = 6;   // headroom bits: up to 64 terms
+static_assert(kMaxCols + 1 <= (1 << kRecHead), "recovery terms within the integer sum's headroom");
+
+// Coefficients x', r', p' of a state into shared memory (values and limbs),
+// by threads 0..kMaxCols-1; returns nonzero in every thread of the block when
+// a coefficient is Inf/NaN (the block then takes the FMA chains).  Ends with
+// a block barrier.
+__device__ __forceinline__ int rec_load_coef(const SolveState* __restrict__ st, int nc, double* cx, double* cr,
+                                             double* cp, int4 (*cl)[3]) {
+  unsigned bad = 0;
+  if (threadIdx.x < kMaxCols) {
+    const int c = threadIdx.x;
+    cx[c] = st->xc[c];
+    cr[c] = st->rc[c];
+    cp[c] = st->pc[c];
+    if (c < nc) {
+      const Limbs lx = to_limbs(cx[c], bad), lr = to_limbs(cr[c], bad), lp = to_limbs(cp[c], bad);
+      cl[c][0] = make_int4(lx.a, lx.b, lx.e, 0);
+      cl[c][1] = make_int4(lr.a, lr.b, lr.e, 0);
+      cl[c][2] = make_int4(lp.a, lp.b, lp.e, 0);
+    }
+  }
+  return __syncthreads_or((int)bad);
+}
+
+// Row i of the recovery: on the FMA chains when `fma_row`, else as exact
+// integer dot products (falling back to the chains for non-finite operands or
+// sums outside the normal range).  sx includes x_i.
+__device__ __forceinline__ void rec_row(const double* __restrict__ Y, int64_t ld, int nc, const double* cx,
+                                        const double* cr, const double* cp, const int4 (*cl)[3], int64_t i,
+                                        double xi, bool fma_row, double& sx, double& sr, double& sp) {
+  if (fma_row) {
+    sx = 0.0;
+    sr = 0.0;
+    sp = 0.0;
+    for (int c = 0; c < nc; ++c) {
+      const double y = Y[(int64_t)c * ld + i];
+      sx = fma(y, cx[c], sx);
+      sr = fma(y, cr[c], sr);
+      sp = fma(y, cp[c], sp);
+    }
+    sx += xi;
+    return;
+  }
+  unsigned ybad = 0;
+  OnlineSum<kRecHead> ax, ar, ap;
+  ax.add(Limbs{1 << 30, 0, 1023}, to_limbs(xi, ybad));   // x * 1.0
+#pragma unroll 2
+  for (int c = 0; c < nc; ++c) {
+    const Limbs ly = to_limbs(Y[(int64_t)c * ld + i], ybad);
+    const int4 lx = cl[c][0], lr = cl[c][1], lp = cl[c][2];
+    ax.add(Limbs{lx.x, lx.y, lx.z}, ly);
+    ar.add(Limbs{lr.x, lr.y, lr.z}, ly);
+    ap.add(Limbs{lp.x, lp.y, lp.z}, ly);
+  }
+  bool ok = true;
+  sx = ax.result(ok);
+  sr = ar.result(ok);
+  sp = ap.result(ok);
+  if (!ok || ybad) {
+    recombine_row_fma(Y, ld, nc, cx, cr, cp, i, sx, sr, sp);
+    sx += xi;
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads, 4) recombine_hybrid_kernel(const SolveState* __restrict__ st,
+                                                                          double* __restrict__ Y, int64_t ld,
+                                                                          double* __restrict__ x, int64_t n,
+                                                                          int fp64_per16) {
+  if (st->done) return;
+  const int nc = st->nc;
+  __shared__ double cx[kMaxCols], cr[kMaxCols], cp[kMaxCols];
+  __shared__ int4 cl[kMaxCols][3];   // limbs (a, b, e) of the x', r', p' coefficients
+  const int coef_bad = rec_load_coef(st, nc, cx, cr, cp, cl);
+  const unsigned f16 = (unsigned)fp64_per16;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned g = (unsigned)(i >> 5);   // the row group: the same for the 32 lanes of a warp
+    double sx, sr, sp;
+    rec_row(Y, ld, nc, cx, cr, cp, cl, i, x[i], coef_bad || ((g * f16) & 15u) < f16, sx, sr, sp);
+    x[i] = sx;
+    Y[i] = sp;
+    Y[ld + i] = sr;
   }
 }
 
@@ -494,9 +606,15 @@ __global__ void __launch_bounds__(kVecThreads) batch_zero_x_kernel(BatchView v, 
   }
 }
 
+// The batched recovery: each chunk's rows with the coefficients of its pair,
+// split between the FMA chains and exact integer dot products as
+// recombine_hybrid_kernel (row groups of 32 rows counted from the pair's
+// first row; fp64_per16 = 16: FMA chains only).
 __global__ void __launch_bounds__(kVecThreads) batch_recombine_kernel(BatchView v, double* __restrict__ Y, int64_t LD,
-                                                                      double* __restrict__ x) {
+                                                                      double* __restrict__ x, int fp64_per16) {
   __shared__ double cx[kMaxCols], cr[kMaxCols], cp[kMaxCols];
+  __shared__ int4 cl[kMaxCols][3];
+  const unsigned f16 = (unsigned)fp64_per16;
   for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
     const int j = v.chunk_pair[c];
     const BatchPair& bp = v.pairs[j];
@@ -504,25 +622,17 @@ __global__ void __launch_bounds__(kVecThreads) batch_recombine_kernel(BatchView 
     if (st->done) continue;
     const int nc = st->nc;
     __syncthreads();
-    if (threadIdx.x < kMaxCols) {
-      cx[threadIdx.x] = st->xc[threadIdx.x];
-      cr[threadIdx.x] = st->rc[threadIdx.x];
-      cp[threadIdx.x] = st->pc[threadIdx.x];
-    }
-    __syncthreads();
+    const int coef_bad = rec_load_coef(st, nc, cx, cr, cp, cl);
     const int64_t r0 = (int64_t)(c - bp.chunk0) * v.chunk_rows;
     int64_t r1 = r0 + v.chunk_rows;
     if (r1 > bp.n) r1 = bp.n;
     double* Yp = Y + bp.off;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      double sx = 0.0, sr = 0.0, sp = 0.0;
-      for (int k = 0; k < nc; ++k) {
-        const double y = Yp[(int64_t)k * LD + i];
-        sx = fma(y, cx[k], sx);
-        sr = fma(y, cr[k], sr);
-        sp = fma(y, cp[k], sp);
-      }
-      x[bp.off + i] += sx;
+      const unsigned g = (unsigned)(i >> 5);
+      double sx, sr, sp;
+      rec_row(Yp, LD, nc, cx, cr, cp, cl, i, x[bp.off + i], f16 >= 16u || coef_bad || ((g * f16) & 15u) < f16, sx,
+              sr, sp);
+      x[bp.off + i] = sx;
       Yp[i] = sp;
       Yp[LD + i] = sr;
     }
@@ -852,8 +962,10 @@ cudaError_t launch_batch_init(const BatchView& v, const double* b, double* x, do
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_recombine(const BatchView& v, double* Y, int64_t LD, double* x, cudaStream_t st) {
-  batch_recombine_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, Y, LD, x);
+cudaError_t launch_batch_recombine(const BatchView& v, double* Y, int64_t LD, double* x, cudaStream_t st,
+                                   int fp64_per16) {
+  batch_recombine_kernel<<<chunk_grid(v), kVecThreads, 0, st>>>(v, Y, LD, x,
+                                                                fp64_per16 < 0 ? kRecFp64Per16 : fp64_per16);
   return cudaGetLastError();
 }
 
@@ -919,8 +1031,11 @@ cudaError_t launch_batch_arm(cudaGraphConditionalHandle cond, cudaStream_t st) {
 }
 
 cudaError_t launch_recombine(const SolveState* state, void* Y, int64_t ld, double* x, double* r64, double* p64,
-                             int64_t n, bool y32, cudaStream_t st) {
-  if (y32)
+                             int64_t n, bool y32, cudaStream_t st, int fp64_per16) {
+  const int f16 = fp64_per16 < 0 ? kRecFp64Per16 : fp64_per16;
+  if (!y32 && f16 < 16)
+    recombine_hybrid_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(state, static_cast<double*>(Y), ld, x, n, f16);
+  else if (y32)
     recombine_kernel<float><<<vec_grid(n), kVecThreads, 0, st>>>(state, static_cast<float*>(Y), ld, x, r64, p64, n);
   else
     recombine_kernel<double><<<vec_grid(n), kVecThreads, 0, st>>>(state, static_cast<double*>(Y), ld, x, nullptr,

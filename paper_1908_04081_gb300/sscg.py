@@ -34,7 +34,8 @@ class Opts(C.Structure):
                 ("y_fp32", C.c_int), ("variant", C.c_int), ("check_every", C.c_int),
                 ("use_graph", C.c_int), ("profile", C.c_int), ("c_const", C.c_double),
                 ("eps", C.c_double), ("kappa_cut", C.c_double), ("gram_mode", C.c_int),
-                ("batch_chunk_rows", C.c_int), ("batch_gram_rows", C.c_int), ("mpk_fp64_per16", C.c_int)]
+                ("batch_chunk_rows", C.c_int), ("batch_gram_rows", C.c_int), ("mpk_fp64_per16", C.c_int),
+                ("rec_fp64_per16", C.c_int)]
 
 
 class OuterRecord(C.Structure):
@@ -99,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sscg_gram_noalloc": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _P]),
         "sscg_gram_ex": (C.c_int, [_P, _I64, _I64, C.c_int, _P, C.c_int, _P]),
         "sscg_kappa": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, _P, _P, _P, _P]),
+        "sscg_recombine": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int, _P, _P, C.c_int, _P]),
         "sscg_leja": (C.c_int, [C.c_int, _P]),
         "sscg_stencil_face_grad": (C.c_int, [_P, _P, _P, _P, _P, _P]),
         "sscg_csr_value_grad": (C.c_int, [_P, _P, _P, _P]),
@@ -315,6 +317,15 @@ def sscg_wait_failures(clear: bool = True) -> int:
 def sscg_kappa(G, ldg: int, sbar: int, kappa_cut: float, kappa, lmin, lmax, stream=None) -> None:
     _check(load_library().sscg_kappa(_f64(G), ldg, sbar, kappa_cut, _f64(kappa), _f64(lmin), _f64(lmax),
                                      _stream_ptr(stream)), "sscg_kappa")
+
+
+def sscg_recombine(Y, n: int, ldy: int, ncols: int, coef, x, rec_fp64_per16: int = -1, stream=None) -> None:
+    """x += Y x', Y[:, 0] = Y p', Y[:, 1] = Y r' on device buffers; coef (host) = x', r', p'."""
+    c = np.ascontiguousarray(coef, dtype=np.float64).ravel()
+    if c.size != 3 * ncols:
+        raise ValueError("coef must hold x', r', p' (3 * ncols values)")
+    _check(load_library().sscg_recombine(_f64(Y), n, ldy, ncols, c.ctypes.data, _f64(x), rec_fp64_per16,
+                                         _stream_ptr(stream)), "sscg_recombine")
 
 
 def sscg_leja(s: int) -> np.ndarray:

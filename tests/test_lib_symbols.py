@@ -58,6 +58,9 @@ def test_binding_defaults(lib):
     # the FP64/integer split of the stencil matrix-powers level: -1 (library default) .. 16
     assert sscg.sscg_opts_default().mpk_fp64_per16 == -1
     assert L_opts_rejects_split(sscg)
+    # the same for the recovery's split
+    assert sscg.sscg_opts_default().rec_fp64_per16 == -1
+    assert L_opts_rejects_split(sscg, "rec_fp64_per16")
 
 
 def test_invalid_arguments_rejected_without_gpu(lib):
@@ -71,11 +74,19 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     fake = ctypes.c_void_p(16)
     for mode in (-1, 4):
         assert L.sscg_gram_ex(fake, ctypes.c_int64(10), ctypes.c_int64(10), 3, fake, mode, None) == -1
+    # the recovery step: sizes and split checked before any pointer is used
+    coef = (ctypes.c_double * 9)()
+    n10 = ctypes.c_int64(10)
+    assert L.sscg_recombine(fake, ctypes.c_int64(0), n10, 3, coef, fake, -1, None) == -1
+    assert L.sscg_recombine(fake, n10, ctypes.c_int64(9), 3, coef, fake, -1, None) == -1
+    assert L.sscg_recombine(fake, n10, n10, 34, coef, fake, -1, None) == -1
+    assert L.sscg_recombine(fake, n10, n10, 3, coef, fake, 17, None) == -1
+    assert L.sscg_recombine(fake, n10, n10, 3, coef, fake, -2, None) == -1
 
 
-def L_opts_rejects_split(sscg):
+def L_opts_rejects_split(sscg, field="mpk_fp64_per16"):
     """A split outside -1..16 is rejected (before any GPU work)."""
     L = sscg.load_library()
-    o = sscg.sscg_opts_default(mpk_fp64_per16=17)
+    o = sscg.sscg_opts_default(**{field: 17})
     return L.sscg_solve(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 1e-10, 8, 2,
                         ctypes.byref(o), None) == -1
