@@ -101,6 +101,12 @@ typedef struct {
                             m (1 + 2^-5) 2^-54 of the largest term before that rounding, m <= 34 terms;
                             an FMA chain is bounded by m 2^-53 sum|terms|); 16 = FMA only, 0 = integer
                             only; default -1 = the library's tuned share */
+  int ritz_exact;        /* 0: the extremal Ritz value estimates of Algorithms 3-4 (Section 4, the method as
+                            written); 1: the extremal eigenvalues of T_m (eq. T) themselves after every inner
+                            iteration, by multisection with Sturm counts on one thread block (O(m) binary64
+                            operations per count, so the control step grows with the iteration count m; for
+                            studies, not speed).  The solve stops SSCG_NOT_CONVERGED if m reaches
+                            min(max_outer * s_max, 2^20).  Not supported by sscg_solve_batch.  Default 0 */
 } sscg_opts;
 
 /* Per-outer-loop decision record (Alg. 5): s-bar_k, s-tilde_k, s_k, c at the

@@ -47,7 +47,7 @@ import math
 import numpy as np
 
 from . import basis as bs
-from .ritz import RitzTracker
+from .ritz import ExactRitz, RitzTracker
 
 EPS64 = 2.0 ** -53
 KAPPA_CUT = 2.0 ** -44
@@ -128,6 +128,9 @@ class Options:
     # residual estimate has fallen by this factor since the last replacement
     fp32_replace_drop: float = 2.0 ** -4
     variant: str = "improved"          # improved (Alg. 5) | fixed (s_k = sigma) | old (Alg. 2)
+    # ritz: "mt" = the Meurant-Tichy estimates of Algs. 3-4 (Section 4); "exact"
+    # = the extremal eigenvalues of T_m itself (eq. T) after every iteration
+    ritz: str = "mt"
     # replay: a decision log [{"stilde", "sk", "replaced"}, ...] from another
     # implementation.  The oracle then takes those decisions instead of its own,
     # evaluates its own ones beside them and records, for each decision, the
@@ -241,7 +244,9 @@ def sstep_cg(A, b, x0, tol: float, opts: Options | None = None, record_vectors: 
     c = 1.0 / math.sqrt(eps)  # c_1 = eps^{-1/2}
     m = 0
     theta, gamma, mu = bs.basis_params(bs.MONOMIAL, sigma, None, None)
-    ritz = RitzTracker()
+    if o.ritz not in ("mt", "exact"):
+        raise ValueError(f"unknown ritz mode {o.ritz!r}")
+    ritz = RitzTracker() if o.ritz == "mt" else ExactRitz()
     alphas, betas = [], []
     hist = []
     replacements = 0

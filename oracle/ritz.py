@@ -6,6 +6,8 @@ Carson 2019, Section 4:
   eq. (lest)  lmax = ||L_i||^2, lmin = ||L_i^{-1}||^{-2}
   Alg. 3      incremental estimate of ||L_i||^2 (Meurant-Tichy)
   Alg. 4      incremental estimate of ||L_i^{-1}||^{-2} (Meurant-Tichy)
+  ExactRitz   the extremal eigenvalues of T_i themselves (the exact Ritz
+              values that Algs. 3-4 estimate), after every CG iteration
 
 Readings.  Alg. 3 prints "xi_{l+1}^2" in a_l; the matching entry of T is
 eta_l^2 + zeta_{l+1}^2, so xi is read as zeta (reading C1).  sign(0) = +1; when
@@ -134,4 +136,38 @@ class RitzTracker:
         self._zeta_prev = zeta
         self._alpha_prev = alpha
         self.n += 1
+        return self.lmin, self.lmax
+
+
+class ExactRitz:
+    """The extremal eigenvalues of T_i (eq. T) after every CG iteration, in
+    place of the estimates of Algs. 3-4: the same ``push(alpha_i, beta_{i-1})``
+    interface, T grown by one row per push (diagonal 1/alpha_i +
+    beta_{i-1}/alpha_{i-1}, off-diagonal sqrt(beta_{i-1})/alpha_{i-1}), and its
+    smallest and largest eigenvalues from LAPACK's tridiagonal bisection
+    (scipy.linalg.eigvalsh_tridiagonal)."""
+
+    def __init__(self):
+        self.n = 0
+        self.lmin = None
+        self.lmax = None
+        self.d: list[float] = []
+        self.e: list[float] = []
+        self._alpha_prev = None
+
+    def push(self, alpha: float, beta_prev: float | None):
+        from scipy.linalg import eigvalsh_tridiagonal
+        if self.n == 0:
+            self.d.append(1.0 / alpha)
+        else:
+            self.d.append(1.0 / alpha + beta_prev / self._alpha_prev)
+            self.e.append(math.sqrt(beta_prev) / self._alpha_prev)
+        self._alpha_prev = alpha
+        self.n += 1
+        if self.n == 1:
+            self.lmin = self.lmax = self.d[0]
+        else:
+            d, e = np.array(self.d), np.array(self.e)
+            self.lmin = float(eigvalsh_tridiagonal(d, e, select="i", select_range=(0, 0))[0])
+            self.lmax = float(eigvalsh_tridiagonal(d, e, select="i", select_range=(self.n - 1, self.n - 1))[0])
         return self.lmin, self.lmax

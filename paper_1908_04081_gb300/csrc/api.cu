@@ -73,6 +73,7 @@ struct sscg_ctx {
   // solve storage
   int64_t ld = 0;
   DevBuf<double> Y, G, partials, rt, b, x, r, p, q;
+  DevBuf<double> ritz_t;   // T_m of eq. (T) for ritz_exact: diagonal, then squared off-diagonal
   const double* leja = nullptr;  // the device's Leja table (not owned)
   DevBuf<int> chunk_exp;  // gram_mode 2 scratch
   DevBuf<SolveState> state;
@@ -85,6 +86,7 @@ struct sscg_ctx {
   int graph_gram_mode = 0;
   int graph_mpk_split = -1;
   int graph_rec_split = -1;
+  int graph_ritz_exact = -1;
   int graph_launches = 0;
   double last_lmin = 0.0, last_lmax = 0.0;
 };
@@ -187,7 +189,8 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
                   ds->glmax, sigma, st));
   ++count;
   if ((rc = mark(3))) return rc;
-  CK(launch_control(ds, h->G.p, kMaxCols, h->leja, h->hist.n ? h->hist.p : nullptr, st));
+  CK(launch_control(ds, h->G.p, kMaxCols, h->leja, h->hist.n ? h->hist.p : nullptr, st,
+                    h->host_state->ritz_exact != 0));
   ++count;
   if ((rc = mark(4))) return rc;
   CK(launch_recombine(ds, h->Y.p, h->ld, h->x.p, y32 ? h->r.p : nullptr, y32 ? h->p.p : nullptr, h->n, y32, st,
@@ -212,7 +215,8 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
 // WHILE node repeats one outer loop until the device sets done.
 int build_graph(sscg_ctx* h, int sigma, bool y32) {
   if (h->graph && h->graph_sigma == sigma && h->graph_y32 == y32 && h->graph_gram_mode == h->host_state->gram_mode &&
-      h->graph_mpk_split == h->host_state->mpk_fp64_per16 && h->graph_rec_split == h->host_state->rec_fp64_per16)
+      h->graph_mpk_split == h->host_state->mpk_fp64_per16 && h->graph_rec_split == h->host_state->rec_fp64_per16 &&
+      h->graph_ritz_exact == h->host_state->ritz_exact)
     return SSCG_OK;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
@@ -267,6 +271,7 @@ int build_graph(sscg_ctx* h, int sigma, bool y32) {
   h->graph_gram_mode = h->host_state->gram_mode;
   h->graph_mpk_split = h->host_state->mpk_fp64_per16;
   h->graph_rec_split = h->host_state->rec_fp64_per16;
+  h->graph_ritz_exact = h->host_state->ritz_exact;
   h->graph_launches = nl + 1;
   return SSCG_OK;
 }
@@ -297,6 +302,7 @@ void fill_state_config(SolveState& s, int sigma, double tol, int basis, const ss
   s.gram_mode = o.gram_mode;
   s.mpk_fp64_per16 = o.mpk_fp64_per16;
   s.rec_fp64_per16 = o.rec_fp64_per16;
+  s.ritz_exact = o.ritz_exact;
   s.rho_last = 1.0;
   for (int l = 0; l < kMaxS; ++l) {
     s.theta[l] = 0.0;  // monomial basis until Ritz values exist
@@ -316,6 +322,7 @@ int validate_opts(const sscg_opts& o) {
   if (!(o.eps > 0.0) || !(o.kappa_cut >= 0.0)) return SSCG_ERR_INVALID_ARG;
   if (o.mpk_fp64_per16 < -1 || o.mpk_fp64_per16 > 16) return SSCG_ERR_INVALID_ARG;
   if (o.rec_fp64_per16 < -1 || o.rec_fp64_per16 > 16) return SSCG_ERR_INVALID_ARG;
+  if (o.ritz_exact != 0 && o.ritz_exact != 1) return SSCG_ERR_INVALID_ARG;
   return SSCG_OK;
 }
 
@@ -365,6 +372,7 @@ void sscg_opts_default(sscg_opts* o) {
   o->batch_gram_rows = 0;
   o->mpk_fp64_per16 = -1;
   o->rec_fp64_per16 = -1;
+  o->ritz_exact = 0;
 }
 
 int sscg_create_csr(sscg_t* out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
@@ -556,6 +564,7 @@ void sscg_destroy(sscg_t h) {
   h->p.release();
   h->q.release();
   h->state.release();
+  h->ritz_t.release();
   h->hist.release();
   if (h->host_state) cudaFreeHost(h->host_state);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -590,6 +599,14 @@ int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg
   // configuration -> device state, as a kernel argument (no host wait); the
   // pinned mirror keeps a copy for the host-side choices below
   fill_state_config(*h->host_state, sigma, tol, (int)basis, o, hist_cap);
+  if (o.ritz_exact) {
+    const int64_t mo = o.max_outer > 0 ? o.max_outer : 100000;
+    const int cap = (int)std::min<int64_t>(mo * sigma, (int64_t)1 << 20);
+    CK(h->ritz_t.ensure(2 * (size_t)cap));
+    h->host_state->ritz_cap = cap;
+    h->host_state->ritz_d = h->ritz_t.p;
+    h->host_state->ritz_e2 = h->ritz_t.p + cap;
+  }
   CK(launch_set_state(h->state.p, *h->host_state, st));
   CK(launch_init_state(h->state.p, h->op, h->b.p, h->x.p, h->Y.p, h->ld, y32 ? h->r.p : nullptr,
                        y32 ? h->p.p : nullptr, h->partials.p, reduce_blocks(n), y32, st));
@@ -834,7 +851,7 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
   if (opts) o = *opts;
   int rc = validate_opts(o);
   if (rc) return rc;
-  if (o.y_fp32 || (o.gram_mode != 0 && o.gram_mode != 3)) return SSCG_ERR_UNSUPPORTED;
+  if (o.y_fp32 || (o.gram_mode != 0 && o.gram_mode != 3) || o.ritz_exact) return SSCG_ERR_UNSUPPORTED;
   // ---- pairs, chunks and Gram blocks (host)
   const int chunk_rows = o.batch_chunk_rows > 0 ? o.batch_chunk_rows : kBatchChunk;
   const int gram_rows = o.batch_gram_rows > 0 ? o.batch_gram_rows : kBatchGramRows;

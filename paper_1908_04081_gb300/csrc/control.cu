@@ -517,6 +517,124 @@ __device__ void basis_update_level(SolveState* st, const double* leja, int l) {
 // alpha_j and beta_{j-1}) while warps 0-1 update x', r' and form r'^T G r' and
 // thread 0 the scalars that do not depend on the Ritz values; thread 0 then
 // commits the Ritz state and takes the c update and the break test.
+// ------------------------------------------------------- exact Ritz values
+// ritz_exact = 1: the extremal eigenvalues of T_m (eq. T) after every inner
+// iteration, in place of the Meurant-Tichy estimates of Algs. 3-4.  T grows by
+// one row per CG step (diagonal 1/alpha_m + beta_{m-1}/alpha_{m-1}, squared
+// coupling beta_{m-1}/alpha_{m-1}^2, kept in global memory); each extremal
+// eigenvalue is bracketed from its previous value (interlacing: lambda_max
+// never falls and lambda_min never rises as T grows; Weyl: bordering T by the
+// new row moves them by at most the coupling) and narrowed by multisection,
+// 64 Sturm counts per round on one half of the block.
+
+// Eigenvalues of the m x m tridiagonal (d, e2) below x: the sign changes of
+// p_0 = 1, p_k = det(T_k - x I) = (d_k - x) p_{k-1} - e2_{k-1} p_{k-2} (a zero
+// takes the sign opposite to its predecessor), p_k and p_{k-1} rescaled
+// together by a power of two whenever the larger leaves [2^-400, 2^400].
+__device__ int sturm_below(const double* d, const double* e2, int m, double x) {
+  double p2 = 1.0, p1 = d[0] - x;
+  int s1 = p1 > 0.0 ? 1 : -1;
+  int cnt = s1 < 0 ? 1 : 0;
+  for (int k = 1; k < m; ++k) {
+    const double p = fma(d[k] - x, p1, -e2[k - 1] * p2);
+    const int s = p > 0.0 ? 1 : (p < 0.0 ? -1 : -s1);
+    cnt += s != s1;
+    p2 = p1;
+    p1 = p;
+    s1 = s;
+    const int E1 = (int)(((unsigned long long)__double_as_longlong(p1) >> 52) & 0x7ff);
+    const int E2 = (int)(((unsigned long long)__double_as_longlong(p2) >> 52) & 0x7ff);
+    const int Em = E1 > E2 ? E1 : E2;
+    if ((Em > 1423 && Em < 2047) || Em < 623) {
+      const double sc = __longlong_as_double((long long)(2046 - Em) << 52);   // 2^(1023 - Em), exact
+      p1 *= sc;
+      p2 *= sc;
+    }
+  }
+  return cnt;
+}
+
+// Narrow [lo, hi] around the largest (largest = true) or the smallest
+// eigenvalue by the 64 threads of one half of the block (ht = 0..63, named
+// barrier BAR): each round counts at 64 interior points and keeps the gap
+// between the last point below the eigenvalue and the first above it; every
+// thread computes the same brackets.
+template <int BAR>
+__device__ double multisect(const double* d, const double* e2, int m, double lo, double hi, bool largest, int ht,
+                            unsigned* ball) {
+  for (int round = 0; round < 16; ++round) {
+    if (!(hi - lo > 0x1p-51 * fmax(fabs(lo), fabs(hi)))) break;
+    const double w = hi - lo;
+    const double x = lo + w * ((double)(ht + 1) * (1.0 / 65.0));
+    const int c = sturm_below(d, e2, m, x);
+    const bool above = largest ? c >= m : c >= 1;
+    const unsigned b = __ballot_sync(0xffffffffu, above);
+    if ((ht & 31) == 0) ball[ht >> 5] = b;
+    group_sync(BAR, 64);
+    const unsigned long long all = (unsigned long long)ball[0] | ((unsigned long long)ball[1] << 32);
+    const int first = all ? __ffsll((long long)all) - 1 : 64;
+    const double nlo = first == 0 ? lo : lo + w * ((double)first * (1.0 / 65.0));
+    const double nhi = first == 64 ? hi : lo + w * ((double)(first + 1) * (1.0 / 65.0));
+    group_sync(BAR, 64);
+    lo = nlo;
+    hi = nhi;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// One push of (alpha, beta_prev) into T (row n = st->mt_n) and its extremal
+// eigenvalues into out[0] (lambda_min), out[1] (lambda_max); *full = 1 when T
+// has no room for the row (out keeps the previous values).  All threads.
+__device__ __forceinline__ void exact_ritz_step(SolveState* __restrict__ st, double alpha, double* out, int* full) {
+  static_assert(kControlThreads == 128, "two halves of 64 threads");
+  __shared__ unsigned ball[2][2];
+  const int t = threadIdx.x;
+  const int n = st->mt_n;
+  if (n >= st->ritz_cap) {
+    if (t == 0) {
+      *full = 1;
+      out[0] = st->lmin;
+      out[1] = st->lmax;
+    }
+    __syncthreads();
+    return;
+  }
+  if (t == 0) {
+    const double bp = st->beta_prev, ap = st->alpha_prev;
+    st->ritz_d[n] = 1.0 / alpha + (n >= 1 ? bp / ap : 0.0);
+    if (n >= 1) st->ritz_e2[n - 1] = bp / (ap * ap);
+  }
+  __syncthreads();
+  const double* d = st->ritz_d;
+  const double* e2 = st->ritz_e2;
+  const int m = n + 1;
+  if (m == 1) {
+    if (t == 0) out[0] = out[1] = d[0];
+    __syncthreads();
+    return;
+  }
+  const double dn = d[n], e = sqrt(e2[n - 1]);
+  const double pmin = st->lmin, pmax = st->lmax;
+  const int half = t >> 6, ht = t & 63;
+  double lo, hi;
+  if (half == 0) {
+    lo = pmax - 0x1p-50 * fabs(pmax);
+    hi = fmax(pmax, dn) + e;
+    hi += 0x1p-50 * fabs(hi);
+  } else {
+    lo = fmin(pmin, dn) - e;
+    lo -= 0x1p-50 * fabs(lo);
+    hi = pmin + 0x1p-50 * fabs(pmin);
+  }
+  const double v = half == 0 ? multisect<2>(d, e2, m, lo, hi, true, ht, ball[0])
+                             : multisect<3>(d, e2, m, lo, hi, false, ht, ball[1]);
+  if (ht == 0) out[half == 0 ? 1 : 0] = v;
+  __syncthreads();
+}
+
+// EXACT: the control step of ritz_exact = 1 (its own kernel, so that the
+// default step keeps its registers)
+template <bool EXACT>
 __device__ void control_body(SolveState* __restrict__ st, const double* __restrict__ G, int ldg,
                              const double* __restrict__ leja, sscg_outer_record* __restrict__ hist) {
   static_assert(kControlThreads == 128, "four warps");
@@ -527,8 +645,9 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
   __shared__ double th[kMaxS], ga[kMaxS], mu[kMaxS];
   __shared__ double red[4], red2[2];
   __shared__ double mt_up[3], mt_lo[6];
-  __shared__ int s_stilde, s_flag, s_valid, s_basis;
+  __shared__ int s_stilde, s_flag, s_valid, s_basis, s_rfull;
   __shared__ double s_alpha, s_beta;
+  __shared__ double ex_ritz[2];   // ritz_exact: lambda_min, lambda_max of T after this step
 
   const int sbar = st->sbar;
   if (warp == 0) {
@@ -546,6 +665,7 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
     if (lane == 0) {
       if (st->variant == 2) st->c = st->c_const;
       s_stilde = stl;
+      s_rfull = 0;
     }
   }
   if (t < kMaxS) {
@@ -591,6 +711,7 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
     __syncthreads();
     if (s_flag) break;
     const double alpha = s_alpha;
+    if constexpr (EXACT) exact_ritz_step(st, alpha, ex_ritz, &s_rfull);
     double beta = 0.0;
     if (warp >= 2) {
       if (lane == 0) {
@@ -635,8 +756,18 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
       st->lo_d = mt_lo[2];
       st->lo_g = mt_lo[3];
       st->lo_h = mt_lo[4];
-      st->lmax = mt_up[0];
-      st->lmin = mt_lo[5];
+      if constexpr (EXACT) {
+        st->lmax = ex_ritz[1];
+        st->lmin = ex_ritz[0];
+        if (s_rfull) {   // no room left for T: stop
+          st->status = SSCG_NOT_CONVERGED;
+          st->done = 1;
+          s_flag = 1;
+        }
+      } else {
+        st->lmax = mt_up[0];
+        st->lmin = mt_lo[5];
+      }
       st->zeta_prev = mt_up[2];
       st->alpha_prev = alpha;
       st->mt_n += 1;
@@ -713,12 +844,13 @@ __device__ void control_body(SolveState* __restrict__ st, const double* __restri
   if (s_basis && t < st->sigma) basis_update_level(st, leja, t);
 }
 
+template <bool EXACT>
 __global__ void __launch_bounds__(kControlThreads) control_kernel(SolveState* __restrict__ st,
                                                                   const double* __restrict__ G, int ldg,
                                                                   const double* __restrict__ leja,
                                                                   sscg_outer_record* __restrict__ hist) {
   if (st->done) return;
-  control_body(st, G, ldg, leja, hist);
+  control_body<EXACT>(st, G, ldg, leja, hist);
 }
 
 
@@ -739,7 +871,7 @@ __global__ void __launch_bounds__(kControlThreads) batch_control_kernel(BatchVie
   if (st->done) return;
   const double* G = v.G + (int64_t)j * kMaxCols * kMaxCols;
   sscg_outer_record* h = v.hist != nullptr ? v.hist + (int64_t)j * v.hist_cap : nullptr;
-  control_body(st, G, kMaxCols, leja, h);
+  control_body<false>(st, G, kMaxCols, leja, h);
 }
 
 // ------------------------------------------------------------------ Leja
@@ -836,8 +968,11 @@ cudaError_t launch_kappa(const double* G, int ldg, const SolveState* state, int 
 }
 
 cudaError_t launch_control(SolveState* state, const double* G, int ldg, const double* leja,
-                           sscg_outer_record* hist, cudaStream_t st) {
-  control_kernel<<<1, kControlThreads, 0, st>>>(state, G, ldg, leja, hist);
+                           sscg_outer_record* hist, cudaStream_t st, bool ritz_exact) {
+  if (ritz_exact)
+    control_kernel<true><<<1, kControlThreads, 0, st>>>(state, G, ldg, leja, hist);
+  else
+    control_kernel<false><<<1, kControlThreads, 0, st>>>(state, G, ldg, leja, hist);
   return cudaGetLastError();
 }
 

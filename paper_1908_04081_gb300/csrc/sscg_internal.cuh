@@ -105,6 +105,11 @@ struct SolveState {
   double lo_omega, lo_a, lo_d, lo_g, lo_h;
   double alpha_prev, zeta_prev, beta_prev;
   double lmin, lmax;
+  // exact Ritz values (ritz_exact = 1): T_m of eq. (T) kept as its diagonal
+  // ritz_d[0..m) and squared off-diagonal ritz_e2[0..m-1), room for ritz_cap rows
+  int ritz_exact, ritz_cap;
+  double* ritz_d;
+  double* ritz_e2;
   // recurrence coefficients of the loop in progress (eq. rho)
   double theta[kMaxS], gamma[kMaxS], inv_gamma[kMaxS], mu[kMaxS];
   // control output: coordinates of x - x_m, r, p in the basis (eq. coords)
@@ -167,8 +172,9 @@ cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* ncols_d
 cudaError_t launch_kappa(const double* G, int ldg, const SolveState* state, int sbar_fixed,
                          double kappa_cut, double* kappa, double* lmin, double* lmax, int grid,
                          cudaStream_t st);
+// ritz_exact: the step with exact Ritz values (state->ritz_exact = 1)
 cudaError_t launch_control(SolveState* state, const double* G, int ldg, const double* leja,
-                           sscg_outer_record* hist, cudaStream_t st);
+                           sscg_outer_record* hist, cudaStream_t st, bool ritz_exact = false);
 cudaError_t launch_leja(double* t, int s, cudaStream_t st);
 // the device's table of the first kMaxS Leja points (computed on `st` by the
 // first call on a device, a no-op kernel afterwards) and its device address

@@ -107,3 +107,27 @@ def cg_coefficients(A, b, iters):
         rs.append(r.copy())
         ps.append(p.copy())
     return al, be, rs, ps
+
+
+def check_exact_ritz(tracker_cls, iters=16, seed=8) -> float:
+    """Largest |extremal value - extremal eigenvalue of V_i^T A V_i| / lambda_max
+    over i = 1..iters for a tracker fed CG's (alpha_i, beta_{i-1}): the Ritz
+    values of A on the Krylov space, with V_i the normalised residuals of plain
+    CG (a dense matrix product, independent of the tracker's T; 16 iterations
+    on a 72-unknown system, before the residuals lose orthogonality).  Returns inf if
+    the values violate interlacing (lmax rising, lmin falling with i)."""
+    A = np.asarray(__import__("oracle.operators", fromlist=["as_matrix"]).as_matrix(
+        __import__("sscg_inputs.generators", fromlist=["varcoef_stencil"]).varcoef_stencil((9, 8), seed=seed)).todense())
+    b = np.random.default_rng(seed).standard_normal(A.shape[0])
+    al, be, rs, _ = cg_coefficients(A, b, iters)
+    tr = tracker_cls()
+    worst, prev = 0.0, None
+    for i in range(iters):
+        lmin, lmax = tr.push(al[i], be[i - 1] if i else None)
+        V = np.column_stack([rs[j] / np.linalg.norm(rs[j]) for j in range(i + 1)])
+        w = np.linalg.eigvalsh(V.T @ A @ V)
+        worst = max(worst, abs(lmin - w[0]) / w[-1], abs(lmax - w[-1]) / w[-1])
+        if prev is not None and (lmax < prev[1] * (1 - 1e-13) or lmin > prev[0] * (1 + 1e-13)):
+            return math.inf
+        prev = (lmin, lmax)
+    return worst

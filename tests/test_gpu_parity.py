@@ -17,6 +17,7 @@ from oracle import basis as obs
 from oracle import cg
 from oracle.operators import as_matrix
 from sscg_inputs import generators as gen
+from tests import pins
 
 pytestmark = pytest.mark.gpu
 
@@ -904,3 +905,46 @@ def test_gram_tcgen05_equals_mma_sync(pkg, n, ncols):
     d = np.sqrt(np.outer(np.diag(a), np.diag(a)))
     assert np.max(np.abs(a - b) / d) <= 1e-15
     assert pkg.sscg.sscg_wait_failures() == 0
+
+
+@pytest.mark.parametrize("case,basis,smax", [("poisson64", "chebyshev", 8), ("poisson64", "newton", 8),
+                                             ("varcoef12", "newton", 16), ("varcoef2d", "chebyshev", 10)])
+def test_exact_ritz_values_solve(pkg, case, basis, smax):
+    """NEXT row f3: ritz_exact = 1 replaces the Meurant-Tichy estimates by the
+    extremal eigenvalues of T_m (eq. T) after every inner iteration
+    (multisection with Sturm counts on the GPU, LAPACK's tridiagonal bisection
+    in the oracle's Options(ritz="exact")).  Decisions, counts and x as every
+    solve test (the Ritz values to 1e-6 on the agreeing prefix: the two runs'
+    alpha, beta agree to about 1e-8 there, and lambda_min moves with them),
+    and the final values inside A's spectrum.  The Meurant-Tichy estimates differ
+    from these by far more (7 % in lambda_max on the 64^2 Poisson problem), so
+    the test tells the two modes apart."""
+    if case == "poisson64":
+        A, b, x0, _ = gen.config_problem("poisson2d_64")
+        M = as_matrix(A)
+        s = pkg.Solver.csr(A.rowptr, A.col, A.val)
+    else:
+        st_ = gen.varcoef_stencil((12, 10, 9) if case == "varcoef12" else (40, 36), seed=17)
+        M = as_matrix(st_)
+        b = gen.random_rhs(st_.n, 18)
+        x0 = np.zeros(st_.n)
+        s = stencil_solver(pkg, st_)
+    x_o, info = cg.sstep_cg(M, b, x0, 1e-10, cg.Options(smax=smax, basis=basis, ritz="exact"))
+    xt = dev(x0)
+    st = s.solve(dev(b), xt, tol=1e-10, s_max=smax, basis=basis, hist_cap=2000, ritz_exact=1)
+    hist = pkg.sscg.history(st)
+    compare_solves(xt.cpu().numpy(), st, hist, x_o, info, 1e-10)
+    # the final values are Ritz values of A: inside its spectrum, lambda_max
+    # already close to A's largest eigenvalue (the two runs end with different
+    # T, so their final values are not compared with each other)
+    lmin, lmax = s.ritz()
+    if case == "poisson64":
+        ev = pins.poisson2d_eigs(64)
+        amin, amax = float(ev.min()), float(ev.max())
+    else:
+        ev = np.linalg.eigvalsh(M.toarray())
+        amin, amax = float(ev[0]), float(ev[-1])
+    # (finite-precision CG coefficients make T the Lanczos matrix of a slightly
+    # perturbed operator: the oracle's own run ends 2e-6 outside A's spectrum)
+    assert amin * (1 - 1e-5) <= lmin <= lmax <= amax * (1 + 1e-5), (amin, lmin, lmax, amax)
+    assert lmax >= (1 - 1e-3) * amax, (lmax, amax)

@@ -61,6 +61,12 @@ def test_binding_defaults(lib):
     # the same for the recovery's split
     assert sscg.sscg_opts_default().rec_fp64_per16 == -1
     assert L_opts_rejects_split(sscg, "rec_fp64_per16")
+    # exact Ritz values (0 = Algorithms 3-4, 1 = eigenvalues of T_m): other values rejected
+    assert sscg.sscg_opts_default().ritz_exact == 0
+    L = sscg.load_library()
+    o = sscg.sscg_opts_default(ritz_exact=2)
+    assert L.sscg_solve(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 1e-10, 8, 2,
+                        ctypes.byref(o), None) == -1
 
 
 def test_invalid_arguments_rejected_without_gpu(lib):

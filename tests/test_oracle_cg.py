@@ -193,3 +193,25 @@ def test_failure_detection_on_the_host():
     assert i2["status"] == cg.BREAKDOWN
     _, i3 = cg.sstep_cg(M, b, x0, 1e-14, cg.Options(smax=4, max_outer=3))
     assert i3["status"] == cg.NOT_CONVERGED and i3["outer"] == 3
+
+
+@pytest.mark.parametrize("basis", ["newton", "chebyshev"])
+def test_exact_ritz_mode_converges_and_tracks_t(basis):
+    # f3: Options(ritz="exact") feeds the extremal eigenvalues of T_m itself
+    # (eq. T) to the basis parameters and to c; the solve converges, and the
+    # final values are the extreme eigenvalues of T built from all of the
+    # solve's CG coefficients
+    from oracle import ritz as oritz
+    st = gen.varcoef_stencil((20, 18), seed=21)
+    A = as_matrix(st)
+    b = gen.random_rhs(st.n, 22)
+    x, info = cg.sstep_cg(A, b, np.zeros(st.n), 1e-10, cg.Options(smax=8, basis=basis, ritz="exact"))
+    assert info["status"] == cg.OK
+    assert np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b)
+    al, be = info["alphas"], info["betas"]
+    w = np.linalg.eigvalsh(oritz.lanczos_t(al, be[:len(al) - 1]))
+    assert abs(info["lmax"] - w[-1]) <= 1e-12 * w[-1] and abs(info["lmin"] - w[0]) <= 1e-12 * w[-1]
+    _, mt = cg.sstep_cg(A, b, np.zeros(st.n), 1e-10, cg.Options(smax=8, basis=basis))
+    assert abs(info["inner"] - mt["inner"]) <= 0.3 * mt["inner"]
+    with pytest.raises(ValueError):
+        cg.sstep_cg(A, b, np.zeros(st.n), 1e-10, cg.Options(smax=8, basis=basis, ritz="lanczos"))

@@ -216,3 +216,17 @@ def test_c_from_stale_psi_fails_first_ritz_pin():
 def test_kappa_cut_strict_fails_boundary_pin():
     m = mutated("cg", "w[0] <= kappa_cut * w[-1]", "w[0] < kappa_cut * w[-1]")
     assert _fails(dec.test_kappa_cut_boundary, m.kappa_estimates)
+
+
+def test_exact_ritz_offdiagonal_index_fails_pin():
+    # f3: the coupling sqrt(beta_{i-1}) / alpha_{i-1} taken with alpha_i
+    m = mutated("ritz", "self.e.append(math.sqrt(beta_prev) / self._alpha_prev)",
+                "self.e.append(math.sqrt(beta_prev) / alpha)")
+    assert pins.check_exact_ritz(m.ExactRitz) > 1e-6
+
+
+def test_exact_ritz_diagonal_term_fails_pin():
+    # f3: the diagonal 1/alpha_i + beta_{i-1}/alpha_{i-1} taken with alpha_i twice
+    m = mutated("ritz", "self.d.append(1.0 / alpha + beta_prev / self._alpha_prev)",
+                "self.d.append(1.0 / alpha + beta_prev / alpha)")
+    assert pins.check_exact_ritz(m.ExactRitz) > 1e-6

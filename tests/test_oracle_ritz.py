@@ -112,3 +112,20 @@ def test_alg3_vector_is_a_unit_rayleigh_vector():
         q, v = max(cands, key=lambda t: t[0])
         assert abs(q - est.omega) / est.omega < 1e-12
         assert est.omega >= om_prev
+
+
+def test_exact_ritz_values_are_the_ritz_values():
+    # f3: the exact tracker's values are the extreme eigenvalues of V^T A V
+    assert pins.check_exact_ritz(ritz.ExactRitz) < 1e-13
+
+
+def test_mt_estimates_lie_inside_the_exact_ritz_interval(poisson64_cg):
+    # Algs. 3-4 give Rayleigh quotients of T_i (unit vectors), so they lie in
+    # [lambda_min(T_i), lambda_max(T_i)]
+    _, al, be, _, _ = poisson64_cg
+    mt, ex = ritz.RitzTracker(), ritz.ExactRitz()
+    for i in range(60):
+        a, b_ = al[i], be[i - 1] if i else None
+        mn, mx = mt.push(a, b_)
+        en, exx = ex.push(a, b_)
+        assert en * (1 - 1e-12) <= mn and mx <= exx * (1 + 1e-12), (i, en, mn, mx, exx)
