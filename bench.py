@@ -46,6 +46,11 @@ WORKLOADS = {
     "rgg_400k": dict(desc="FP64 CSR: Laplacian of a 3D random geometric graph, N=400,000 (the 2M workload's "
                           "recipe at a smaller size), for kernel profiles", smax=16, basis="newton", tol=1e-10,
                      base="rgg_2m", scale=400_000),
+    # the forward solve of the differentiable workload's operator, with and
+    # without a stored basis (recompute_y, NEXT row f4)
+    "varcoef2d_512": dict(desc="FP64 2D 5-pt var-coef Poisson 512^2 (N=262,144), theta=exp(g) per edge, b~N(0,1), "
+                               "x0=0; stored basis against recompute-Y (no stored basis)", smax=16, basis="newton",
+                          tol=1e-10, base="adjoint2d_512", gram_mode=0),
     # a smaller grid of the same stencil family, used for kernel profiles
     "varcoef3d_96": dict(desc="FP64 3D 7-pt var-coef diffusion 96^3 (N=884,736), k=exp(N(0,1)) per face, "
                               "b~N(0,1), x0=0", smax=16, basis="newton", tol=1e-10, base="varcoef3d_160",
@@ -538,6 +543,59 @@ def run_adjoint(args, cfg, pkg, torch, dev):
     print(json.dumps(line))
 
 
+def run_recompute(args, cfg, pkg, torch, dev):
+    """Converged solves/s of a 2D stencil with the stored basis (binary64 Gram)
+    and without it (recompute_y = 1: the basis formed tile by tile twice per
+    outer loop), the same right-hand side and tolerance."""
+    op, b_np, _, _ = load_inputs(args.workload)
+    n = b_np.size
+    solver = pkg.Solver.stencil(op.kx, op.ky, None)
+    b = torch.tensor(b_np, dtype=torch.float64, device=dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    out = {}
+    for rcy in (0, 1):
+        def solve(profile=0):
+            x.zero_()
+            return solver.solve(b, x, tol=cfg["tol"], s_max=cfg["smax"], basis=cfg["basis"], gram_mode=0,
+                                recompute_y=rcy, profile=profile)
+        for _ in range(args.warmup):
+            solve()
+        evs, sts = [], []
+        with ClockSampler(0) as clk:
+            for _ in range(args.steps):
+                flush.add_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                sts.append(solve())
+                e1.record()
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+        el = sum(a.elapsed_time(b_) for a, b_ in evs) / 1e3
+        sp = solve(profile=1)
+        torch.cuda.synchronize()
+        ol = max(sp.outer_iters, 1)
+        st = sts[-1]
+        out[rcy] = {"value": args.steps / el, "ms_per_step": el / args.steps * 1e3, "outer_loops": st.outer_iters,
+                    "inner_iters": st.inner_iters, "true_relres": st.true_relres,
+                    "converged": all(s.status == 0 and s.true_relres <= cfg["tol"] for s in sts),
+                    "basis_bytes": 0 if rcy else 8 * n * (2 * cfg["smax"] + 1),
+                    "ms_per_outer_loop_profiled": {k: getattr(sp, "t_" + k + "_ms") / ol
+                                                   for k in ("mpk", "gram", "kappa", "control", "recombine",
+                                                             "other")},
+                    "clocks": clk.summary()}
+    line = {"metric": METRIC, "value": out[0]["value"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out[0]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["desc"], "s_max": cfg["smax"], "basis": cfg["basis"], "tol": cfg["tol"],
+                       "l2": f"L2 flushed between timed solves ({L2_FLUSH_BYTES >> 20} MB write)", "gram_mode": 0,
+                       "timing": "CUDA events around each solve (graph path); phases from one profiled solve"},
+            "stored_basis": out[0], "recompute_y": out[1],
+            "note": "recompute_y: the (2 s + 1) N basis is not stored; the Gram phase forms the basis and G, the "
+                    "recombine phase forms it again for x, r, p"}
+    print(json.dumps(line))
+
+
 def main():
     args = parse_args()
     cfg = dict(WORKLOADS[args.workload])
@@ -563,10 +621,10 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
-    if args.workload in ("rgg_2m", "rgg_400k", "batched_256", "adjoint2d_512"):
+    if args.workload in ("rgg_2m", "rgg_400k", "batched_256", "adjoint2d_512", "varcoef2d_512"):
         if rank == 0:
             {"rgg_2m": run_rgg, "rgg_400k": run_rgg, "batched_256": run_batched,
-             "adjoint2d_512": run_adjoint}[args.workload](
+             "adjoint2d_512": run_adjoint, "varcoef2d_512": run_recompute}[args.workload](
                 args, cfg, pkg, torch, dev)
         if world > 1:
             dist.destroy_process_group()

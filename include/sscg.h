@@ -107,6 +107,12 @@ typedef struct {
                             operations per count, so the control step grows with the iteration count m; for
                             studies, not speed).  The solve stops SSCG_NOT_CONVERGED if m reaches
                             min(max_outer * s_max, 2^20).  Not supported by sscg_solve_batch.  Default 0 */
+  int recompute_y;       /* 1: no stored basis (2D stencils, gram_mode 0, binary64 basis): each outer loop forms
+                            the basis of eq. (rho) tile by tile from p and r with a halo of s-bar cells, once
+                            to sum G = Y^T Y and once more, after the control step, to form x += Y x',
+                            r = Y r', p = Y p' (eq. coords).  The (2 s + 1) N basis values are never stored
+                            (4 N instead); the stencil work grows with the halo.  Other operators or options:
+                            SSCG_ERR_UNSUPPORTED.  Not supported by sscg_solve_batch.  Default 0 */
 } sscg_opts;
 
 /* Per-outer-loop decision record (Alg. 5): s-bar_k, s-tilde_k, s_k, c at the

@@ -21,7 +21,8 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relax
 # the control step evaluates its scalar formulas without FMA contraction so that
 # its decisions follow the written operation order
 PER_FILE = {"control.cu": ["-fmad=false"]}
-SOURCES = ["api.cu", "ops_operator.cu", "gram.cu", "control.cu", "vec.cu", "adjoint.cu", "gram_noalloc.cu"]
+SOURCES = ["api.cu", "ops_operator.cu", "gram.cu", "control.cu", "vec.cu", "adjoint.cu", "gram_noalloc.cu",
+           "recompute.cu"]
 
 
 def nvcc() -> str:

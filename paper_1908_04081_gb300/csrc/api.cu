@@ -74,6 +74,8 @@ struct sscg_ctx {
   int64_t ld = 0;
   DevBuf<double> Y, G, partials, rt, b, x, r, p, q;
   DevBuf<double> ritz_t;   // T_m of eq. (T) for ritz_exact: diagonal, then squared off-diagonal
+  DevBuf<double> pr;       // recompute_y: p, r (columns 0, 1, leading dimension n), the new p, r, the
+                           // loop's recurrence coefficients (3 kMaxS)
   const double* leja = nullptr;  // the device's Leja table (not owned)
   DevBuf<int> chunk_exp;  // gram_mode 2 scratch
   DevBuf<SolveState> state;
@@ -87,6 +89,7 @@ struct sscg_ctx {
   int graph_mpk_split = -1;
   int graph_rec_split = -1;
   int graph_ritz_exact = -1;
+  int graph_recompute = -1;
   int graph_launches = 0;
   double last_lmin = 0.0, last_lmax = 0.0;
 };
@@ -123,22 +126,33 @@ cudaMemcpyKind kind_of(int on_device) {
   return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 }
 
-int ensure_solve_buffers(sscg_ctx* h, int sigma, int hist_cap, bool y32 = false) {
+int ensure_solve_buffers(sscg_ctx* h, int sigma, int hist_cap, bool y32 = false, bool recompute = false) {
   const int64_t n = h->n;
   h->ld = round_up(n, 32);
-  const size_t ycount = (size_t)h->ld * (2 * sigma + 1);
-  if (ycount > h->Y.n) {
+  auto drop_graph = [&]() {
     if (h->graph) {
       cudaGraphExecDestroy(h->graph);
       h->graph = nullptr;
       h->graph_sigma = -1;
     }
-  }
-  CK(h->Y.ensure(ycount));
+  };
   const int gb = gram_blocks(n);
   const int rb = reduce_blocks(n);
+  size_t npart = std::max((size_t)gb * kMaxPairs, (size_t)4 * rb);
+  if (recompute) {
+    // no basis: p and r twice, and one partial Gram per tile
+    if (h->pr.n < 4 * (size_t)n + 3 * kMaxS) drop_graph();
+    CK(h->pr.ensure(4 * (size_t)n + 3 * kMaxS));
+    CK(recompute_prepare());
+    npart = std::max(npart, (size_t)recompute_partials(h->op));
+  } else {
+    const size_t ycount = (size_t)h->ld * (2 * sigma + 1);
+    if (ycount > h->Y.n) drop_graph();
+    CK(h->Y.ensure(ycount));
+  }
   CK(gram_prepare());
-  CK(h->partials.ensure(std::max((size_t)gb * kMaxPairs, (size_t)4 * rb)));
+  if (npart > h->partials.n) drop_graph();
+  CK(h->partials.ensure(npart));
   CK(h->chunk_exp.ensure((size_t)gram_exp_ints(n)));
   CK(h->rt.ensure(n));
   CK(h->b.ensure(n));
@@ -166,7 +180,44 @@ int ensure_solve_buffers(sscg_ctx* h, int sigma, int hist_cap, bool y32 = false)
 }
 
 // Enqueue one outer loop of Algorithm 5.  Returns the number of kernels.
+// One outer loop without a stored basis (recompute_y, 2D stencils): the
+// basis is formed tile by tile twice, for G and for the recovery.
+int enqueue_body_recompute(sscg_ctx* h, cudaStream_t st, std::vector<cudaEvent_t>* evs, int* nlaunch) {
+  SolveState* ds = h->state.p;
+  double* PR = h->pr.p;
+  int count = 0;
+  auto mark = [&](int i) -> int {
+    if (evs) CK(cudaEventRecord((*evs)[i], st));
+    return SSCG_OK;
+  };
+  int rc;
+  if ((rc = mark(0))) return rc;
+  if ((rc = mark(1))) return rc;
+  CK(launch_recompute_gram(h->op, PR, ds, h->partials.p, PR + 4 * h->n, h->G.p, kMaxCols, st));
+  count += 2;
+  if ((rc = mark(2))) return rc;
+  CK(launch_kappa(h->G.p, kMaxCols, ds, 0, 0.0 /* taken from the state */, ds->kappa, ds->glmin,
+                  ds->glmax, h->host_state->sigma, st));
+  ++count;
+  if ((rc = mark(3))) return rc;
+  CK(launch_control(ds, h->G.p, kMaxCols, h->leja, h->hist.n ? h->hist.p : nullptr, st,
+                    h->host_state->ritz_exact != 0));
+  ++count;
+  if ((rc = mark(4))) return rc;
+  CK(launch_recompute_recover(h->op, PR, PR + 2 * h->n, h->x.p, ds, PR + 4 * h->n, st));
+  ++count;
+  if ((rc = mark(5))) return rc;
+  CK(launch_true_residual(ds, h->op, h->b.p, h->x.p, h->rt.p, h->partials.p, reduce_blocks(h->n), st));
+  CK(launch_apply_replacement(ds, h->rt.p, PR, h->n, nullptr, nullptr, h->n, false,
+                              h->hist.n ? h->hist.p : nullptr, st));
+  count += 4;
+  if ((rc = mark(6))) return rc;
+  *nlaunch = count;
+  return SSCG_OK;
+}
+
 int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<cudaEvent_t>* evs, int* nlaunch) {
+  if (h->host_state->recompute_y) return enqueue_body_recompute(h, st, evs, nlaunch);
   SolveState* ds = h->state.p;
   LevelCoef coef{ds->theta, ds->inv_gamma, ds->mu};
   int count = 0;
@@ -216,7 +267,7 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
 int build_graph(sscg_ctx* h, int sigma, bool y32) {
   if (h->graph && h->graph_sigma == sigma && h->graph_y32 == y32 && h->graph_gram_mode == h->host_state->gram_mode &&
       h->graph_mpk_split == h->host_state->mpk_fp64_per16 && h->graph_rec_split == h->host_state->rec_fp64_per16 &&
-      h->graph_ritz_exact == h->host_state->ritz_exact)
+      h->graph_ritz_exact == h->host_state->ritz_exact && h->graph_recompute == h->host_state->recompute_y)
     return SSCG_OK;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
@@ -272,6 +323,7 @@ int build_graph(sscg_ctx* h, int sigma, bool y32) {
   h->graph_mpk_split = h->host_state->mpk_fp64_per16;
   h->graph_rec_split = h->host_state->rec_fp64_per16;
   h->graph_ritz_exact = h->host_state->ritz_exact;
+  h->graph_recompute = h->host_state->recompute_y;
   h->graph_launches = nl + 1;
   return SSCG_OK;
 }
@@ -303,6 +355,7 @@ void fill_state_config(SolveState& s, int sigma, double tol, int basis, const ss
   s.mpk_fp64_per16 = o.mpk_fp64_per16;
   s.rec_fp64_per16 = o.rec_fp64_per16;
   s.ritz_exact = o.ritz_exact;
+  s.recompute_y = o.recompute_y;
   s.rho_last = 1.0;
   for (int l = 0; l < kMaxS; ++l) {
     s.theta[l] = 0.0;  // monomial basis until Ritz values exist
@@ -323,6 +376,7 @@ int validate_opts(const sscg_opts& o) {
   if (o.mpk_fp64_per16 < -1 || o.mpk_fp64_per16 > 16) return SSCG_ERR_INVALID_ARG;
   if (o.rec_fp64_per16 < -1 || o.rec_fp64_per16 > 16) return SSCG_ERR_INVALID_ARG;
   if (o.ritz_exact != 0 && o.ritz_exact != 1) return SSCG_ERR_INVALID_ARG;
+  if (o.recompute_y != 0 && o.recompute_y != 1) return SSCG_ERR_INVALID_ARG;
   return SSCG_OK;
 }
 
@@ -373,6 +427,7 @@ void sscg_opts_default(sscg_opts* o) {
   o->mpk_fp64_per16 = -1;
   o->rec_fp64_per16 = -1;
   o->ritz_exact = 0;
+  o->recompute_y = 0;
 }
 
 int sscg_create_csr(sscg_t* out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
@@ -565,6 +620,7 @@ void sscg_destroy(sscg_t h) {
   h->q.release();
   h->state.release();
   h->ritz_t.release();
+  h->pr.release();
   h->hist.release();
   if (h->host_state) cudaFreeHost(h->host_state);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -590,7 +646,9 @@ int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg
   if (o.profile && hist_cap == 0) hist_cap = std::min(o.max_outer > 0 ? o.max_outer : 100000, 100000);
   hist_cap = std::min(hist_cap, o.max_outer > 0 ? o.max_outer : 100000);
   const bool y32 = o.y_fp32 != 0;
-  if ((rc = ensure_solve_buffers(h, sigma, hist_cap, y32))) return rc;
+  const bool recompute = o.recompute_y != 0;
+  if (recompute && (!recompute_supported(h->op) || y32 || o.gram_mode != 0)) return SSCG_ERR_UNSUPPORTED;
+  if ((rc = ensure_solve_buffers(h, sigma, hist_cap, y32, recompute))) return rc;
   if ((rc = join_in(h))) return rc;
   cudaStream_t st = h->stream;
   const int64_t n = h->n;
@@ -608,7 +666,8 @@ int sscg_solve(sscg_t h, const double* b, double* x, double tol, int s_max, sscg
     h->host_state->ritz_e2 = h->ritz_t.p + cap;
   }
   CK(launch_set_state(h->state.p, *h->host_state, st));
-  CK(launch_init_state(h->state.p, h->op, h->b.p, h->x.p, h->Y.p, h->ld, y32 ? h->r.p : nullptr,
+  CK(launch_init_state(h->state.p, h->op, h->b.p, h->x.p, recompute ? h->pr.p : h->Y.p, recompute ? h->n : h->ld,
+                       y32 ? h->r.p : nullptr,
                        y32 ? h->p.p : nullptr, h->partials.p, reduce_blocks(n), y32, st));
   int launches = 3;
   int host_syncs = 0;
@@ -851,7 +910,8 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
   if (opts) o = *opts;
   int rc = validate_opts(o);
   if (rc) return rc;
-  if (o.y_fp32 || (o.gram_mode != 0 && o.gram_mode != 3) || o.ritz_exact) return SSCG_ERR_UNSUPPORTED;
+  if (o.y_fp32 || (o.gram_mode != 0 && o.gram_mode != 3) || o.ritz_exact || o.recompute_y)
+    return SSCG_ERR_UNSUPPORTED;
   // ---- pairs, chunks and Gram blocks (host)
   const int chunk_rows = o.batch_chunk_rows > 0 ? o.batch_chunk_rows : kBatchChunk;
   const int gram_rows = o.batch_gram_rows > 0 ? o.batch_gram_rows : kBatchGramRows;

@@ -1374,6 +1374,14 @@ cudaError_t launch_batch_gram(const BatchView& v, const double* Y, int64_t LD, d
   return cudaGetLastError();
 }
 
+cudaError_t launch_gram_reduce(const double* partials, int nblocks, const SolveState* state, int ncols_fixed,
+                               double* G, int ldg, cudaStream_t st) {
+  const int warps_per_block = 256 / 32;
+  gram_reduce_kernel<<<(kMaxPairs + warps_per_block - 1) / warps_per_block, 256, 0, st>>>(partials, nblocks, state,
+                                                                                          ncols_fixed, G, ldg);
+  return cudaGetLastError();
+}
+
 int gram_blocks(int64_t n) {
   int64_t tiles = (n + kGramTileRows - 1) / kGramTileRows;
   int64_t b = kGramMaxBlocks;

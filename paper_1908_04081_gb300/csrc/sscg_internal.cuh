@@ -97,6 +97,7 @@ struct SolveState {
   int gram_mode;      // 0: binary64 Gram; 1: binary32-pair products; 2, 3: f16 digit products (mma.sync, tcgen05)
   int mpk_fp64_per16; // warps (of 16) on the binary64 FMA chain in stencil levels; -1: library default
   int rec_fp64_per16; // row groups (of 16) on the binary64 FMA chains in the recovery; -1: library default
+  int recompute_y;    // 1: no stored basis (recompute.cu)
   int fp32_replace_pending, fp32_replacements;
   double c, psi, normb, upd_relres;
   // Meurant-Tichy state (Algs. 3-4)
@@ -152,6 +153,21 @@ cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level,
 
 // gram.cu
 int gram_blocks(int64_t n);
+// G from per-block partial sums (nblocks x kMaxPairs, fixed order)
+cudaError_t launch_gram_reduce(const double* partials, int nblocks, const SolveState* state, int ncols_fixed,
+                               double* G, int ldg, cudaStream_t st);
+
+// recompute.cu: the outer loop without a stored basis (2D stencils).  PR
+// holds p (column 0) and r (column 1) with leading dimension n.
+bool recompute_supported(const Operator& A);
+int64_t recompute_partials(const Operator& A);     // doubles of partial sums
+cudaError_t recompute_prepare();                   // shared-memory limits (once per device)
+// coef (3 kMaxS doubles): the loop's recurrence coefficients, saved by the
+// Gram pass for the recovery pass
+cudaError_t launch_recompute_gram(const Operator& A, const double* PR, const SolveState* state, double* partials,
+                                  double* coef, double* G, int ldg, cudaStream_t st);   // G (2 kernels)
+cudaError_t launch_recompute_recover(const Operator& A, double* PR, double* PRnew, double* x,
+                                     const SolveState* state, double* coef, cudaStream_t st);   // 1 kernel + copy
 // per-device one-time setup of the gram_mode 1 and 2 kernels (shared memory
 // above the 48 KB default); call outside stream capture, before launch_gram
 cudaError_t gram_prepare();

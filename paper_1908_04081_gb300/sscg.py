@@ -35,7 +35,8 @@ class Opts(C.Structure):
                 ("use_graph", C.c_int), ("profile", C.c_int), ("c_const", C.c_double),
                 ("eps", C.c_double), ("kappa_cut", C.c_double), ("gram_mode", C.c_int),
                 ("batch_chunk_rows", C.c_int), ("batch_gram_rows", C.c_int), ("mpk_fp64_per16", C.c_int),
-                ("rec_fp64_per16", C.c_int), ("ritz_exact", C.c_int)]
+                ("rec_fp64_per16", C.c_int), ("ritz_exact", C.c_int),
+                ("recompute_y", C.c_int)]
 
 
 class OuterRecord(C.Structure):

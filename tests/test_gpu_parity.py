@@ -948,3 +948,61 @@ def test_exact_ritz_values_solve(pkg, case, basis, smax):
     # perturbed operator: the oracle's own run ends 2e-6 outside A's spectrum)
     assert amin * (1 - 1e-5) <= lmin <= lmax <= amax * (1 + 1e-5), (amin, lmin, lmax, amax)
     assert lmax >= (1 - 1e-3) * amax, (lmax, amax)
+
+
+@pytest.mark.parametrize("shape,basis,smax,seed", [((48, 40), "chebyshev", 10, 29), ((64, 64), "newton", 16, 23),
+                                                   ((37, 23), "newton", 8, 23), ((7, 5), "chebyshev", 4, 23)])
+def test_recompute_y_solve(pkg, shape, basis, smax, seed):
+    """NEXT row f4: recompute_y = 1 stores no basis; every outer loop forms it
+    tile by tile (16 x 16 tiles, halo of s-bar cells) once for G and once for
+    the recovery.  Against the oracle as every solve test; the grids include a
+    ragged one and one smaller than a tile (the 48 x 40 case keeps the
+    oracle's outer-loop count under rounding-size perturbations of its Gram
+    matrix; a 40 x 36 one moved between 58 and 65)."""
+    st_ = gen.varcoef_stencil(shape, seed=seed)
+    M = as_matrix(st_)
+    b = gen.random_rhs(st_.n, seed + 1)
+    x0 = np.zeros(st_.n)
+    x_o, info = cg.sstep_cg(M, b, x0, 1e-10, cg.Options(smax=smax, basis=basis))
+    s = stencil_solver(pkg, st_)
+    xt = dev(x0)
+    st = s.solve(dev(b), xt, tol=1e-10, s_max=smax, basis=basis, hist_cap=2000, recompute_y=1)
+    hist = pkg.sscg.history(st)
+    compare_solves(xt.cpu().numpy(), st, hist, x_o, info, 1e-10)
+
+
+def test_recompute_y_equals_the_stored_basis(pkg):
+    """The recomputed columns are the stored path's (its binary64 FMA forms:
+    mpk_fp64_per16 = rec_fp64_per16 = 16) bit for bit; only G's summation
+    order differs, so two outer loops (the first is one step, p_0 = r_0) give
+    the same decisions and x to rounding."""
+    st_ = gen.varcoef_stencil((50, 45), seed=25)
+    b = gen.random_rhs(st_.n, 26)
+    s = stencil_solver(pkg, st_)
+    out = {}
+    for rcy in (0, 1):
+        xt = dev(np.zeros(st_.n))
+        st = s.solve(dev(b), xt, tol=1e-10, s_max=12, basis="newton", hist_cap=10, max_outer=3, recompute_y=rcy,
+                     mpk_fp64_per16=16, rec_fp64_per16=16)
+        h = pkg.sscg.history(st)
+        out[rcy] = (xt.cpu().numpy(), [(r["sbar"], r["stilde"], r["sk"]) for r in h])
+    assert out[0][1] == out[1][1], out
+    x0_, x1_ = out[0][0], out[1][0]
+    assert np.linalg.norm(x1_ - x0_) <= 1e-11 * np.linalg.norm(x0_)
+
+
+def test_recompute_y_unsupported_cases(pkg):
+    st3 = gen.varcoef_stencil((6, 5, 4), seed=2)
+    s3 = stencil_solver(pkg, st3)
+    b = dev(gen.random_rhs(st3.n, 3))
+    with pytest.raises(Exception, match="unsupported"):
+        s3.solve(b, dev(np.zeros(st3.n)), tol=1e-8, s_max=4, basis="newton", recompute_y=1)
+    st2 = gen.varcoef_stencil((9, 8), seed=2)
+    s2 = stencil_solver(pkg, st2)
+    b2 = dev(gen.random_rhs(st2.n, 3))
+    with pytest.raises(Exception, match="unsupported"):
+        s2.solve(b2, dev(np.zeros(st2.n)), tol=1e-8, s_max=4, basis="newton", recompute_y=1, gram_mode=3)
+    A = gen.poisson2d_csr(8)
+    sc = pkg.Solver.csr(A.rowptr, A.col, A.val)
+    with pytest.raises(Exception, match="unsupported"):
+        sc.solve(dev(gen.random_rhs(A.n, 3)), dev(np.zeros(A.n)), tol=1e-8, s_max=4, basis="newton", recompute_y=1)
