@@ -247,15 +247,16 @@ __device__ __noinline__ double mpk_cell_fma(const Operator& A, const double* __r
 // work split between two units: of every 16 warps, `fp64_per16` form their
 // cells' sums as the binary64 FMA chain of stencil_mpk_grid_kernel, the others
 // with exact integer products (exact_sum.cuh: the 5 or 7 stencil products,
-// and the mu term, summed exactly and rounded once, then times 1/gamma in
-// binary64).  GB300's FP64 unit and its integer pipes run concurrently, so
+// and the mu term, streamed through one OnlineSum per chain and rounded once,
+// then times 1/gamma in binary64; few values stay live, so five blocks fit on
+// an SM).  GB300's FP64 unit and its integer pipes run concurrently, so
 // the level's time falls towards that of the slower share.  Both forms are
 // binary64-accurate (the integer one more so); a cell's result depends only
 // on which form its warp takes, which depends only on the warp's position, so
 // results are reproducible.  Inf or NaN among a cell's inputs, or a sum
 // outside the normal binary64 range, sends that cell to the FMA chain.
 template <bool DIM3>
-__global__ void __launch_bounds__(256, 4) stencil_mpk_hybrid_kernel(Operator A, double* __restrict__ Y, int64_t ld,
+__global__ void __launch_bounds__(256, 5) stencil_mpk_hybrid_kernel(Operator A, double* __restrict__ Y, int64_t ld,
                                                                       int level, const SolveState* __restrict__ st,
                                                                       int sbar_fixed, LevelCoef coef, int fp64_per16) {
   int sbar = sbar_fixed;
@@ -325,64 +326,50 @@ __global__ void __launch_bounds__(256, 4) stencil_mpk_hybrid_kernel(Operator A, 
     }
     return;
   }
-  // exact integer products: coefficients -k_f and (diag - theta), shared by both chains
-  constexpr int K = DIM3 ? 7 : 5;
-  unsigned cbad = 0;
-  Limbs c[K + 1];
-  c[0] = to_limbs(ds, cbad);
-  c[1] = to_limbs<true>(__ldg(A.kx + fx), cbad);
-  c[2] = to_limbs<true>(__ldg(A.kx + fx + 1), cbad);
-  c[3] = to_limbs<true>(__ldg(A.ky + fy), cbad);
-  c[4] = to_limbs<true>(__ldg(A.ky + fy + nx), cbad);
+  // exact integer products, term by term for both chains at once: each
+  // coefficient (-k_f, diag - theta, -mu) is split once and its products with
+  // P_l and R_l stream into one running sum per chain (OnlineSum: aligned to
+  // the largest exponent so far, rounded to nearest there, rounded once at
+  // the end), so few values stay live
+  unsigned bad2 = 0;
+  const int nch = doR ? 2 : 1;
+  OnlineSum<3> acc0, acc1;
+  auto term = [&](const Limbs& c, const Limbs& y0, const Limbs& y1) {
+    acc0.add(c, y0);
+    if (nch > 1) acc1.add(c, y1);
+  };
+  auto tile = [&](int ch, int oy, int ox) {
+    const int2 t = lv[ch][ly + oy][lx + ox];
+    return Limbs{t.x, t.y, ev[ch][ly + oy][lx + ox]};
+  };
+  term(to_limbs(ds, bad2), tile(0, 0, 0), tile(1, 0, 0));
+  term(to_limbs<true>(__ldg(A.kx + fx), bad2), tile(0, 0, -1), tile(1, 0, -1));
+  term(to_limbs<true>(__ldg(A.kx + fx + 1), bad2), tile(0, 0, 1), tile(1, 0, 1));
+  term(to_limbs<true>(__ldg(A.ky + fy), bad2), tile(0, -1, 0), tile(1, -1, 0));
+  term(to_limbs<true>(__ldg(A.ky + fy + nx), bad2), tile(0, 1, 0), tile(1, 1, 0));
+  const double* P = Y + (int64_t)(2 * level) * ld;
+  const double* R = P + ld;
   if (DIM3) {
-    c[5] = to_limbs<true>(__ldg(A.kz + i), cbad);
-    c[6] = to_limbs<true>(__ldg(A.kz + i + plane), cbad);
+    const Limbs zero{0, 0, 1};
+    const Limbs cd = to_limbs<true>(__ldg(A.kz + i), bad2);
+    term(cd, z > 0 ? to_limbs(__ldg(P + i - plane), bad2) : zero,
+         z > 0 && nch > 1 ? to_limbs(__ldg(R + i - plane), bad2) : zero);
+    const Limbs cu = to_limbs<true>(__ldg(A.kz + i + plane), bad2);
+    term(cu, z < nz - 1 ? to_limbs(__ldg(P + i + plane), bad2) : zero,
+         z < nz - 1 && nch > 1 ? to_limbs(__ldg(R + i + plane), bad2) : zero);
   }
-  c[K] = to_limbs<true>(mu, cbad);
-  const int nterm = mu != 0.0 ? K + 1 : K;
+  if (mu != 0.0) {
+    const double* Pm = Y + (int64_t)(2 * level - 2) * ld;
+    term(to_limbs<true>(mu, bad2), to_limbs(__ldg(Pm + i), bad2),
+         nch > 1 ? to_limbs(__ldg(Pm + ld + i), bad2) : Limbs{0, 0, 1});
+  }
 #pragma unroll 1
-  for (int ch = 0; ch < (doR ? 2 : 1); ++ch) {
-    const double* Vl = Y + (int64_t)(2 * level + ch) * ld;
-    unsigned ybad = cbad;
-    Limbs yz[3];   // the global operands: z - 1, z + 1 and the mu term's value
-    yz[0] = to_limbs(DIM3 && z > 0 ? __ldg(Vl + i - plane) : 0.0, ybad);
-    yz[1] = to_limbs(DIM3 && z < nz - 1 ? __ldg(Vl + i + plane) : 0.0, ybad);
-    yz[2] = to_limbs(mu != 0.0 ? __ldg(Y + (int64_t)(2 * level - 2 + ch) * ld + i) : 0.0, ybad);
-    // exponent sums first, then the aligned products
-    const int e0 = ev[ch][ly][lx], e1 = ev[ch][ly][lx - 1], e2 = ev[ch][ly][lx + 1];
-    const int e3 = ev[ch][ly - 1][lx], e4 = ev[ch][ly + 1][lx];
-    int E[K + 1];
-    E[0] = c[0].e + e0;
-    E[1] = c[1].e + e1;
-    E[2] = c[2].e + e2;
-    E[3] = c[3].e + e3;
-    E[4] = c[4].e + e4;
-    if (DIM3) {
-      E[5] = c[5].e + yz[0].e;
-      E[6] = c[6].e + yz[1].e;
-    }
-    E[K] = c[K].e + yz[2].e;
-    int Em = 0;
-#pragma unroll
-    for (int j = 0; j < K + 1; ++j)
-      if (j < nterm) Em = E[j] > Em ? E[j] : Em;
-    long long S = 0;
-    auto add = [&](int j, const Limbs& y) { S += shift_down(limb_product(c[j], y), Em - E[j] + 3); };
-    int2 t;
-    t = lv[ch][ly][lx];     add(0, Limbs{t.x, t.y, e0});
-    t = lv[ch][ly][lx - 1]; add(1, Limbs{t.x, t.y, e1});
-    t = lv[ch][ly][lx + 1]; add(2, Limbs{t.x, t.y, e2});
-    t = lv[ch][ly - 1][lx]; add(3, Limbs{t.x, t.y, e3});
-    t = lv[ch][ly + 1][lx]; add(4, Limbs{t.x, t.y, e4});
-    if (DIM3) {
-      add(5, yz[0]);
-      add(6, yz[1]);
-    }
-    if (mu != 0.0) add(K, yz[2]);
+  for (int ch = 0; ch < nch; ++ch) {
     bool ok = true;
-    double w = to_binary64(S, Em, ok);
-    if (!ok || ybad)
-      w = mpk_cell_fma<DIM3>(A, Vl, Y + (int64_t)(2 * level - 2 + ch) * ld, i, x, yy, z, ds, mu);
+    double w = (ch == 0 ? acc0 : acc1).result(ok);
+    if (!ok || bad2)
+      w = mpk_cell_fma<DIM3>(A, Y + (int64_t)(2 * level + ch) * ld, Y + (int64_t)(2 * level - 2 + ch) * ld, i, x,
+                             yy, z, ds, mu);
     Y[(int64_t)(2 * level + 2 + ch) * ld + i] = w * ig;
   }
 }

@@ -146,7 +146,7 @@ cudaError_t launch_residual(const Operator& A, const double* b, const double* x,
 // binary64 FMA chain, the others exact integer products (16: FMA chain only;
 // negative: kMpkFp64Per16).
 struct LevelCoef { const double* theta; const double* inv_gamma; const double* mu; };
-constexpr int kMpkFp64Per16 = 6;
+constexpr int kMpkFp64Per16 = 8;
 cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level,
                              const SolveState* state, int sbar_fixed, LevelCoef coef, bool y32,
                              cudaStream_t st, int fp64_per16 = -1);
