@@ -92,7 +92,7 @@ def dg_tiles(ncols):
 
 DG_MMA_FLOP_PER_ROW_TILE = 78 * 16 * 8 * 16 * 2 // 16   # 78 f16 m16n8k16 MMAs per 16 rows and tile
 # gram_mode 3: four tcgen05.mma of M = N = 128, K = 16 per 16 rows (columns 0..31)
-TC_MMA_FLOP_PER_ROW = 4 * 128 * 128 * 16 * 2 // 16
+TC_MMA_FLOP_PER_ROW = (2 * 128 * 128 + 2 * 128 * 64) * 16 * 2 // 16   # per 16 rows: two N = 128, two N = 64 MMAs
 FF_OPS_PER_PRODUCT = 13                       # binary32 instructions per pair and row (gram_mode 1)
 # binary64 lane operations per cell of one 3D matrix-powers level (both chains,
 # stencil_mpk_grid_kernel): 17 (Newton and monomial, mu = 0), 19 (Chebyshev)
@@ -751,11 +751,11 @@ def main():
                     "traffic": gram_traffic, "traffic_source": traffic_src, "launches": n_gram,
                     "peak_note": fp64_note}
     elif args.gram_mode == 3:
-        # executed tcgen05 f16 MMA flops (4 MMAs of 128 x 128 x 16 per 16 rows)
+        # executed tcgen05 f16 MMA flops (per 16 rows: 128 x 128 x 16 twice, 128 x 64 x 16 twice)
         tc_flop = sum(n * TC_MMA_FLOP_PER_ROW for h in hist_p)
         tc_tf = tc_flop / t_gram / 1e12 if t_gram > 0 else None
         roofline = {"bound": "tensor", "kernel": "gram_chunk_exp+gram_partial_tc+gram_reduce (G = Y^T Y, exact "
-                                                  "5-bit digit products by tcgen05.mma into tensor memory)",
+                                                  "6-bit digit products by tcgen05.mma into tensor memory)",
                     "achieved": tc_tf, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": (tc_tf / BF16_PEAK_TFLOPS) if tc_tf else None,
                     "traffic": gram_traffic, "traffic_source": traffic_src, "launches": n_gram,

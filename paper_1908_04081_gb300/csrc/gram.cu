@@ -782,35 +782,40 @@ gram_partial_dg_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
 // ------------------------------------------------------------------------
 // The digit Gram on the 5th-generation tensor cores (gram_mode = 3).
 //
-// Columns 0..31: the arithmetic of gram_mode 2 (the same 60-bit integers per
-// value and chunk, the same 12 signed 5-bit digits as f16 subnormals, exact
-// binary32 sums of digit products, combined in two 64-bit integers per entry
-// and added in binary64; here once per 4096-row scale chunk, since each
-// accumulator sums a single plane pair), run as tcgen05.mma (kind::f16,
-// M = N = 128, K = 16, f32 accumulators in tensor memory) issued by one
-// thread.  Since H_u = sum_{s+t=u} D_s^T D_t (D_s the digit plane s of the
-// columns) is symmetric, it is formed from the pairs s <= t only:
+// Columns 0..31: the 60-bit integers F of gram_mode 2 (the same per-value,
+// per-chunk scales), here written as ten signed 6-bit digits (|d| <= 63) as
+// f16 subnormals, with exact binary32 sums of digit products combined in two
+// 64-bit integers per entry and added in binary64 once per 4096-row scale
+// chunk (each accumulator sums a single plane pair: below 4096 * 63^2 < 2^24,
+// exact), run as tcgen05.mma (kind::f16, M = 128, N = 128 or 64, K = 16, f32
+// accumulators in tensor memory) issued by one thread.  Since
+// H_u = sum_{s+t=u} D_s^T D_t (D_s the digit plane s of the columns) is
+// symmetric, it is formed from the pairs s <= t only:
 //   H_u = sum_{s<t, s+t=u} (X_st + X_st^T) + [u even] X_{u/2,u/2},
 //   X_st = D_s^T D_t,
-// 42 plane pairs.  Each MMA takes four consecutive planes on each side (A:
-// planes a..a+3 x 32 columns = 128 rows, B: planes b..b+3 = 128 columns), so
-// block (k, l) of its 128 x 128 accumulator is X_{a+k, b+l}; the four
-// accumulators (a, b) = (0, 0), (0, 4), (0, 8), (4, 4) hold every pair with
-// s <= t and s + t <= 11, and fill tensor memory (4 x 128 columns).  Four
-// MMAs per 16 rows; 42 of the 64 plane-pair blocks computed are used.
+// 30 plane pairs (s + t <= 9; the pairs beyond weigh at most about 2^-57 of
+// the product of the two columns' largest values per row).  Each MMA takes
+// four consecutive planes on the A side (planes a..a+3 x 32 columns = 128
+// rows) and four or two on the B side, so block (k, l) of its accumulator is
+// X_{a+k, b+l}; the four accumulators (a, b) = (0, 0), (0, 4) (N = 128) and
+// (0, 8), (4, 4) (N = 64, planes b, b+1) hold every pair with s <= t and
+// s + t <= 9 in 384 tensor-memory columns.  Four MMAs per 16 rows; 30 of the
+// 48 plane-pair blocks computed are used.  (Six-bit digits need ten planes
+// where five-bit ones need twelve: a sixth less conversion work, a quarter
+// less MMA work.)
 // Column 32 (ncols = 33): its 33 entries are binary64 FMA sums (the FP64
 // unit is otherwise idle here), formed by three warps from Y in global memory.
 //
 // Shared memory holds each 64-row stage in the no-swizzle canonical K-major
 // layout: the 16-byte unit of 8 rows of (plane, column) at
-// [8-row block][plane][column] (LBO = one 8-row block, 6,144 bytes; SBO = 128
+// [8-row block][plane][column] (LBO = one 8-row block, 5,120 bytes; SBO = 128
 // bytes between groups of 8 operand rows).
 //
 // Warp roles (768 threads): warp 0 allocates tensor memory and one of its
 // threads issues the MMAs; warps 1..3 the column-32 dot products; warps 4..7
 // the epilogue of each scale chunk (tcgen05.ld reaches lane quadrant w % 4
-// from warp w); warps 8..23 stage and convert the rows (the digits of
-// gram_mode 2, four rows per thread).  Hand-offs are mbarriers: full[b] (conversion -> MMA, per
+// from warp w); warps 8..23 stage and convert the rows (four rows per
+// thread).  Hand-offs are mbarriers: full[b] (conversion -> MMA, per
 // stage buffer), empty[b] (tcgen05.commit -> conversion), tfull
 // (tcgen05.commit -> epilogue), tempty (epilogue -> MMA, before a block's
 // first MMA overwrites the accumulators).  Every wait gives up after about a
@@ -821,8 +826,9 @@ constexpr int kTcKB = kTcStageRows / 8;
 constexpr int kTcCols = 32;
 constexpr uint32_t kTcCore = 128;                                      // 8 rows x 16 bytes
 constexpr uint32_t kTcPlaneBytes = (kTcCols / 8) * kTcCore;            // 512: one plane of 32 columns
-constexpr uint32_t kTcKBBytes = kDgPlanes * kTcPlaneBytes;             // 6,144: LBO
-constexpr uint32_t kTcStage = kTcKB * kTcKBBytes;                      // 49,152
+constexpr int kTcPlanes = 10;                                          // six-bit digit planes
+constexpr uint32_t kTcKBBytes = kTcPlanes * kTcPlaneBytes;             // 5,120: LBO
+constexpr uint32_t kTcStage = kTcKB * kTcKBBytes;                      // 40,960
 constexpr int kTcConvWarps = 16;                                       // conversion warps (4 rows per thread)
 constexpr int kTcThreads = 32 * (8 + kTcConvWarps);                    // 768
 constexpr int kTcC32W0 = 1, kTcEpi0 = 4, kTcConv0 = 8;                 // first column-32 / epilogue / conversion warp
@@ -830,9 +836,11 @@ constexpr uint32_t kTcTmemCols = 512;
 constexpr int kTcAcc = 4;                                              // accumulators (a, b)
 __device__ __constant__ int kTcAccA[kTcAcc] = {0, 0, 0, 4};
 __device__ __constant__ int kTcAccB[kTcAcc] = {0, 4, 8, 4};
-static_assert(kTcStageRows == kDgStageRows, "the conversion of gram_mode 2 is reused");
+__device__ __constant__ int kTcAccL[kTcAcc] = {4, 4, 2, 2};            // B planes (N / 32)
+__device__ __constant__ int kTcAccCol[kTcAcc] = {0, 128, 256, 320};    // tensor-memory column of each
+static_assert(kTcStageRows == kDgStageRows, "the raw stages of gram_mode 2 are reused");
 template <typename T>
-constexpr size_t tc_smem_bytes() { return 2 * (size_t)kTcStage + 2 * dg_raw_bytes<T>(); }   // 133,152 for binary64
+constexpr size_t tc_smem_bytes() { return 2 * (size_t)kTcStage + 2 * dg_raw_bytes<T>(); }   // 116,768 for binary64
 
 __device__ int g_gram_tc_error;   // set when a wait of gram_partial_tc_kernel gave up
 
@@ -894,7 +902,20 @@ __device__ __forceinline__ void tc_ld8(uint32_t (&r)[8], uint32_t taddr) {
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// the 12 digit planes of 4 consecutive rows of one column: words 2h, 2h + 1
+// six-bit digit t (0 = most significant) of the 60-bit F = (h << 32) | l:
+// bits 54 - 6t .. 59 - 6t
+template <int t>
+__device__ __forceinline__ unsigned tc_digit(unsigned h, unsigned l) {
+  constexpr int lo = 54 - 6 * t;
+  if constexpr (lo >= 32)
+    return (h >> (lo - 32)) & 63u;
+  else if constexpr (lo + 6 <= 32)
+    return (l >> lo) & 63u;
+  else
+    return __funnelshift_r(l, h, lo) & 63u;
+}
+
+// the 10 digit planes of 4 consecutive rows of one column: words 2h, 2h + 1
 // of the 16-byte units unit + t * plane_stride
 __device__ __forceinline__ void tc_store4(const double (&v)[4], int ce, unsigned char* unit, uint32_t plane_stride,
                                           int h2) {
@@ -912,10 +933,10 @@ __device__ __forceinline__ void tc_store4(const double (&v)[4], int ce, unsigned
   unsigned char* u = unit + 8 * h2;
 #define TC_PLANE4(t)                                                                                      \
   *reinterpret_cast<uint2*>(u + (t) * plane_stride) =                                                     \
-      make_uint2(dg_digit<t>(h[0], l[0]) | (dg_digit<t>(h[1], l[1]) << 16) | sg[0],                       \
-                 dg_digit<t>(h[2], l[2]) | (dg_digit<t>(h[3], l[3]) << 16) | sg[1]);
+      make_uint2(tc_digit<t>(h[0], l[0]) | (tc_digit<t>(h[1], l[1]) << 16) | sg[0],                       \
+                 tc_digit<t>(h[2], l[2]) | (tc_digit<t>(h[3], l[3]) << 16) | sg[1]);
   TC_PLANE4(0) TC_PLANE4(1) TC_PLANE4(2) TC_PLANE4(3) TC_PLANE4(4) TC_PLANE4(5)
-  TC_PLANE4(6) TC_PLANE4(7) TC_PLANE4(8) TC_PLANE4(9) TC_PLANE4(10) TC_PLANE4(11)
+  TC_PLANE4(6) TC_PLANE4(7) TC_PLANE4(8) TC_PLANE4(9)
 #undef TC_PLANE4
 }
 
@@ -976,11 +997,11 @@ __device__ __forceinline__ void tc_convert(const T* raw, unsigned char* stage, c
   }
 }
 
-// Each accumulator sums one plane pair: below 961 R for R rows, exact in
-// binary32 up to R = 17,458, so the block sums are read out once per scale
+// Each accumulator sums one plane pair: below 3969 R for R rows, exact in
+// binary32 up to R = 4227, so the block sums are read out once per scale
 // chunk (4096 rows), where the scales change.
 constexpr int kTcFlushShift = kDgChunkShift;
-static_assert((1 << kTcFlushShift) * 961 < (1 << 24), "exact binary32 sums of one plane pair");
+static_assert((1 << kTcFlushShift) * 63 * 63 < (1 << 24), "exact binary32 sums of one plane pair");
 
 // whether stage rows r0..r0+63 end a flush block within [.., r_end)
 __device__ __forceinline__ bool tc_block_end(int64_t r0, int64_t r_end) {
@@ -1109,7 +1130,7 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
     // ---- MMA issue (one thread)
     if (lane == 0) {
       const uint32_t sbase = smem_addr(tc_smem);
-      constexpr uint32_t idesc = tc_idesc(128, 128);
+      constexpr uint32_t idesc128 = tc_idesc(128, 128), idesc64 = tc_idesc(128, 64);
       int64_t blk = -1;
       bool new_block = true;
       for (int64_t k = 0; k < nst; ++k) {
@@ -1130,7 +1151,7 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
           for (int q = 0; q < kTcAcc; ++q) {
             const uint64_t da = tc_desc(km + (uint32_t)kTcAccA[q] * kTcPlaneBytes, kTcKBBytes, kTcCore);
             const uint64_t db = tc_desc(km + (uint32_t)kTcAccB[q] * kTcPlaneBytes, kTcKBBytes, kTcCore);
-            tc_mma(tmem + 128u * (uint32_t)q, da, db, idesc, acc);
+            tc_mma(tmem + (uint32_t)kTcAccCol[q], da, db, kTcAccL[q] == 4 ? idesc128 : idesc64, acc);
           }
         }
         tc_commit(b_empty + 8 * b);                     // stage buffer b may be refilled
@@ -1177,8 +1198,8 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
       const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
       // Half a row of columns j at a time, summed over every plane-pair block
       // of this quadrant: 2^48 X is an integer below 2^24; u = s + t < 6 goes
-      // to the high Horner sum (weight 32^(5 - u)), u >= 6 to the low one
-      // (32^(11 - u)).  X_st (s < t) enters entry (min(i,j), max(i,j)) from
+      // to the high Horner sum (weight 64^(4 - u)), u >= 5 to the low one
+      // (64^(9 - u)).  X_st (s < t) enters entry (min(i,j), max(i,j)) from
       // both (i, j) and (j, i) (twice on the diagonal); X_ss only once, from
       // i <= j.
 #pragma unroll 1
@@ -1190,21 +1211,21 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
         for (int acc = 0; acc < kTcAcc; ++acc) {
           const int s = kTcAccA[acc] + q;
 #pragma unroll 1
-          for (int l = 0; l < 4; ++l) {
+          for (int l = 0; l < kTcAccL[acc]; ++l) {
             const int tt = kTcAccB[acc] + l;
-            if (s > tt || s + tt > 11) continue;       // uniform: pairs s <= t, s + t <= 11
+            if (s > tt || s + tt > 9) continue;        // uniform: pairs s <= t, s + t <= 9
             uint32_t x[8];
-            tc_ld8(x, tq + (uint32_t)(128 * acc + 32 * l + 8 * half));
+            tc_ld8(x, tq + (uint32_t)(kTcAccCol[acc] + 32 * l + 8 * half));
             tc_wait_ld();
             const int u = s + tt;
-            const long long w = u < 6 ? (1ll << (5 * (5 - u))) : (1ll << (5 * (11 - u)));
+            const long long w = u < 5 ? (1ll << (6 * (4 - u))) : (1ll << (6 * (9 - u)));
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
               const int j = 8 * half + jj;
               if (s < tt || i <= j) {
                 const long long v =
                     (long long)__float2int_rz(__uint_as_float(x[jj]) * 0x1p48f) * (s < tt && i == j ? 2 * w : w);
-                if (u < 6) hi[jj] += v;
+                if (u < 5) hi[jj] += v;
                 else lo[jj] += v;
               }
             }
@@ -1238,9 +1259,11 @@ gram_partial_tc_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const Sol
         if (ci_ == 2047 || cj_ == 2047) {
           gacc[p] = __longlong_as_double(0x7ff8000000000000ll);
         } else {
-          const int kk = ci_ + cj_ - 2006;
-          if (shi != 0) gacc[p] += dg_scale((double)shi, kk - 5 * 5 - 48);
-          if (slo != 0) gacc[p] += dg_scale((double)slo, kk - 5 * 11 - 48);
+          // y_i y_j = F_i F_j 2^(ce_i + ce_j - 2164), F_i F_j = sum_u H_u 2^(108 - 6u):
+          // the high sum at 2^84, the low one at 2^54
+          const int kk = ci_ + cj_ - 2164;
+          if (shi != 0) gacc[p] += dg_scale((double)shi, kk + 84);
+          if (slo != 0) gacc[p] += dg_scale((double)slo, kk + 54);
         }
       }
       bar_sync(1, 128);                                 // sums cleared before the next block
