@@ -91,17 +91,18 @@ def dg_tiles(ncols):
 
 
 DG_MMA_FLOP_PER_ROW_TILE = 78 * 16 * 8 * 16 * 2 // 16   # 78 f16 m16n8k16 MMAs per 16 rows and tile
-# gram_mode 3: four tcgen05.mma of M = N = 128, K = 16 per 16 rows (columns 0..31)
+# gram_mode 3: tcgen05.mma of M = 128, K = 16 per 16 rows (columns 0..31)
 TC_MMA_FLOP_PER_ROW = (2 * 128 * 128 + 2 * 128 * 64) * 16 * 2 // 16   # per 16 rows: two N = 128, two N = 64 MMAs
 FF_OPS_PER_PRODUCT = 13                       # binary32 instructions per pair and row (gram_mode 1)
 # binary64 lane operations per cell of one 3D matrix-powers level (both chains,
 # stencil_mpk_grid_kernel): 17 (Newton and monomial, mu = 0), 19 (Chebyshev)
 MPK_FP64_OPS_PER_CELL = {"newton": 17, "monomial": 17, "chebyshev": 19}
 FP64_PEAK_TOPS = 152 * 4 * 32 / 64 * 2.070e9 / 1e12   # binary64 lane ops/s: 4 sub-partitions x 32 lanes / 64 cycles
-# DRAM bytes per cell and level of stencil_mpk_grid_kernel (read + write),
+# DRAM bytes per cell and level of stencil_mpk_hybrid_kernel (read + write),
 # from a one-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
-# of two levels of the 160^3 case: 242.9 MB per launch / 4,096,000 cells
-MPK_DRAM_BYTES_PER_CELL = 59.30
+# of four steady-state levels of the 160^3 case: 197.25 MB read and
+# 44.8-47.7 MB written per launch, 242.1 MB / 4,096,000 cells
+MPK_DRAM_BYTES_PER_CELL = 59.11
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -736,7 +737,10 @@ def main():
                     "achieved": mpk_tops, "peak": peak_ops, "unit": "T binary64 lane-ops/s",
                     "frac": mpk_tops / peak_ops,
                     "traffic": (MPK_DRAM_BYTES_PER_CELL * n) if MPK_DRAM_BYTES_PER_CELL else None,
-                    "traffic_source": traffic_src, "launches": levels,
+                    "traffic_source": "an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of this "
+                                      "kernel at 160^3 (four steady-state levels), bytes per cell times the "
+                                      "cells of a launch; not measured in this run",
+                    "launches": levels,
                     "algorithmic": f"{ops} binary64 operations per cell and level (formed by the FP64 unit or, in "
                                    f"the integer warps, exactly by the integer pipes)",
                     "peak_note": fp64_note + " (as lane operations: TFLOP/s / 2); the integer warps add work "
