@@ -66,6 +66,11 @@ struct sscg_ctx {
   cudaStream_t user_stream = nullptr;
   cudaStream_t stream = nullptr;  // private stream (stream capture needs a non-legacy stream)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // digit Grams: the column scales of each level's new columns are found on
+  // a side stream while the next level runs (ev_lvl[l]: level l - 1 done,
+  // ev_lvl[kMaxS + 1]: the side stream's last pass done)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_lvl[kMaxS + 2] = {};
   // operator storage
   DevBuf<int64_t> rowptr, s_off;
   DevBuf<int32_t> col, s_row, s_len, s_col;
@@ -101,6 +106,8 @@ int init_common(sscg_ctx* h, void* cuda_stream) {
   CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  for (auto& e : h->ev_lvl) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   CK(cudaMallocHost(&h->host_state, sizeof(SolveState)));
   CK(leja_table(&h->leja, h->stream));
   CK(h->state.ensure(1));
@@ -227,14 +234,42 @@ int enqueue_body(sscg_ctx* h, int sigma, bool y32, cudaStream_t st, std::vector<
   };
   int rc;
   if ((rc = mark(0))) return rc;
-  for (int l = 0; l < sigma; ++l) {
-    CK(launch_mpk_level(h->op, h->Y.p, h->ld, l, ds, 0, coef, y32, st, h->host_state->mpk_fp64_per16));
-    ++count;
+  // digit Grams: each pair of new columns gets its scales on the side stream
+  // while the next level runs on st (the levels are bound by the FP64 unit
+  // and the integer pipes, the scale pass by memory); only the last pair's
+  // pass is on the path to the Gram
+  const bool digit = h->host_state->gram_mode >= 2;
+  bool forked = false;
+  auto join = [&]() -> cudaError_t {   // the side stream back into st (also before an error return)
+    if (!forked) return cudaSuccess;
+    forked = false;
+    cudaError_t e = cudaEventRecord(h->ev_lvl[kMaxS + 1], h->side);
+    cudaError_t e2 = cudaStreamWaitEvent(st, h->ev_lvl[kMaxS + 1], 0);
+    return e != cudaSuccess ? e : e2;
+  };
+  auto scales = [&](int l) -> cudaError_t {   // after level l - 1 (l = 0: columns 0, 1 from the last loop)
+    cudaError_t e = cudaEventRecord(h->ev_lvl[l], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_lvl[l], 0);
+    if (e == cudaSuccess) {
+      forked = true;
+      e = launch_chunk_exp(h->Y.p, h->n, h->ld, ds, 2 * l, 2, y32, h->chunk_exp.p, h->side);
+    }
+    if (e == cudaSuccess) ++count;
+    return e;
+  };
+  cudaError_t ef = digit ? scales(0) : cudaSuccess;
+  for (int l = 0; l < sigma && ef == cudaSuccess; ++l) {
+    ef = launch_mpk_level(h->op, h->Y.p, h->ld, l, ds, 0, coef, y32, st, h->host_state->mpk_fp64_per16);
+    if (ef == cudaSuccess) ++count;
+    if (ef == cudaSuccess && digit) ef = scales(l + 1);
   }
+  const cudaError_t ej = join();
+  CK(ef);
+  CK(ej);
   if ((rc = mark(1))) return rc;
   CK(launch_gram(h->Y.p, h->n, h->ld, nullptr, 0, ds, h->partials.p, gram_blocks(h->n), h->G.p, kMaxCols, y32,
-                 st, h->host_state->gram_mode, h->chunk_exp.p));
-  count += h->host_state->gram_mode >= 2 ? 3 : 2;
+                 st, h->host_state->gram_mode, h->chunk_exp.p, digit));
+  count += 2;
   if ((rc = mark(2))) return rc;
   CK(launch_kappa(h->G.p, kMaxCols, ds, 0, 0.0 /* taken from the state */, ds->kappa, ds->glmin,
                   ds->glmax, sigma, st));
@@ -625,6 +660,9 @@ void sscg_destroy(sscg_t h) {
   if (h->host_state) cudaFreeHost(h->host_state);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
+  for (auto& e : h->ev_lvl)
+    if (e) cudaEventDestroy(e);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }

@@ -408,13 +408,13 @@ __device__ __forceinline__ void mma_f16(float (&c)[4], const unsigned (&a)[4], c
 template <typename T>
 __global__ void __launch_bounds__(256)
 gram_chunk_exp_kernel(const T* __restrict__ Y, int64_t n, int64_t ld, const SolveState* __restrict__ st,
-                      int ncols_fixed, int* __restrict__ cexp) {
+                      int ncols_fixed, int* __restrict__ cexp, int c0 = 0) {
   int ncols = ncols_fixed;
   if (ncols <= 0) {
     if (st->done) return;
     ncols = 2 * st->sbar + 1;
   }
-  const int c = blockIdx.y;
+  const int c = c0 + (int)blockIdx.y;   // columns c0 .. c0 + gridDim.y - 1
   if (c >= ncols) return;
   const int64_t r0 = (int64_t)blockIdx.x * kDgChunkRows;
   const T* col = Y + (int64_t)c * ld;
@@ -1397,6 +1397,22 @@ cudaError_t launch_batch_gram(const BatchView& v, const double* Y, int64_t LD, d
   return cudaGetLastError();
 }
 
+cudaError_t launch_chunk_exp(const void* Y, int64_t n, int64_t ld, const SolveState* state, int c0, int count,
+                             bool y32, int* chunk_exp, cudaStream_t st) {
+  const int64_t nchunks = (n + kDgChunkRows - 1) / kDgChunkRows;
+  if (c0 + count > kMaxCols) count = kMaxCols - c0;   // columns past the basis: nothing to do
+  if (count < 1) return cudaSuccess;
+  if (nchunks > 0x7fffffff || c0 < 0) return cudaErrorInvalidValue;
+  const dim3 egrid((unsigned)nchunks, (unsigned)count);
+  if (y32)
+    gram_chunk_exp_kernel<float><<<egrid, 256, 0, st>>>(static_cast<const float*>(Y), n, ld, state, 0, chunk_exp,
+                                                        c0);
+  else
+    gram_chunk_exp_kernel<double><<<egrid, 256, 0, st>>>(static_cast<const double*>(Y), n, ld, state, 0, chunk_exp,
+                                                         c0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gram_reduce(const double* partials, int nblocks, const SolveState* state, int ncols_fixed,
                                double* G, int ldg, cudaStream_t st) {
   const int warps_per_block = 256 / 32;
@@ -1455,7 +1471,7 @@ int64_t gram_exp_ints(int64_t n) { return ((n + kDgChunkRows - 1) / kDgChunkRows
 
 cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* /*ncols_dev*/, int ncols_fixed,
                         const SolveState* state, double* partials, int nblocks, double* G, int ldg, bool y32,
-                        cudaStream_t st, int gram_mode, int* chunk_exp) {
+                        cudaStream_t st, int gram_mode, int* chunk_exp, bool exp_ready) {
   if (gram_mode == 2 || gram_mode == 3) {
     if (!chunk_exp) return cudaErrorInvalidValue;
     const int64_t nchunks = (n + kDgChunkRows - 1) / kDgChunkRows;
@@ -1470,8 +1486,9 @@ cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* /*ncols
     const size_t esz = y32 ? 4 : 8;
     const bool vec16 = ((uintptr_t)Y % 16 == 0) && ((size_t)ld * esz) % 16 == 0;
     if (y32) {
-      gram_chunk_exp_kernel<float><<<egrid, 256, 0, st>>>(static_cast<const float*>(Y), n, ld, state, ncols_fixed,
-                                                          chunk_exp);
+      if (!exp_ready)
+        gram_chunk_exp_kernel<float><<<egrid, 256, 0, st>>>(static_cast<const float*>(Y), n, ld, state,
+                                                            ncols_fixed, chunk_exp);
       if (gram_mode == 3)
         gram_partial_tc_kernel<float, false><<<nblocks, kTcThreads, tc_smem_bytes<float>(), st>>>(
             static_cast<const float*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16, BatchView{});
@@ -1479,8 +1496,9 @@ cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* /*ncols
         gram_partial_dg_kernel<float><<<nblocks, kDgThreads, dg_smem_bytes<float>(), st>>>(
             static_cast<const float*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16);
     } else {
-      gram_chunk_exp_kernel<double><<<egrid, 256, 0, st>>>(static_cast<const double*>(Y), n, ld, state,
-                                                           ncols_fixed, chunk_exp);
+      if (!exp_ready)
+        gram_chunk_exp_kernel<double><<<egrid, 256, 0, st>>>(static_cast<const double*>(Y), n, ld, state,
+                                                             ncols_fixed, chunk_exp);
       if (gram_mode == 3)
         gram_partial_tc_kernel<double, false><<<nblocks, kTcThreads, tc_smem_bytes<double>(), st>>>(
             static_cast<const double*>(Y), n, ld, state, ncols_fixed, chunk_exp, partials, vec16, BatchView{});

@@ -182,7 +182,13 @@ int64_t gram_exp_ints(int64_t n);
 cudaError_t gram_tc_error(int* flag, bool clear);
 cudaError_t launch_gram(const void* Y, int64_t n, int64_t ld, const int* ncols_dev, int ncols_fixed,
                         const SolveState* state, double* partials, int nblocks, double* G, int ldg,
-                        bool y32, cudaStream_t st, int gram_mode = 0, int* chunk_exp = nullptr);
+                        bool y32, cudaStream_t st, int gram_mode = 0, int* chunk_exp = nullptr,
+                        bool exp_ready = false);
+// gram_mode 2, 3: the column scales of columns c0 .. c0 + count - 1 (those
+// below the state's 2 s-bar + 1) into chunk_exp; launch_gram with exp_ready
+// then skips its own pass over Y
+cudaError_t launch_chunk_exp(const void* Y, int64_t n, int64_t ld, const SolveState* state, int c0, int count,
+                             bool y32, int* chunk_exp, cudaStream_t st);
 
 // control.cu
 cudaError_t launch_kappa(const double* G, int ldg, const SolveState* state, int sbar_fixed,
