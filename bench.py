@@ -100,9 +100,9 @@ MPK_FP64_OPS_PER_CELL = {"newton": 17, "monomial": 17, "chebyshev": 19}
 FP64_PEAK_TOPS = 152 * 4 * 32 / 64 * 2.070e9 / 1e12   # binary64 lane ops/s: 4 sub-partitions x 32 lanes / 64 cycles
 # DRAM bytes per cell and level of stencil_mpk_hybrid_kernel (read + write),
 # from a one-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
-# of four steady-state levels of the 160^3 case: 197.25 MB read and
-# 44.8-47.7 MB written per launch, 242.1 MB / 4,096,000 cells
-MPK_DRAM_BYTES_PER_CELL = 59.11
+# of four steady-state levels of the 160^3 case: 197.27 MB read and
+# 44.3-48.6 MB written per launch, 243.6 MB / 4,096,000 cells
+MPK_DRAM_BYTES_PER_CELL = 59.48
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -392,11 +392,14 @@ def run_batched(args, cfg, pkg, torch, dev):
                                              basis=cfg["basis"])
             classes[key] = best
     s_max = [classes[(st.dim, int(round(math.log(st.n, 4))))] for st, _ in systems]
-    # autotuner, tile shapes: rows per work chunk and per Gram block, by timed trial batches
-    shapes = [(1024, 1024), (2048, 2048), (4096, 4096), (8192, 8192), (2048, 8192)]
+    # autotuner, tile shapes and Gram: rows per work chunk and per Gram block,
+    # and the binary64 or the tcgen05 Gram, by timed trial batches
+    tiles = [(1024, 1024), (2048, 2048), (4096, 4096), (8192, 8192), (2048, 8192)]
+    grams = [0, 3] if args.gram_mode == 3 else [0]
+    shapes = [(c, g, m) for m in grams for c, g in tiles]
     ib, shape_us = pkg.sscg.sscg_autotune_batch([s.h for s in solvers], nrhs, b, cfg["tol"], s_max, shapes,
                                                 trial_outer=20, basis=cfg["basis"])
-    batch_gram = 3 if args.gram_mode == 3 else 0   # the batch runs the binary64 or the tcgen05 Gram
+    batch_gram = shapes[ib][2]
     opts = pkg.sscg.sscg_opts_default(batch_chunk_rows=shapes[ib][0], batch_gram_rows=shapes[ib][1],
                                       gram_mode=batch_gram)
     t_tune = time.perf_counter() - t_tune
@@ -477,7 +480,7 @@ def run_batched(args, cfg, pkg, torch, dev):
             "config": {"workload": cfg["desc"], "systems": len(systems), "pairs": pairs,
                        "unknowns": int(b_np.size), "sigma_by_class": {f"{k[0]}d_4^{k[1]}": v for k, v in classes.items()},
                        "tile_rows": {"chunk": shapes[ib][0], "gram": shapes[ib][1]},
-                       "tile_us_per_inner": {f"{c}x{g}": t for (c, g), t in zip(shapes, shape_us)},
+                       "tile_us_per_inner": {f"{c}x{g} gram_mode {m}": t for (c, g, m), t in zip(shapes, shape_us)},
                        "gram_mode": batch_gram,
                        "autotune_s": t_tune},
             "status": rc, "converged": stats["converged"], "outer_loops": stats["outer_loops"],
@@ -812,25 +815,34 @@ def main():
                   "true_relres": gs[-1].true_relres, "converged": all(g.status == 0 for g in gs),
                   "note": "gram_mode 0: G = Y^T Y by binary64 FMAs, graph path"}
 
-    # ---- HSCG on the same GPU
-    hs = []
-    if args.hscg_steps > 0:
-        solver.hscg(b, x.zero_(), tol=cfg["tol"])
+    # ---- HSCG on the same GPU: with binary64 FMA chains in its SpMV (the
+    # comparator as written) and, for stencils, with the SpMV split between
+    # FMA chains and exact integer products like the s-step matrix powers
+    def time_hscg(split):
+        solver.hscg(b, x.zero_(), tol=cfg["tol"], spmv_fp64_per16=split)
         torch.cuda.synchronize()
         h0 = torch.cuda.Event(enable_timing=True)
         h1 = torch.cuda.Event(enable_timing=True)
+        hs = []
         h0.record(stream)
         for _ in range(args.hscg_steps):
             x.zero_()
-            hs.append(solver.hscg(b, x, tol=cfg["tol"]))
+            hs.append(solver.hscg(b, x, tol=cfg["tol"], spmv_fp64_per16=split))
         h1.record(stream)
         torch.cuda.synchronize()
         hscg_el = h0.elapsed_time(h1) / 1e3
-        hscg = {"value": args.hscg_steps / hscg_el, "unit": "solves/s", "ms_per_step": hscg_el / args.hscg_steps * 1e3,
+        return {"value": args.hscg_steps / hscg_el, "unit": "solves/s", "ms_per_step": hscg_el / args.hscg_steps * 1e3,
                 "iters": hs[-1].inner_iters, "true_relres": hs[-1].true_relres,
+                "converged": all(h.status == 0 for h in hs),
                 "hbm_gbs_alg": (hs[-1].inner_iters * (bytes_a + 8.0 * n * 9)) / (hscg_el / args.hscg_steps) / 1e9}
-    else:
-        hscg = None
+
+    hscg = hscg_split = None
+    if args.hscg_steps > 0:
+        hscg = time_hscg(16)
+        if hasattr(op, "kx"):
+            hscg_split = time_hscg(-1)
+            hscg_split["note"] = ("sscg_solve_hscg_ex: the SpMV's warps split between binary64 FMA chains and "
+                                  "exact integer products, the library's default share (as the s-step levels)")
 
     # ---- end to end through the C ABI with host buffers (copies inside)
     pin_b = torch.tensor(b_np, dtype=torch.float64).pin_memory()
@@ -892,6 +904,7 @@ def main():
                                "ms": sum(phase_ms.values()), "host_syncs": sp.host_syncs},
             "gram_binary64": gram64,
             "hscg": hscg,
+            "hscg_split_spmv": hscg_split,
             "roofline": roofline,
             "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         }

@@ -89,7 +89,8 @@ typedef struct {
   int batch_chunk_rows;  /* sscg_solve_batch only: rows per work chunk of the row kernels (matrix powers,
                             recombination, residual checks); 0 = 2048, else 128..1048576 */
   int batch_gram_rows;   /* sscg_solve_batch only: rows per Gram block; 0 = 2048, else 128..1048576 */
-  int mpk_fp64_per16;    /* stencil matrix-powers levels with a binary64 basis: of every 16 warps, this many
+  int mpk_fp64_per16;    /* stencil matrix-powers levels with a binary64 basis (also the stencil pairs of
+                            sscg_solve_batch, by groups of 32 rows): of every 16 warps, this many
                             form each cell's (A - theta I) v - mu v' as the binary64 FMA chain and the others
                             as exact integer products summed exactly and rounded once (both binary64-accurate;
                             the two share the level between GB300's FP64 unit and its integer pipes);
@@ -218,6 +219,18 @@ int sscg_solve_host(sscg_t h, const double* b_host, double* x_host, double tol, 
 int sscg_solve_hscg(sscg_t h, const double* b, double* x, double tol, int max_iters,
                     sscg_stats* stats);
 
+/* sscg_solve_hscg with its SpMV q = A p split like the s-step matrix powers
+ * (sscg_opts.mpk_fp64_per16): for a stencil operator, of every 16 warps
+ * spmv_fp64_per16 sum their rows as the binary64 FMA chain and the others as
+ * exact integer products rounded once (binary64-accurate, the integer form
+ * more so), so that the comparator can use GB300's integer pipes the way the
+ * s-step path does.  16 = FMA chain only (sscg_solve_hscg), 0 = integer
+ * products only, -1 = the library's tuned share; CSR operators always take
+ * the FMA chain.  Other arguments, results and errors as sscg_solve_hscg;
+ * spmv_fp64_per16 outside -1..16 returns SSCG_ERR_INVALID_ARG. */
+int sscg_solve_hscg_ex(sscg_t h, const double* b, double* x, double tol, int max_iters,
+                       int spmv_fp64_per16, sscg_stats* stats);
+
 /* Statistics of a batched solve.  The per-pair arrays are caller-owned and
  * optional (length = total number of right-hand sides when non-NULL). */
 typedef struct {
@@ -295,6 +308,17 @@ int sscg_autotune_batch(const sscg_t* systems, int nsys, const int* nrhs, const 
                         const int* s_max, sscg_basis basis, const int* chunk_rows, const int* gram_rows, int ncand,
                         int trial_outer, int* best, double* times, void* cuda_stream);
 
+/* sscg_autotune_batch with the Gram of each candidate as a third dimension:
+ * gram_modes[i] (0: binary64 FMAs, 3: the tcgen05 digit Gram; other values
+ * return SSCG_ERR_INVALID_ARG) is the sscg_opts.gram_mode of trial i; NULL
+ * means 0 for every candidate (sscg_autotune_batch).  Which Gram is faster
+ * depends on the batch's block sizes: the digit Gram's cost does not shrink
+ * with the number of columns below 32, the binary64 Gram's does. */
+int sscg_autotune_batch_ex(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double tol,
+                           const int* s_max, sscg_basis basis, const int* chunk_rows, const int* gram_rows,
+                           const int* gram_modes, int ncand, int trial_outer, int* best, double* times,
+                           void* cuda_stream);
+
 /* Ritz estimates (Algs. 3-4, eq. lest) of the handle's last s-step solve. */
 int sscg_ritz(sscg_t h, double* lmin, double* lmax);
 
@@ -302,6 +326,11 @@ int sscg_ritz(sscg_t h, double* lmin, double* lmax);
 
 /* y = A v (device pointers, length n). */
 int sscg_spmv(sscg_t h, const double* v, double* y);
+
+/* y = A v with a stencil's rows split between binary64 FMA chains and exact
+ * integer products as in sscg_solve_hscg_ex (fp64_per16: -1..16; 16 is
+ * sscg_spmv; CSR operators take the FMA chain).  Waits for the result. */
+int sscg_spmv_ex(sscg_t h, const double* v, double* y, int fp64_per16);
 
 /* The s-step basis of eq. (cg-krylovbasis) by the recurrence eq. (rho):
  * Y = [P_0, R_0, P_1, R_1, ..., P_{s-1}, R_{s-1}, P_s] (interleaved column

@@ -48,8 +48,8 @@ def _compile(src: str, verbose: bool) -> str:
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "sscg_internal.cuh"),
-                   os.path.join(HERE, "..", "include", "sscg.h"), __file__]
+    headers = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cuh")]
+    deps = srcs + headers + [os.path.join(HERE, "..", "include", "sscg.h"), __file__]
     if not force and os.path.exists(LIB):
         lib_t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= lib_t for d in deps):

@@ -835,7 +835,13 @@ int sscg_solve_host(sscg_t h, const double* b_host, double* x_host, double tol, 
 }
 
 int sscg_solve_hscg(sscg_t h, const double* b, double* x, double tol, int max_iters, sscg_stats* stats) {
+  return sscg_solve_hscg_ex(h, b, x, tol, max_iters, 16, stats);
+}
+
+int sscg_solve_hscg_ex(sscg_t h, const double* b, double* x, double tol, int max_iters, int spmv_fp64_per16,
+                       sscg_stats* stats) {
   if (!h || !b || !x || !(tol > 0.0)) return SSCG_ERR_INVALID_ARG;
+  if (spmv_fp64_per16 < -1 || spmv_fp64_per16 > 16) return SSCG_ERR_INVALID_ARG;
   const int64_t n = h->n;
   cudaStream_t st = h->stream;
   int rc;
@@ -896,7 +902,8 @@ int sscg_solve_hscg(sscg_t h, const double* b, double* x, double tol, int max_it
       return fail(e, "capture body");
     cudaError_t eb = cudaSuccess;
     for (int it = 0; it < per_check && eb == cudaSuccess; ++it)
-      eb = launch_hscg_iteration(h->state.p, h->op, h->x.p, h->r.p, h->p.p, h->q.p, h->partials.p, nb, st);
+      eb = launch_hscg_iteration(h->state.p, h->op, h->x.p, h->r.p, h->p.p, h->q.p, h->partials.p, nb, st,
+                                 spmv_fp64_per16);
     if (eb == cudaSuccess)
       eb = launch_hscg_check(h->state.p, h->op, h->b.p, h->x.p, h->r.p, h->p.p, h->rt.p, h->partials.p, nb, st);
     if (eb == cudaSuccess) eb = launch_solve_cond(h->state.p, cond, st);
@@ -1058,7 +1065,7 @@ int sscg_solve_batch(const sscg_t* systems, int nsys, const int* nrhs, const dou
       cudaError_t e2;
       if ((e2 = launch_batch_begin(v, st)) != cudaSuccess) return e2;
       for (int l = 0; l < sigma_max; ++l)
-        if ((e2 = launch_batch_mpk(v, d_Y.p, LD, l, st)) != cudaSuccess) return e2;
+        if ((e2 = launch_batch_mpk(v, d_Y.p, LD, l, st, o.mpk_fp64_per16)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_gram(v, d_Y.p, LD, d_part.p, st, o.gram_mode)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_kappa(v, sigma_max, st)) != cudaSuccess) return e2;
       if ((e2 = launch_batch_control(v, d_leja, st)) != cudaSuccess) return e2;
@@ -1348,6 +1355,14 @@ int sscg_solve_batch_hscg(const sscg_t* systems, int nsys, const int* nrhs, cons
 int sscg_autotune_batch(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double tol,
                         const int* s_max, sscg_basis basis, const int* chunk_rows, const int* gram_rows, int ncand,
                         int trial_outer, int* best, double* times, void* cuda_stream) {
+  return sscg_autotune_batch_ex(systems, nsys, nrhs, b, tol, s_max, basis, chunk_rows, gram_rows, nullptr, ncand,
+                                trial_outer, best, times, cuda_stream);
+}
+
+int sscg_autotune_batch_ex(const sscg_t* systems, int nsys, const int* nrhs, const double* b, double tol,
+                           const int* s_max, sscg_basis basis, const int* chunk_rows, const int* gram_rows,
+                           const int* gram_modes, int ncand, int trial_outer, int* best, double* times,
+                           void* cuda_stream) {
   if (!systems || nsys <= 0 || !nrhs || !b || !s_max || !chunk_rows || !gram_rows || ncand <= 0 ||
       trial_outer <= 0 || !best || !(tol > 0.0))
     return SSCG_ERR_INVALID_ARG;
@@ -1372,7 +1387,8 @@ int sscg_autotune_batch(const sscg_t* systems, int nsys, const int* nrhs, const 
     o.max_outer = trial_outer;
     o.batch_chunk_rows = chunk_rows[i];
     o.batch_gram_rows = gram_rows[i];
-    if (validate_opts(o)) {
+    o.gram_mode = gram_modes ? gram_modes[i] : 0;
+    if (validate_opts(o) || (o.gram_mode != 0 && o.gram_mode != 3)) {
       rc = SSCG_ERR_INVALID_ARG;
       break;
     }
@@ -1458,11 +1474,13 @@ int sscg_ritz(sscg_t h, double* lmin, double* lmax) {
   return SSCG_OK;
 }
 
-int sscg_spmv(sscg_t h, const double* v, double* y) {
-  if (!h || !v || !y) return SSCG_ERR_INVALID_ARG;
+int sscg_spmv(sscg_t h, const double* v, double* y) { return sscg_spmv_ex(h, v, y, 16); }
+
+int sscg_spmv_ex(sscg_t h, const double* v, double* y, int fp64_per16) {
+  if (!h || !v || !y || fp64_per16 < -1 || fp64_per16 > 16) return SSCG_ERR_INVALID_ARG;
   int rc;
   if ((rc = join_in(h))) return rc;
-  CK(launch_spmv(h->op, v, y, h->stream));
+  CK(launch_spmv_split(h->op, v, y, h->stream, nullptr, 0, fp64_per16));
   if ((rc = join_out(h))) return rc;
   CK(cudaStreamSynchronize(h->stream));
   return SSCG_OK;

@@ -90,20 +90,12 @@ __device__ __forceinline__ double to_binary64(long long S, int Em, bool& ok) {
   return __longlong_as_double((long long)((sg << 63) | (((unsigned long long)be << 52) + frac + up)));
 }
 
-// sum_j c_j y_j for K terms (K <= 8), rounded once; ok cleared as above
-template <int K>
-__device__ __forceinline__ double exact_dot(const Limbs (&c)[K], const Limbs (&y)[K], bool& ok) {
-  int E[K], Em = 0;
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    E[j] = c[j].e + y[j].e;
-    Em = E[j] > Em ? E[j] : Em;
-  }
-  long long S = 0;
-#pragma unroll
-  for (int j = 0; j < K; ++j) S += shift_down(limb_product(c[j], y[j]), Em - E[j] + 3);
-  return to_binary64(S, Em, ok);
+// c y in units of 2^(Em - 2103), Em >= c.e + y.e the largest exponent sum of
+// the dot product (truncated; see the sum bound above)
+__device__ __forceinline__ long long aligned_product(const Limbs& c, const Limbs& y, int Em) {
+  return shift_down(limb_product(c, y), Em - (c.e + y.e) + 3);
 }
+
 
 // x / 2^d rounded to nearest (ties toward +infinity), d >= 1
 __device__ __forceinline__ long long shift_round(long long x, int d) { return shift_down(shift_down(x, d - 1) + 1, 1); }

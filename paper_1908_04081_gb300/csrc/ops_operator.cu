@@ -246,10 +246,12 @@ __device__ __noinline__ double mpk_cell_fma(const Operator& A, const double* __r
 // One matrix-powers level for a stencil with a binary64 basis, its binary64
 // work split between two units: of every 16 warps, `fp64_per16` form their
 // cells' sums as the binary64 FMA chain of stencil_mpk_grid_kernel, the others
-// with exact integer products (exact_sum.cuh: the 5 or 7 stencil products,
-// and the mu term, streamed through one OnlineSum per chain and rounded once,
-// then times 1/gamma in binary64; few values stay live, so five blocks fit on
-// an SM).  GB300's FP64 unit and its integer pipes run concurrently, so
+// with exact integer products (exact_sum.cuh: the 5 or 7 stencil products and
+// the mu term of each chain, in two passes: the largest exponent sum first,
+// from the high words of the operands alone, then every product aligned to
+// it, summed and rounded once, then times 1/gamma in binary64; the products
+// of a chain are independent, and few values stay live, so five blocks fit
+// on an SM).  GB300's FP64 unit and its integer pipes run concurrently, so
 // the level's time falls towards that of the slower share.  Both forms are
 // binary64-accurate (the integer one more so); a cell's result depends only
 // on which form its warp takes, which depends only on the warp's position, so
@@ -326,17 +328,45 @@ __global__ void __launch_bounds__(256, 5) stencil_mpk_hybrid_kernel(Operator A, 
     }
     return;
   }
-  // exact integer products, term by term for both chains at once: each
-  // coefficient (-k_f, diag - theta, -mu) is split once and its products with
-  // P_l and R_l stream into one running sum per chain (OnlineSum: aligned to
-  // the largest exponent so far, rounded to nearest there, rounded once at
-  // the end), so few values stay live
-  unsigned bad2 = 0;
+  // exact integer products in two passes: the largest exponent sum of each
+  // chain, then every product aligned to it (3 guard bits) and summed
+  const double* P = Y + (int64_t)(2 * level) * ld;
+  const double* R = P + ld;
+  const double* Pm = Y + (int64_t)(2 * level - 2) * ld;
   const int nch = doR ? 2 : 1;
-  OnlineSum<3> acc0, acc1;
+  auto xe = [](double v) {
+    const int e = (int)(((unsigned)__double2hiint(v) >> 20) & 0x7ffu);
+    return e ? e : 1;
+  };
+  // pass-one loads of the high words only, opaque to the compiler so that
+  // pass two loads again instead of holding the values
+  auto ldhi = [](const double* p) {
+    int h;
+    asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(h) : "l"(reinterpret_cast<const char*>(p) + 4));
+    return __hiloint2double(h, 0);
+  };
+  int Em0 = 0, Em1 = 0;
+  auto e1 = [&](int ec, int e0, int e1v) {
+    Em0 = max(Em0, ec + e0);
+    Em1 = max(Em1, ec + e1v);
+  };
+  auto tev = [&](int ch, int oy, int ox) { return ev[ch][ly + oy][lx + ox]; };
+  e1(xe(ds), tev(0, 0, 0), tev(1, 0, 0));
+  e1(xe(ldhi(A.kx + fx)), tev(0, 0, -1), tev(1, 0, -1));
+  e1(xe(ldhi(A.kx + fx + 1)), tev(0, 0, 1), tev(1, 0, 1));
+  e1(xe(ldhi(A.ky + fy)), tev(0, -1, 0), tev(1, -1, 0));
+  e1(xe(ldhi(A.ky + fy + nx)), tev(0, 1, 0), tev(1, 1, 0));
+  if (DIM3) {
+    e1(xe(ldhi(A.kz + i)), z > 0 ? xe(ldhi(P + i - plane)) : 1, z > 0 && nch > 1 ? xe(ldhi(R + i - plane)) : 1);
+    e1(xe(ldhi(A.kz + i + plane)), z < nz - 1 ? xe(ldhi(P + i + plane)) : 1,
+       z < nz - 1 && nch > 1 ? xe(ldhi(R + i + plane)) : 1);
+  }
+  if (mu != 0.0) e1(xe(mu), xe(ldhi(Pm + i)), nch > 1 ? xe(ldhi(Pm + ld + i)) : 1);
+  unsigned bad2 = 0;
+  long long S0 = 0, S1 = 0;
   auto term = [&](const Limbs& c, const Limbs& y0, const Limbs& y1) {
-    acc0.add(c, y0);
-    if (nch > 1) acc1.add(c, y1);
+    S0 += aligned_product(c, y0, Em0);
+    if (nch > 1) S1 += aligned_product(c, y1, Em1);
   };
   auto tile = [&](int ch, int oy, int ox) {
     const int2 t = lv[ch][ly + oy][lx + ox];
@@ -347,8 +377,6 @@ __global__ void __launch_bounds__(256, 5) stencil_mpk_hybrid_kernel(Operator A, 
   term(to_limbs<true>(__ldg(A.kx + fx + 1), bad2), tile(0, 0, 1), tile(1, 0, 1));
   term(to_limbs<true>(__ldg(A.ky + fy), bad2), tile(0, -1, 0), tile(1, -1, 0));
   term(to_limbs<true>(__ldg(A.ky + fy + nx), bad2), tile(0, 1, 0), tile(1, 1, 0));
-  const double* P = Y + (int64_t)(2 * level) * ld;
-  const double* R = P + ld;
   if (DIM3) {
     const Limbs zero{0, 0, 1};
     const Limbs cd = to_limbs<true>(__ldg(A.kz + i), bad2);
@@ -358,20 +386,96 @@ __global__ void __launch_bounds__(256, 5) stencil_mpk_hybrid_kernel(Operator A, 
     term(cu, z < nz - 1 ? to_limbs(__ldg(P + i + plane), bad2) : zero,
          z < nz - 1 && nch > 1 ? to_limbs(__ldg(R + i + plane), bad2) : zero);
   }
-  if (mu != 0.0) {
-    const double* Pm = Y + (int64_t)(2 * level - 2) * ld;
+  if (mu != 0.0)
     term(to_limbs<true>(mu, bad2), to_limbs(__ldg(Pm + i), bad2),
          nch > 1 ? to_limbs(__ldg(Pm + ld + i), bad2) : Limbs{0, 0, 1});
-  }
 #pragma unroll 1
   for (int ch = 0; ch < nch; ++ch) {
     bool ok = true;
-    double w = (ch == 0 ? acc0 : acc1).result(ok);
+    double w = to_binary64(ch == 0 ? S0 : S1, ch == 0 ? Em0 : Em1, ok);
     if (!ok || bad2)
       w = mpk_cell_fma<DIM3>(A, Y + (int64_t)(2 * level + ch) * ld, Y + (int64_t)(2 * level - 2 + ch) * ld, i, x,
                              yy, z, ds, mu);
     Y[(int64_t)(2 * level + 2 + ch) * ld + i] = w * ig;
   }
+}
+
+// y = A v for a stencil, split between the two units like
+// stencil_mpk_hybrid_kernel: of every 16 warps, `fp64_per16` sum their cells
+// as the binary64 FMA chain of stencil_apply (the order of the other stencil
+// apply kernels, so those cells are their bits), the others as exact integer
+// products (exact_sum.cuh) rounded once.  Inf or NaN among a cell's inputs,
+// or a sum outside the normal binary64 range, sends the cell to the FMA
+// chain.  The SpMV of Algorithm 1 (HSCG) when the comparator is run with the
+// same split as the s-step matrix powers.
+template <bool DIM3>
+__global__ void __launch_bounds__(256, 5) stencil_apply_hybrid_kernel(Operator A, const double* __restrict__ v,
+                                                                        double* __restrict__ y,
+                                                                        const SolveState* gate, int gmode,
+                                                                        int fp64_per16) {
+  if (gate_closed(gate, gmode)) return;
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+  const int x = x0 + tx, yy = y0 + ty, z = blockIdx.z;
+  __shared__ double sv[10][34];   // v over the tile and its halo (zero outside the domain)
+  __shared__ int2 lv[10][34];     // its limbs a, b
+  __shared__ int ev[10][34];      // and exponents
+  const int64_t zoff = (int64_t)z * ny * nx;
+  unsigned bad = 0;
+  for (int e = ty * 32 + tx; e < 340; e += 256) {
+    const int ly = e / 34, lx = e - ly * 34;
+    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    const double val = in ? __ldg(v + zoff + (int64_t)gy * nx + gx) : 0.0;
+    sv[ly][lx] = val;
+    const Limbs l = to_limbs(val, bad);
+    lv[ly][lx] = make_int2(l.a, l.b);
+    ev[ly][lx] = l.e;
+  }
+  const int tile_bad = __syncthreads_or((int)bad);
+  if (x >= nx || yy >= ny) return;
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t i = zoff + (int64_t)yy * nx + x;
+  const int64_t fx = ((int64_t)z * ny + yy) * (nx + 1) + x;
+  const int64_t fy = ((int64_t)z * (ny + 1) + yy) * nx + x;
+  const double d = __ldg(A.diag + i);
+  const int ly = ty + 1, lx = tx + 1;
+  const unsigned warp = ((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * 8u + (unsigned)ty;
+  const bool fma_warp = ((warp * (unsigned)fp64_per16) & 15u) < (unsigned)fp64_per16;
+  if (fma_warp || tile_bad) {
+    double acc = d * sv[ly][lx];
+    acc = fma(-__ldg(A.kx + fx), sv[ly][lx - 1], acc);
+    acc = fma(-__ldg(A.kx + fx + 1), sv[ly][lx + 1], acc);
+    acc = fma(-__ldg(A.ky + fy), sv[ly - 1][lx], acc);
+    acc = fma(-__ldg(A.ky + fy + nx), sv[ly + 1][lx], acc);
+    if (DIM3) {
+      acc = fma(-__ldg(A.kz + i), z > 0 ? __ldg(v + i - plane) : 0.0, acc);
+      acc = fma(-__ldg(A.kz + i + plane), z < nz - 1 ? __ldg(v + i + plane) : 0.0, acc);
+    }
+    y[i] = acc;
+    return;
+  }
+  unsigned bad2 = 0;
+  OnlineSum<3> acc;   // at most 7 terms
+  auto tile = [&](int oy, int ox) {
+    const int2 t = lv[ly + oy][lx + ox];
+    return Limbs{t.x, t.y, ev[ly + oy][lx + ox]};
+  };
+  acc.add(to_limbs(d, bad2), tile(0, 0));
+  acc.add(to_limbs<true>(__ldg(A.kx + fx), bad2), tile(0, -1));
+  acc.add(to_limbs<true>(__ldg(A.kx + fx + 1), bad2), tile(0, 1));
+  acc.add(to_limbs<true>(__ldg(A.ky + fy), bad2), tile(-1, 0));
+  acc.add(to_limbs<true>(__ldg(A.ky + fy + nx), bad2), tile(1, 0));
+  if (DIM3) {
+    const Limbs zero{0, 0, 1};
+    acc.add(to_limbs<true>(__ldg(A.kz + i), bad2), z > 0 ? to_limbs(__ldg(v + i - plane), bad2) : zero);
+    acc.add(to_limbs<true>(__ldg(A.kz + i + plane), bad2), z < nz - 1 ? to_limbs(__ldg(v + i + plane), bad2) : zero);
+  }
+  bool ok = true;
+  double w = acc.result(ok);
+  if (!ok || bad2) w = mpk_cell_fma<DIM3>(A, v, v, i, x, yy, z, d, 0.0);
+  y[i] = w;
 }
 
 // ---------------------------------------------------- CSR as sliced ELL
@@ -572,11 +676,56 @@ __global__ void __launch_bounds__(kOpThreads) stencil_diag_kernel(Operator A, do
 }
 
 
+// Both chains of one stencil cell of a matrix-powers level as exact integer
+// products (exact_sum.cuh), every operand split from global memory (the
+// batched level has no tiles): (A - theta I) v - mu v' for v = P_l and R_l
+// (R only with doR), each sum rounded once.  Returns false when an input is
+// Inf or NaN or a sum leaves the normal binary64 range; the caller then takes
+// the FMA chain.
+template <bool DIM3>
+__device__ __forceinline__ bool mpk_cell_int(const Operator& A, const double* __restrict__ Pl,
+                                             const double* __restrict__ Rl, const double* __restrict__ Pm,
+                                             const double* __restrict__ Rm, int64_t i, int x, int yy, int z,
+                                             double ds, double mu, bool doR, double& wp, double& wr) {
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t fx = ((int64_t)z * ny + yy) * (nx + 1) + x;
+  const int64_t fy = ((int64_t)z * (ny + 1) + yy) * nx + x;
+  unsigned bad = 0;
+  OnlineSum<3> a0, a1;
+  const Limbs zero{0, 0, 1};
+  auto term = [&](const Limbs& c, int64_t j, bool in) {
+    a0.add(c, in ? to_limbs(__ldg(Pl + j), bad) : zero);
+    if (doR) a1.add(c, in ? to_limbs(__ldg(Rl + j), bad) : zero);
+  };
+  term(to_limbs(ds, bad), i, true);
+  term(to_limbs<true>(__ldg(A.kx + fx), bad), i - 1, x > 0);
+  term(to_limbs<true>(__ldg(A.kx + fx + 1), bad), i + 1, x < nx - 1);
+  term(to_limbs<true>(__ldg(A.ky + fy), bad), i - nx, yy > 0);
+  term(to_limbs<true>(__ldg(A.ky + fy + nx), bad), i + nx, yy < ny - 1);
+  if (DIM3) {
+    term(to_limbs<true>(__ldg(A.kz + i), bad), i - plane, z > 0);
+    term(to_limbs<true>(__ldg(A.kz + i + plane), bad), i + plane, z < nz - 1);
+  }
+  if (mu != 0.0) {
+    const Limbs cm = to_limbs<true>(mu, bad);
+    a0.add(cm, to_limbs(__ldg(Pm + i), bad));
+    if (doR) a1.add(cm, to_limbs(__ldg(Rm + i), bad));
+  }
+  bool ok = true;
+  wp = a0.result(ok);
+  wr = doR ? a1.result(ok) : 0.0;
+  return ok && !bad;
+}
+
 // Batched matrix-powers level: every chunk belongs to one pair, whose state
 // gives its own s-bar and recurrence coefficients (eq. rho); pairs that are
-// done or whose block is shorter than this level skip their chunks.
-__global__ void __launch_bounds__(kOpThreads) batch_mpk_kernel(BatchView v, double* __restrict__ Y, int64_t LD,
-                                                               int level) {
+// done or whose block is shorter than this level skip their chunks.  Stencil
+// pairs split their warps like stencil_mpk_hybrid_kernel: of every 16 groups
+// of 32 rows, fp64_per16 take the binary64 FMA chain and the others exact
+// integer products (mpk_cell_int), by the group's position alone.
+__global__ void __launch_bounds__(kOpThreads, 4) batch_mpk_kernel(BatchView v, double* __restrict__ Y, int64_t LD,
+                                                               int level, int fp64_per16) {
   for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
     const int j = v.chunk_pair[c];
     const BatchPair& bp = v.pairs[j];
@@ -601,6 +750,22 @@ __global__ void __launch_bounds__(kOpThreads) batch_mpk_kernel(BatchView v, doub
     if (r1 > bp.n) r1 = bp.n;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
       double wp, wr = 0.0;
+      // the row group of this warp (i - r0 is a multiple of 32 on lane 0)
+      const unsigned grp = (unsigned)c * 64u + (unsigned)((i - r0) >> 5);
+      if (A.kind == 1 && ((grp * (unsigned)fp64_per16) & 15u) >= (unsigned)fp64_per16) {
+        const int x = (int)(i % A.nx);
+        const int64_t t = i / A.nx;
+        const int yy = (int)(t % A.ny);
+        const int z = (int)(t / A.ny);
+        const double ds = __ldg(A.diag + i) - theta;
+        const bool ok = A.dim == 3 ? mpk_cell_int<true>(A, Pl, Rl, Pm, Rm, i, x, yy, z, ds, mu, doR, wp, wr)
+                                   : mpk_cell_int<false>(A, Pl, Rl, Pm, Rm, i, x, yy, z, ds, mu, doR, wp, wr);
+        if (ok) {
+          Pn[i] = wp * ig;
+          if (doR) Rn[i] = wr * ig;
+          continue;
+        }
+      }
       if (A.kind == 1) {
         const int x = (int)(i % A.nx);
         const int64_t t = i / A.nx;
@@ -638,9 +803,11 @@ __global__ void __launch_bounds__(kOpThreads) batch_mpk_kernel(BatchView v, doub
 
 }  // namespace
 
-cudaError_t launch_batch_mpk(const BatchView& v, double* Y, int64_t LD, int level, cudaStream_t st) {
+cudaError_t launch_batch_mpk(const BatchView& v, double* Y, int64_t LD, int level, cudaStream_t st,
+                             int fp64_per16) {
   int g = v.nchunks < 152 * 8 ? v.nchunks : 152 * 8;
-  batch_mpk_kernel<<<g < 1 ? 1 : g, kOpThreads, 0, st>>>(v, Y, LD, level);
+  const int f16 = fp64_per16 < 0 ? kBatchMpkFp64Per16 : fp64_per16;
+  batch_mpk_kernel<<<g < 1 ? 1 : g, kOpThreads, 0, st>>>(v, Y, LD, level, f16);
   return cudaGetLastError();
 }
 
@@ -656,6 +823,21 @@ cudaError_t launch_spmv(const Operator& A, const double* v, double* y, cudaStrea
   else if (A.dim == 3)
     stencil3d_apply_kernel<0><<<zmarch_grid(A), dim3(kZTx, kZTy), 0, st>>>(A, v, nullptr, y, gate, gmode);
   else stencil_spmv_kernel<false><<<g, kOpThreads, 0, st>>>(A, v, y, gate, gmode);
+  return cudaGetLastError();
+}
+
+bool spmv_split_supported(const Operator& A) {
+  return A.kind == 1 && A.nz <= 65535 && (A.ny + 7) / 8 <= 65535;
+}
+
+cudaError_t launch_spmv_split(const Operator& A, const double* v, double* y, cudaStream_t st, const SolveState* gate,
+                              int gmode, int fp64_per16) {
+  const int f16 = fp64_per16 < 0 ? kMpkFp64Per16 : fp64_per16;
+  if (f16 >= 16 || !spmv_split_supported(A)) return launch_spmv(A, v, y, st, gate, gmode);
+  if (A.dim == 3)
+    stencil_apply_hybrid_kernel<true><<<cell_grid3(A), dim3(32, 8), 0, st>>>(A, v, y, gate, gmode, f16);
+  else
+    stencil_apply_hybrid_kernel<false><<<cell_grid3(A), dim3(32, 8), 0, st>>>(A, v, y, gate, gmode, f16);
   return cudaGetLastError();
 }
 

@@ -150,6 +150,11 @@ constexpr int kMpkFp64Per16 = 8;
 cudaError_t launch_mpk_level(const Operator& A, void* Y, int64_t ld, int level,
                              const SolveState* state, int sbar_fixed, LevelCoef coef, bool y32,
                              cudaStream_t st, int fp64_per16 = -1);
+// y = A v with a stencil's cells split the same way (fp64_per16 as above; CSR
+// operators, 16, and grids beyond the launch's extents take launch_spmv)
+bool spmv_split_supported(const Operator& A);
+cudaError_t launch_spmv_split(const Operator& A, const double* v, double* y, cudaStream_t st,
+                              const SolveState* gate, int gmode, int fp64_per16);
 
 // gram.cu
 int gram_blocks(int64_t n);
@@ -229,7 +234,7 @@ cudaError_t launch_hscg_init(SolveState* state, const Operator& A, const double*
                              double* r, double* p, double* partials, int nblocks, cudaStream_t st);
 cudaError_t launch_hscg_iteration(SolveState* state, const Operator& A, double* x, double* r,
                                   double* p, double* q, double* partials, int nblocks,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int spmv_fp64_per16 = 16);
 cudaError_t launch_hscg_check(SolveState* state, const Operator& A, const double* b, const double* x,
                               double* r, double* p, double* rt, double* partials, int nblocks,
                               cudaStream_t st);
@@ -277,7 +282,13 @@ struct BatchView {
 };
 
 // batch.cu / per-file batched kernels
-cudaError_t launch_batch_mpk(const BatchView& v, double* Y, int64_t LD, int level, cudaStream_t st);
+// stencil pairs: fp64_per16 of every 16 groups of 32 rows on binary64 FMA
+// chains, the others exact integer products (negative: kBatchMpkFp64Per16,
+// all on FMA chains: without the single-system kernel's shared-memory tiles
+// the integer form costs more than it saves here)
+constexpr int kBatchMpkFp64Per16 = 16;
+cudaError_t launch_batch_mpk(const BatchView& v, double* Y, int64_t LD, int level, cudaStream_t st,
+                             int fp64_per16 = -1);
 // gram_mode 0: binary64 FMAs; 3: the tcgen05 digit Gram (v.gram_rows <= 16384)
 cudaError_t launch_batch_gram(const BatchView& v, const double* Y, int64_t LD, double* partials, cudaStream_t st,
                               int gram_mode = 0);

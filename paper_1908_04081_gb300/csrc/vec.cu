@@ -1114,8 +1114,8 @@ cudaError_t launch_hscg_init(SolveState* state, const Operator& A, const double*
 }
 
 cudaError_t launch_hscg_iteration(SolveState* state, const Operator& A, double* x, double* r, double* p, double* q,
-                                  double* partials, int nblocks, cudaStream_t st) {
-  cudaError_t e = launch_spmv(A, p, q, st, state, 2);
+                                  double* partials, int nblocks, cudaStream_t st, int spmv_fp64_per16) {
+  cudaError_t e = launch_spmv_split(A, p, q, st, state, 2, spmv_fp64_per16);
   if (e != cudaSuccess) return e;
   hscg_pq_kernel<<<nblocks, kVecThreads, 0, st>>>(state, p, q, A.n, partials);
   hscg_update_kernel<<<nblocks, kVecThreads, 0, st>>>(state, x, r, p, q, A.n, partials);

@@ -94,6 +94,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sscg_solve_hscg": (C.c_int, [_P, _P, _P, C.c_double, C.c_int, C.POINTER(Stats)]),
         "sscg_ritz": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "sscg_spmv": (C.c_int, [_P, _P, _P]),
+        "sscg_spmv_ex": (C.c_int, [_P, _P, _P, C.c_int]),
+        "sscg_solve_hscg_ex": (C.c_int, [_P, _P, _P, C.c_double, C.c_int, C.c_int, C.POINTER(Stats)]),
         "sscg_build_basis": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, _P, _I64]),
         "sscg_wait_failures": (C.c_int, [_P, C.c_int]),
         "sscg_build_basis_ex": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, _P, _I64, C.c_int]),
@@ -114,6 +116,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "sscg_autotune_batch": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(C.c_int), _P, C.c_double,
                                           C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                           C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
+        "sscg_autotune_batch_ex": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(C.c_int), _P, C.c_double,
+                                             C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                             C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_int),
+                                             C.POINTER(C.c_double), _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -269,6 +275,14 @@ def sscg_solve_hscg(h: int, b, x, tol: float, max_iters: int = 0) -> Stats:
     return st
 
 
+def sscg_solve_hscg_ex(h: int, b, x, tol: float, max_iters: int = 0, spmv_fp64_per16: int = -1) -> Stats:
+    """Algorithm 1 (HSCG) with its SpMV split between FMA chains and exact integer products."""
+    st = Stats()
+    rc = load_library().sscg_solve_hscg_ex(h, _f64(b), _f64(x), tol, max_iters, spmv_fp64_per16, C.byref(st))
+    _check(rc, "sscg_solve_hscg_ex", allow_status=True)
+    return st
+
+
 def sscg_ritz(h: int) -> tuple[float, float]:
     a, b = C.c_double(), C.c_double()
     _check(load_library().sscg_ritz(h, C.byref(a), C.byref(b)), "sscg_ritz")
@@ -277,6 +291,10 @@ def sscg_ritz(h: int) -> tuple[float, float]:
 
 def sscg_spmv(h: int, v, y) -> None:
     _check(load_library().sscg_spmv(h, _f64(v), _f64(y)), "sscg_spmv")
+
+
+def sscg_spmv_ex(h: int, v, y, fp64_per16: int) -> None:
+    _check(load_library().sscg_spmv_ex(h, _f64(v), _f64(y), fp64_per16), "sscg_spmv_ex")
 
 
 def sscg_build_basis(h: int, p, r, s: int, theta, gamma, mu, Y, ldy: int, mpk_fp64_per16: int | None = None) -> None:
@@ -394,20 +412,26 @@ def sscg_solve_batch_hscg(handles, nrhs, b, x, tol: float, max_iters: int = 0, c
 def sscg_autotune_batch(handles, nrhs, b, tol: float, s_max, shapes, trial_outer: int = 20, basis="newton",
                         stream=None):
     """Pick the batched solve's tile shapes among candidate (chunk_rows,
-    gram_rows) pairs by timed trial batches (the library's autotuner).
-    Returns (index of the best candidate, microseconds per inner iteration
-    for each candidate)."""
+    gram_rows) pairs, or (chunk_rows, gram_rows, gram_mode) triples, by timed
+    trial batches (the library's autotuner).  Returns (index of the best
+    candidate, microseconds per inner iteration for each candidate)."""
     nsys = len(handles)
     hs = (_P * nsys)(*handles)
     nr = (C.c_int * nsys)(*[int(k) for k in nrhs])
     sm = (C.c_int * nsys)(*[int(k) for k in s_max])
-    cr = (C.c_int * len(shapes))(*[int(c) for c, _ in shapes])
-    gr = (C.c_int * len(shapes))(*[int(g) for _, g in shapes])
+    cr = (C.c_int * len(shapes))(*[int(c[0]) for c in shapes])
+    gr = (C.c_int * len(shapes))(*[int(c[1]) for c in shapes])
     best = C.c_int()
     times = (C.c_double * len(shapes))()
-    _check(load_library().sscg_autotune_batch(hs, nsys, nr, _f64(b), tol, sm, BASES.get(basis, basis), cr, gr,
-                                              len(shapes), trial_outer, C.byref(best), times, _stream_ptr(stream)),
-           "sscg_autotune_batch")
+    if all(len(c) == 2 for c in shapes):
+        rc = load_library().sscg_autotune_batch(hs, nsys, nr, _f64(b), tol, sm, BASES.get(basis, basis), cr, gr,
+                                                len(shapes), trial_outer, C.byref(best), times, _stream_ptr(stream))
+    else:
+        gm = (C.c_int * len(shapes))(*[int(c[2]) if len(c) > 2 else 0 for c in shapes])
+        rc = load_library().sscg_autotune_batch_ex(hs, nsys, nr, _f64(b), tol, sm, BASES.get(basis, basis), cr, gr,
+                                                   gm, len(shapes), trial_outer, C.byref(best), times,
+                                                   _stream_ptr(stream))
+    _check(rc, "sscg_autotune_batch")
     return best.value, list(times)
 
 
@@ -458,11 +482,16 @@ class Solver:
         o = sscg_opts_default(**opts) if opts else None
         return sscg_solve_host(self.h, b, x, tol, s_max, basis, o, hist_cap)
 
-    def hscg(self, b, x, tol=1e-10, max_iters=0) -> Stats:
-        return sscg_solve_hscg(self.h, b, x, tol, max_iters)
+    def hscg(self, b, x, tol=1e-10, max_iters=0, spmv_fp64_per16=None) -> Stats:
+        if spmv_fp64_per16 is None:
+            return sscg_solve_hscg(self.h, b, x, tol, max_iters)
+        return sscg_solve_hscg_ex(self.h, b, x, tol, max_iters, spmv_fp64_per16)
 
-    def spmv(self, v, y) -> None:
-        sscg_spmv(self.h, v, y)
+    def spmv(self, v, y, fp64_per16=None) -> None:
+        if fp64_per16 is None:
+            sscg_spmv(self.h, v, y)
+        else:
+            sscg_spmv_ex(self.h, v, y, fp64_per16)
 
     def ritz(self) -> tuple[float, float]:
         return sscg_ritz(self.h)

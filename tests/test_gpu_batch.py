@@ -46,16 +46,20 @@ def split(systems, v):
     return out
 
 
-@pytest.mark.parametrize("gram_mode", [0, 3])
-def test_batch_matches_oracle_per_pair(pkg, gram_mode):
+@pytest.mark.parametrize("gram_mode,mpk_split", [(0, -1), (3, -1), (0, 0), (3, 16)])
+def test_batch_matches_oracle_per_pair(pkg, gram_mode, mpk_split):
     """With the binary64 Gram and with the tcgen05 digit Gram (one thread block
-    per 2048-row Gram block of a pair, its scales computed over its rows)."""
+    per 2048-row Gram block of a pair, its scales computed over its rows), and
+    with the matrix-powers rows split between binary64 FMA chains and exact
+    integer products by default (-1), on integer products alone (0) and on
+    FMA chains alone (16)."""
     systems, solvers, nrhs, b = build(pkg, 7, 1003, 300, 9000, 3)
     bt = torch.tensor(b, device="cuda")
     xt = torch.zeros_like(bt)
     s_max = [8 if st.dim == 2 else 12 for st, _ in systems]
     rc, stats = pkg.sscg.sscg_solve_batch([s.h for s in solvers], nrhs, bt, xt, 1e-10, s_max, "newton",
-                                          pkg.sscg.sscg_opts_default(gram_mode=gram_mode))
+                                          pkg.sscg.sscg_opts_default(gram_mode=gram_mode,
+                                                                     mpk_fp64_per16=mpk_split))
     assert pkg.sscg.sscg_wait_failures() == 0
     assert rc == 0 and stats["converged"] == stats["npairs"] == sum(nrhs)
     assert stats["graph_launches"] == 1 and stats["host_syncs"] == 1
@@ -131,6 +135,13 @@ def test_batch_tile_shapes_and_their_autotuner(pkg):
     best, times = pkg.sscg.sscg_autotune_batch(hs, nrhs, bt, 1e-10, s_max, shapes, trial_outer=8)
     assert 0 <= best < len(shapes)
     assert all(t > 0 for t in times) and times[best] == min(times)
+    # the Gram as a third dimension of the candidates (binary64 or tcgen05)
+    cands = [(2048, 2048, 0), (2048, 2048, 3), (1024, 1024, 3)]
+    best, times = pkg.sscg.sscg_autotune_batch(hs, nrhs, bt, 1e-10, s_max, cands, trial_outer=8)
+    assert 0 <= best < len(cands)
+    assert all(t > 0 for t in times) and times[best] == min(times)
+    with pytest.raises(pkg.sscg.SscgError):
+        pkg.sscg.sscg_autotune_batch(hs, nrhs, bt, 1e-10, s_max, [(2048, 2048, 2)], trial_outer=2)
     with pytest.raises(pkg.sscg.SscgError):
         pkg.sscg.sscg_solve_batch(hs, nrhs, bt, torch.zeros_like(bt), 1e-10, s_max, "newton",
                                   pkg.sscg.sscg_opts_default(batch_chunk_rows=64))

@@ -485,6 +485,109 @@ def test_hscg_matches_oracle(pkg, name):
     assert err <= 1e-8
 
 
+def _stencil_terms(st, v):
+    """The products of each row of A v for a stencil, as the library forms the
+    operator: the diagonal is ((west + east) + south) + north, plus
+    (down + up) in 3D; neighbours outside the domain are zero."""
+    dims = st.shape if len(st.shape) == 3 else (1,) + tuple(st.shape)
+    nz, ny, nx = dims
+    kx = st.kx.reshape(nz, ny, nx + 1)
+    ky = st.ky.reshape(nz, ny + 1, nx)
+    kz = st.kz.reshape(nz + 1, ny, nx) if st.kz is not None else None
+    V = np.pad(v.reshape(nz, ny, nx), 1)
+    faces = [kx[:, :, :-1], kx[:, :, 1:], ky[:, :-1, :], ky[:, 1:, :]]
+    nbrs = [V[1:-1, 1:-1, :-2], V[1:-1, 1:-1, 2:], V[1:-1, :-2, 1:-1], V[1:-1, 2:, 1:-1]]
+    if kz is not None:
+        faces += [kz[:-1], kz[1:]]
+        nbrs += [V[:-2, 1:-1, 1:-1], V[2:, 1:-1, 1:-1]]
+    d = ((faces[0] + faces[1]) + faces[2]) + faces[3]
+    if kz is not None:
+        d = d + (faces[4] + faces[5])
+    coef = [d] + [-f for f in faces]
+    vals = [v.reshape(nz, ny, nx)] + nbrs
+    return [c.ravel() for c in coef], [u.ravel() for u in vals]
+
+
+def _exact_rows(coef, vals):
+    """Each row's sum of products in rational arithmetic (exact)."""
+    from fractions import Fraction
+    return [sum((Fraction(float(c[i])) * Fraction(float(u[i])) for c, u in zip(coef, vals)), Fraction(0))
+            for i in range(coef[0].size)]
+
+
+def _fma_rows(shape, split):
+    """Rows of the split SpMV that take the binary64 FMA chain: warps of 32
+    cells along x in 32 x 8 tiles per z plane, numbered tile by tile, every
+    warp w with (w * split) mod 16 < split."""
+    nz, ny, nx = shape if len(shape) == 3 else (1,) + tuple(shape)
+    gx, gy = (nx + 31) // 32, (ny + 7) // 8
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    warp = ((z * gy + y // 8) * gx + x // 32) * 8 + y % 8
+    return (((warp * split) & 15) < split).ravel()
+
+
+@pytest.mark.parametrize("split", [0, 8, 16])
+@pytest.mark.parametrize("shape", [(19, 17, 7), (37, 29), (40, 9, 3), (1, 1, 1), (2, 3, 1), (70, 11)])
+def test_stencil_spmv_integer_products(pkg, shape, split):
+    """y = A v with the stencil's rows split between the binary64 FMA chain and
+    exact integer products (the SpMV of the split HSCG): against the exact sum
+    of every row (rational arithmetic), the FMA rows bitwise those of the
+    plain SpMV, and the integer rows within the bound of exact_sum.cuh
+    (0.55 ulp of the largest product before one rounding to nearest) even
+    where the products cancel (v constant: interior rows sum to the rounding
+    residue of the diagonal)."""
+    st = gen.varcoef_stencil(shape, seed=12)
+    n = st.n
+    s = stencil_solver(pkg, st)
+    rng = np.random.default_rng(n + split)
+    spread = rng.standard_normal(n) * 2.0 ** rng.integers(-300, 300, n)
+    spread[rng.integers(0, n, max(1, n // 10))] = 0.0
+    fma = _fma_rows(shape, split)
+    u = 2.0 ** -53
+    from fractions import Fraction
+    for v in (spread, np.full(n, 1.3), rng.standard_normal(n)):
+        coef, vals = _stencil_terms(st, v)
+        exact_q = _exact_rows(coef, vals)
+        exact = np.array([float(q) for q in exact_q])
+        absmax = np.max(np.abs(np.array(coef) * np.array(vals)), axis=0)
+        abssum = np.sum(np.abs(np.array(coef) * np.array(vals)), axis=0)
+        y = torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
+        s.spmv(dev(v), y, fp64_per16=split)
+        got = y.cpu().numpy()
+        yf = torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
+        s.spmv(dev(v), yf)
+        ref = yf.cpu().numpy()
+        assert np.array_equal(got[fma], ref[fma])
+        assert np.all(np.abs(got - exact) <= 8 * u * abssum)
+        # integer rows: |got - sum| <= u |sum| + 0.55 u max|product|, the error
+        # taken against the exact sum (not its rounding)
+        for i in np.flatnonzero(~fma):
+            err = abs(Fraction(float(got[i])) - exact_q[i])
+            assert err <= Fraction(1.0001 * u) * (abs(exact_q[i]) + Fraction(0.55 * float(absmax[i]))), \
+                (i, float(err) / max(float(absmax[i]), 1e-300))
+
+
+@pytest.mark.parametrize("split", [0, -1])
+@pytest.mark.parametrize("name", ["varcoef3d", "varcoef2d"])
+def test_hscg_split_spmv_matches_oracle(pkg, name, split):
+    """HSCG with its SpMV split between FMA chains and exact integer products
+    (sscg_solve_hscg_ex): the oracle's iteration count within 1 and x within
+    the workload tolerance.  (The SpMV rounds differently from the oracle's,
+    and over hundreds of iterations CG's count moves by a few: within 2 %.)"""
+    st_ = gen.varcoef_stencil((20, 16, 12) if name == "varcoef3d" else (61, 45), seed=8)
+    b = gen.random_rhs(st_.n, 3)
+    x0 = np.zeros(st_.n)
+    M = as_matrix(st_)
+    s = stencil_solver(pkg, st_)
+    x_o, info = cg.hscg(M, b, x0, 1e-10)
+    xt = dev(x0)
+    st = s.hscg(dev(b), xt, tol=1e-10, spmv_fp64_per16=split)
+    assert st.status == 0 and st.true_relres <= 1e-10
+    assert abs(st.inner_iters - info["iters"]) <= max(1, 0.02 * info["iters"])
+    err = np.linalg.norm(xt.cpu().numpy() - x_o) / np.linalg.norm(x_o)
+    assert err <= 1e-8
+
+
 @pytest.mark.parametrize("case,tol,status,replacements", [("poisson32", 3e-15, 0, 1), ("poisson40", 3e-15, 0, 1),
                                                           ("poisson32", 1e-16, 3, 2), ("varcoef12", 1e-16, 3, 2),
                                                           ("varcoef12", 1e-17, 3, 2)])
