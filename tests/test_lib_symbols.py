@@ -88,6 +88,14 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert L.sscg_recombine(fake, n10, n10, 34, coef, fake, -1, None) == -1
     assert L.sscg_recombine(fake, n10, n10, 3, coef, fake, 17, None) == -1
     assert L.sscg_recombine(fake, n10, n10, 3, coef, fake, -2, None) == -1
+    # the comparator's and the SpMV's split: -1..16
+    for split in (-2, 17):
+        assert L.sscg_solve_hscg_ex(fake, fake, fake, 1e-10, 0, split, None) == -1
+        assert L.sscg_spmv_ex(fake, fake, fake, split) == -1
+    assert L.sscg_solve_hscg_ex(fake, fake, fake, 0.0, 0, 16, None) == -1
+    # the batch autotuner with the Gram as a candidate dimension: arguments checked first
+    assert L.sscg_autotune_batch_ex(None, 0, None, None, 1e-10, None, 2, None, None, None, 0, 1, None, None,
+                                    None) == -1
 
 
 def L_opts_rejects_split(sscg, field="mpk_fp64_per16"):
