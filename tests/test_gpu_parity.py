@@ -588,6 +588,18 @@ def test_hscg_split_spmv_matches_oracle(pkg, name, split):
     assert err <= 1e-8
 
 
+def test_hscg_split_spmv_csr_is_the_fma_comparator(pkg):
+    """CSR operators have no split form: sscg_solve_hscg_ex with any split
+    runs the FMA SpMV, so it equals sscg_solve_hscg bit for bit."""
+    A, b, x0, _ = gen.config_problem("poisson2d_64")
+    s = pkg.Solver.csr(A.rowptr, A.col, A.val)
+    x1, x2 = dev(x0), dev(x0)
+    r1 = s.hscg(dev(b), x1, tol=1e-10)
+    r2 = s.hscg(dev(b), x2, tol=1e-10, spmv_fp64_per16=0)
+    assert r1.status == r2.status == 0 and r1.inner_iters == r2.inner_iters
+    assert torch.equal(x1, x2)
+
+
 @pytest.mark.parametrize("case,tol,status,replacements", [("poisson32", 3e-15, 0, 1), ("poisson40", 3e-15, 0, 1),
                                                           ("poisson32", 1e-16, 3, 2), ("varcoef12", 1e-16, 3, 2),
                                                           ("varcoef12", 1e-17, 3, 2)])
