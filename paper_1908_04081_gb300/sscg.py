@@ -171,7 +171,10 @@ def sscg_opts_default(**kw) -> Opts:
     """Default options (sscg_opts_default), with fields overridden by keyword."""
     o = Opts()
     load_library().sscg_opts_default(C.byref(o))
+    names = {name for name, _ in Opts._fields_}
     for k, v in kw.items():
+        if k not in names:   # a ctypes Structure would take an unknown name as a plain attribute
+            raise SscgError(f"unknown sscg_opts field {k!r}")
         if k == "c_mode" and isinstance(v, str):
             v = C_MODES[v]
         if k == "newton_scale" and isinstance(v, str):

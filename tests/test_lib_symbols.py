@@ -45,6 +45,13 @@ def test_host_only_calls(lib):
     assert b"sscg" in lib.sscg_version()
 
 
+def test_binding_rejects_unknown_options(lib):
+    from paper_1908_04081_gb300 import sscg
+    with pytest.raises(sscg.SscgError):
+        sscg.sscg_opts_default(mpk_fp64_per_16=8)   # misspelt: not a field of sscg_opts
+    assert sscg.sscg_opts_default(mpk_fp64_per16=8).mpk_fp64_per16 == 8
+
+
 def test_binding_defaults(lib):
     from paper_1908_04081_gb300 import sscg
     o = sscg.sscg_opts_default()
