@@ -95,7 +95,8 @@ typedef struct {
                             as exact integer products summed exactly and rounded once (both binary64-accurate;
                             the two share the level between GB300's FP64 unit and its integer pipes);
                             16 = FMA chain only, 0 = integer products only; default -1 = the library's
-                            tuned share */
+                            tuned share (8 for a single system; 16 in sscg_solve_batch, whose untiled
+                            level gains nothing from the integer form) */
   int rec_fp64_per16;    /* the recovery x += Y x', r = Y r', p = Y p' (eq. coords) with a binary64 basis:
                             of every 16 groups of 32 rows, this many are summed by binary64 FMA chains and
                             the others as exact integer dot products rounded once per output (within
